@@ -1,0 +1,168 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle tests and bench.py.
+
+This module holds no arithmetic of the method itself: thermodynamic quantities
+(T_c, the Maxwell coexistence densities) are passed in by the caller, who gets
+them either from the oracle (tests) or from the CUDA library's host helpers
+(bench).  It only lays out initial fields, boundary settings and random
+numbers.
+
+Random numbers come from a counter-based generator, splitmix64(seed ^ index),
+so any cell's value can be regenerated alone.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+PERIODIC, WALL, OPEN = 0, 1, 2
+
+# Parameters used by the paper's runs (Sec. 4: a, b, R, omega, relaxation
+# settings) with a = 2/49 as in the workloads of this project.
+DEFAULTS = dict(
+    a=2.0 / 49.0, b=2.0 / 21.0, R=1.0, omega=0.344, G=-1.0,
+    s_e=1.25, s_v=0.8, s_q=1.0, s_pi=1.0,
+    cv=5.0, wbar=0.75, lambda_l=1.0 / 3.0, lambda_v=1.0 / 3.0,
+    rho_l=1.0, rho_v=1.0,
+    vartheta=0, meq_printed=0, wall_ueq_zero=1, eos_kind=0, eos_c0=0.0,
+    face_kind=[PERIODIC] * 6, face_T=[0.0] * 6, face_rho=[0.0] * 6, face_theta_deg=[90.0] * 6,
+)
+
+
+def base_params(nx: int, ny: int, nz: int, **kw) -> dict:
+    d = {k: (list(v) if isinstance(v, list) else v) for k, v in DEFAULTS.items()}
+    d.update(nx=nx, ny=ny, nz=nz)
+    d.update(kw)
+    return d
+
+
+# ----------------------------------------------------------------- RNG ------
+
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """Steele, Lea & Flood's splitmix64 finaliser applied to a uint64 counter array."""
+    with np.errstate(over="ignore"):
+        z = (x + np.uint64(0x9E3779B97F4A7C15)) & _M64
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & _M64
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & _M64
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform(seed: int, n: int, stream: int = 0) -> np.ndarray:
+    """n doubles in [0, 1) from splitmix64(seed ^ (stream << 40) ^ index)."""
+    idx = np.arange(n, dtype=np.uint64)
+    key = np.uint64(seed) ^ (np.uint64(stream) << np.uint64(40))
+    r = splitmix64(idx ^ key)
+    return (r >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def perturb(field: np.ndarray, amp: float, seed: int, stream: int = 1) -> np.ndarray:
+    """field * 1 + uniform(-amp, amp) additive perturbation, seeded."""
+    r = uniform(seed, field.size, stream).reshape(field.shape)
+    return field + amp * (2.0 * r - 1.0)
+
+
+# ------------------------------------------------------------ geometry -------
+
+def grid(nx, ny, nz):
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    return x.astype(np.float64), y.astype(np.float64), z.astype(np.float64)
+
+
+def tanh_profile(dist: np.ndarray, rho_v: float, rho_l: float, W: float) -> np.ndarray:
+    """rho = (rho_l+rho_v)/2 - (rho_l-rho_v)/2 tanh(2 dist / W), dist > 0 outside the liquid (Sec. 4.2)."""
+    return 0.5 * (rho_l + rho_v) - 0.5 * (rho_l - rho_v) * np.tanh(2.0 * dist / W)
+
+
+def liquid_fraction(rho, rho_v, rho_l):
+    return np.clip((rho - rho_v) / (rho_l - rho_v), 0.0, 1.0)
+
+
+# ------------------------------------------------------------- configs ------
+
+def slab(Tc, rho_v, rho_l, nx=16, ny=16, nz=64, W=2.0, dT_bottom=0.02, lam=(0.4, 0.2), Ts_frac=0.86):
+    """Flat liquid slab z in [nz/4, 3nz/4) between bounce-back walls at z = 0 and nz-1.
+
+    Periodic in x, y; bottom wall at (Ts_frac + dT_bottom) Tc, top wall at Ts_frac Tc,
+    everything initially at T_s.
+    """
+    Ts = Ts_frac * Tc
+    x, y, z = grid(nx, ny, nz)
+    z0, z1 = nz / 4.0, 3.0 * nz / 4.0
+    # signed distance to the liquid slab [z0, z1) measured from cell centres
+    dist = np.maximum(z0 - 0.5 - z, z - (z1 - 0.5))
+    rho0 = tanh_profile(dist, rho_v, rho_l, W)
+    T0 = np.full_like(rho0, Ts)
+    p = base_params(nx, ny, nz, rho_l=rho_l, rho_v=rho_v, lambda_l=lam[0], lambda_v=lam[1],
+                    face_kind=[PERIODIC, PERIODIC, PERIODIC, PERIODIC, WALL, WALL],
+                    face_T=[0, 0, 0, 0, Ts + dT_bottom * Tc, Ts])
+    return p, rho0, T0
+
+
+def droplet(Tc, rho_v, rho_l, n=128, R=15.0, W=5.0, seed=2206, amp=1e-4, Ts_frac=0.86, Tg_frac=1.0,
+            lam=1.0 / 3.0, faces=OPEN, shape=None):
+    """Spherical droplet of radius R at the domain centre in vapor at coexistence density.
+
+    faces=OPEN: constant-pressure faces (rho_b = rho_v) on all six sides with T = Tg;
+    faces=PERIODIC: the paper's own periodic velocity field.  T0 = T_s inside the
+    liquid, Tg outside, blended by the liquid fraction.  rho carries a seeded
+    uniform(-amp, amp) perturbation.
+    """
+    nx, ny, nz = (n, n, n) if shape is None else shape
+    Ts, Tg = Ts_frac * Tc, Tg_frac * Tc
+    x, y, z = grid(nx, ny, nz)
+    cx, cy, cz = (nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0
+    r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2)
+    rho0 = tanh_profile(r - R, rho_v, rho_l, W)
+    if amp:
+        rho0 = perturb(rho0, amp, seed)
+    phi = liquid_fraction(rho0, rho_v, rho_l)
+    T0 = Ts + (Tg - Ts) * (1.0 - phi)
+    kinds = [faces] * 6
+    p = base_params(nx, ny, nz, rho_l=rho_l, rho_v=rho_v, lambda_l=lam, lambda_v=lam,
+                    face_kind=kinds, face_T=[Tg] * 6, face_rho=[rho_v] * 6)
+    return p, rho0, T0
+
+
+def sessile(Tc, rho_v, rho_l, nx=256, ny=256, nz=128, R=30.0, W=5.0, dTw=0.1, Ts_frac=0.86, theta=90.0,
+            lam=1.0 / 3.0, seed=2206, amp=0.0):
+    """Hemispherical droplet of radius R centred on a heated bottom wall.
+
+    Periodic in x, y; bounce-back wall at z = 0 held at (Ts_frac + dTw) Tc with
+    contact angle theta; constant-pressure top face (rho_b = rho_v) at T_s.
+    """
+    Ts, Tw = Ts_frac * Tc, (Ts_frac + dTw) * Tc
+    x, y, z = grid(nx, ny, nz)
+    cx, cy = nx / 2.0, ny / 2.0
+    r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + z ** 2)
+    rho0 = tanh_profile(r - R, rho_v, rho_l, W)
+    if amp:
+        rho0 = perturb(rho0, amp, seed)
+    T0 = np.full_like(rho0, Ts)
+    T0[0] = Tw
+    p = base_params(nx, ny, nz, rho_l=rho_l, rho_v=rho_v, lambda_l=lam, lambda_v=lam,
+                    face_kind=[PERIODIC, PERIODIC, PERIODIC, PERIODIC, WALL, OPEN],
+                    face_T=[0, 0, 0, 0, Tw, Ts], face_rho=[0, 0, 0, 0, 0, rho_v],
+                    face_theta_deg=[90, 90, 90, 90, theta, 90])
+    return p, rho0, T0
+
+
+def random_populations(nx, ny, nz, rho_base, T_base, w19, w7, amp, seed):
+    """Populations w_i * base * (1 + uniform(-amp, amp)), seeded; rho_base/T_base scalars or fields."""
+    N = nx * ny * nz
+    rb = np.broadcast_to(np.asarray(rho_base, dtype=np.float64), (nz, ny, nx)).reshape(-1)
+    tb = np.broadcast_to(np.asarray(T_base, dtype=np.float64), (nz, ny, nx)).reshape(-1)
+    rf = uniform(seed, 19 * N, stream=7).reshape(19, N)
+    rg = uniform(seed, 7 * N, stream=8).reshape(7, N)
+    f = np.asarray(w19)[:, None] * rb[None, :] * (1.0 + amp * (2.0 * rf - 1.0))
+    g = np.asarray(w7)[:, None] * tb[None, :] * (1.0 + amp * (2.0 * rg - 1.0))
+    return f, g
+
+
+# D3Q19 / D3Q7 weights as printed with Eqs. 2 and 14 (constants, used only to
+# scale random populations to realistic magnitudes).
+W19 = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+
+
+def w7(wbar):
+    return np.array([1.0 - wbar] + [wbar / 6.0] * 6)

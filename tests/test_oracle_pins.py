@@ -1,0 +1,628 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these tests re-types the oracle's own formulas: each checks an
+algebraic identity, a closed form, a conservation law, a symmetry, a textbook
+property of the Peng-Robinson EOS, or a printed value of the paper.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import Oracle, feq19, tables
+from paper_2206_00946_gb300 import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+T = tables()
+C19 = T["c19"].astype(float)
+C7 = T["c7"].astype(float)
+W19 = T["w19"]
+
+
+# ------------------------------------------------------------- matrices ----
+
+def test_velocity_set_and_weights_match_eq2():
+    gold = json.load(open(os.path.join(GOLD, "paper_values.json")))["d3q19_weights"]
+    c2 = (C19 ** 2).sum(1)
+    assert c2[0] == 0 and all(c2[1:7] == 1) and all(c2[7:] == 2)
+    np.testing.assert_allclose(W19[0], gold["w0"], rtol=0, atol=1e-16)
+    np.testing.assert_allclose(W19[1:7], gold["w1_6"], rtol=0, atol=1e-16)
+    np.testing.assert_allclose(W19[7:], gold["w7_18"], rtol=0, atol=1e-16)
+    # opposite pairs are (2k-1, 2k)
+    for k in range(1, 10):
+        np.testing.assert_array_equal(C19[2 * k - 1], -C19[2 * k])
+    # isotropy: sum w = 1, sum w c c = c_s^2 I, sum w c c c c = c_s^4 (delta delta + ...)
+    assert abs(W19.sum() - 1) < 1e-15
+    np.testing.assert_allclose(np.einsum("i,ia,ib->ab", W19, C19, C19), np.eye(3) / 3, atol=1e-15)
+    m4 = np.einsum("i,ia,ib,ic,id->abcd", W19, C19, C19, C19, C19)
+    d = np.eye(3)
+    iso = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d) + np.einsum("ad,bc->abcd", d, d)) / 9
+    np.testing.assert_allclose(m4, iso, atol=1e-15)
+    # Eq. 6 weights: sum varpi c c = I (so the force is -G psi grad psi to leading order)
+    varpi = np.where(c2 == 1, 1 / 6, np.where(c2 == 2, 1 / 12, 0.0))
+    np.testing.assert_allclose(np.einsum("i,ia,ib->ab", varpi, C19, C19), np.eye(3), atol=1e-15)
+
+
+def test_mhat_rows_are_the_monomials_and_inverse_exact():
+    cx, cy, cz = C19.T
+    mono = np.stack([np.ones(19), cx, cy, cz, cx**2 + cy**2 + cz**2, 2 * cx**2 - cy**2 - cz**2, cy**2 - cz**2,
+                     cx * cy, cx * cz, cy * cz, cx**2 * cy, cx * cy**2, cx**2 * cz, cx * cz**2, cy**2 * cz,
+                     cy * cz**2, cx**2 * cy**2, cx**2 * cz**2, cy**2 * cz**2])
+    np.testing.assert_array_equal(T["Mhat"], mono)
+    assert round(np.linalg.det(T["Mhat"])) == -196608
+    np.testing.assert_allclose(T["Mhat"] @ T["Mhat_inv"], np.eye(19), atol=1e-14)
+    np.testing.assert_allclose(T["Mhat_inv"] @ T["Mhat"], np.eye(19), atol=1e-14)
+    # exact rational inverse: every entry is k/12
+    np.testing.assert_allclose(T["Mhat_inv"] * 12, np.round(T["Mhat_inv"] * 12), atol=1e-12)
+
+
+def test_d3q7_matrix_and_inverse():
+    cx, cy, cz = C7.T
+    mono = np.stack([np.ones(7), cx, cy, cz, cx**2 + cy**2 + cz**2, cx**2 - cy**2, cx**2 - cz**2])
+    np.testing.assert_array_equal(T["M7"], mono)
+    np.testing.assert_allclose(T["M7"] @ T["M7_inv"], np.eye(7), atol=1e-15)
+    np.testing.assert_allclose(T["M7_inv"] * 12, np.round(T["M7_inv"] * 12), atol=1e-13)
+
+
+# ------------------------------------------------------------ equilibria ---
+
+@pytest.mark.parametrize("rho,u", [(1.0, (0, 0, 0)), (0.38, (0.05, -0.02, 0.03)), (6.5, (-0.01, 0.04, 0.07))])
+def test_feq_hermite_moments(rho, u):
+    u = np.array(u, float)
+    fe = feq19(rho, u)
+    assert abs(fe.sum() - rho) < 1e-14 * rho
+    np.testing.assert_allclose(C19.T @ fe, rho * u, atol=1e-15 * rho)
+    np.testing.assert_allclose(np.einsum("i,ia,ib->ab", fe, C19, C19), rho / 3 * np.eye(3) + rho * np.outer(u, u),
+                               atol=1e-14 * rho)
+    # third moments of the second-order Hermite equilibrium: sum c_a^2 c_b f = rho c_s^2 u_b (a != b)
+    for a in range(3):
+        for b in range(3):
+            if a != b:
+                assert abs((C19[:, a] ** 2 * C19[:, b] * fe).sum() - rho / 3 * u[b]) < 1e-15 * rho * 10
+
+
+def test_meq_closed_form_rows_0_15_and_reading_of_rows_16_18():
+    """Rows 0-15 of Eq. 9 equal M-hat f^eq; rows 16-18 of the default reading equal M-hat f^eq,
+    and with meq_printed they equal the printed expression (which differs by -rho(ua^2+ub^2)/6)."""
+    o = Oracle(W.base_params(2, 2, 2))
+    op = Oracle(W.base_params(2, 2, 2, meq_printed=1))
+    rho, u = 1.7, np.array([0.03, -0.05, 0.02])
+    ux, uy, uz = u
+    cs2 = 1 / 3
+    closed = np.array([rho, rho * ux, rho * uy, rho * uz, rho + rho * (u @ u), rho * (2 * ux**2 - uy**2 - uz**2),
+                       rho * (uy**2 - uz**2), rho * ux * uy, rho * ux * uz, rho * uy * uz, rho * cs2 * uy,
+                       rho * cs2 * ux, rho * cs2 * uz, rho * cs2 * ux, rho * cs2 * uz, rho * cs2 * uy])
+    m = o.meq19(rho, u)
+    np.testing.assert_allclose(m[:16], closed, atol=1e-15)
+    np.testing.assert_allclose(m, T["Mhat"] @ feq19(rho, u), atol=1e-15)
+    base = rho * cs2**2 * (1 - 1.5 * (u @ u))
+    printed = np.array([base + rho * cs2 * (ux**2 + uy**2), base + rho * cs2 * (ux**2 + uz**2),
+                        base + rho * cs2 * (uy**2 + uz**2)])
+    mp = op.meq19(rho, u)
+    np.testing.assert_allclose(mp[16:], printed, atol=1e-15)
+    np.testing.assert_allclose(m[16:] - mp[16:], [rho * (ux**2 + uy**2) / 6, rho * (ux**2 + uz**2) / 6,
+                                                  rho * (uy**2 + uz**2) / 6], atol=1e-15)
+
+
+# ------------------------------------------------------------- collision ---
+
+def test_collision_conserves_mass_and_adds_force_exactly():
+    o = Oracle(W.base_params(2, 2, 2))
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        rho = rng.uniform(0.3, 7)
+        u = rng.uniform(-0.05, 0.05, 3)
+        f = feq19(rho, u) * (1 + 0.05 * rng.uniform(-1, 1, 19))
+        rho_f = f.sum()
+        ueq = C19.T @ f / rho_f
+        F = rng.uniform(-0.01, 0.01, 3)
+        fs = o.collide19(f, rho_f, ueq, F)
+        assert abs(fs.sum() - rho_f) < 1e-14 * rho_f
+        np.testing.assert_allclose(C19.T @ fs, C19.T @ f + F, atol=1e-14 * rho_f)
+
+
+def test_collision_relaxes_each_moment_group_at_its_rate():
+    """With F = 0, M-hat (f* - f^eq) = (1 - s_k) M-hat (f - f^eq) for each row k (Eq. 8 + Eq. 10)."""
+    p = W.base_params(2, 2, 2, s_e=1.3, s_v=0.7, s_q=1.1, s_pi=0.9)
+    o = Oracle(p)
+    rng = np.random.default_rng(2)
+    rho, u = 1.3, np.array([0.02, 0.01, -0.03])
+    fe = feq19(rho, u)
+    d = rng.uniform(-1e-3, 1e-3, 19)
+    d -= T["Mhat_inv"][:, :4] @ (T["Mhat"][:4] @ d)  # keep rho and j unchanged
+    f = fe + d
+    fs = o.collide19(f, rho, u, np.zeros(3))
+    lam = np.array([1, 1, 1, 1, 1.3] + [0.7] * 5 + [1.1] * 6 + [0.9] * 3)
+    np.testing.assert_allclose(T["Mhat"] @ (fs - fe), (1 - lam) * (T["Mhat"] @ d), atol=1e-15)
+
+
+def test_edm_forcing_identities():
+    """Eq. 4: sum F_i = 0 and sum c_i F_i = F (the force term alone, s = 0 limit)."""
+    p = W.base_params(2, 2, 2, s_e=0.0, s_v=0.0, s_q=0.0, s_pi=0.0)
+    o = Oracle(p)
+    rho, u, F = 0.9, np.array([0.01, -0.02, 0.03]), np.array([0.004, -0.003, 0.002])
+    f = feq19(rho, u)
+    fs = o.collide19(f, rho, u, F)
+    Fi = fs - f
+    np.testing.assert_allclose(Fi, feq19(rho, u + F / rho) - feq19(rho, u), atol=1e-15)
+    assert abs(Fi.sum()) < 1e-15
+    np.testing.assert_allclose(C19.T @ Fi, F, atol=1e-15)
+
+
+def test_d3q7_collision_moments():
+    """Eq. 13 with Eq. 14-15: zeroth moment T - Fbar, first moments relaxed by (1 - varsigma),
+    m4 -> wbar T, m5, m6 -> 0, and grad T = -varsigma m_alpha / c_s^2 (Eqs. 27-29)."""
+    wbar, lam_, cv = 0.75, 0.3, 5.0
+    p = W.base_params(2, 2, 2, wbar=wbar, lambda_l=lam_, lambda_v=lam_, cv=cv)
+    o = Oracle(p)
+    rng = np.random.default_rng(3)
+    g = (np.array([1 - wbar] + [wbar / 6] * 6)) * 0.06 * (1 + 0.01 * rng.uniform(-1, 1, 7))
+    Tm = g.sum()
+    rho, u, divu, dpdT = 2.0, np.array([0.01, 0.02, -0.01]), 1e-3, 0.5
+    gs = o.collide7(g, rho, Tm, u, divu, dpdT)
+    cs2 = wbar / 3
+    vs = 1 / (lam_ / cs2 + 0.5)
+    m = T["M7"] @ g
+    gradT = -vs * m[1:4] / cs2
+    Fbar = rho * cv * (u @ gradT) + Tm * dpdT * divu
+    ms = T["M7"] @ gs
+    w7 = np.array([1 - wbar] + [wbar / 6] * 6)
+    src = T["M7"] @ (-w7 * Fbar)
+    np.testing.assert_allclose(ms[0], Tm - Fbar, rtol=1e-14)
+    np.testing.assert_allclose(ms[1:4], (1 - vs) * m[1:4] + src[1:4], atol=1e-17)
+    np.testing.assert_allclose(ms[4], wbar * Tm + src[4], rtol=1e-14)
+    np.testing.assert_allclose(ms[5:], src[5:], atol=1e-17)
+    # the source has no first moment, so grad T reads off the relaxed first moment
+    np.testing.assert_allclose(src[1:4], 0, atol=1e-18)
+
+
+# ------------------------------------------------------------------ EOS ----
+
+def _pr(a=2 / 49):
+    return Oracle(W.base_params(2, 2, 2, a=a))
+
+
+def test_pr_critical_point_textbook_values():
+    """At T_c of Eq. 38 the PR isotherm has an inflection with Z_c = 0.3074 and b rho_c = 0.2531."""
+    o = _pr()
+    Tc = o.Tc()
+    assert abs(Tc - 0.0778 * (2 / 49) / (0.45724 * (2 / 21))) < 1e-16
+    rr = np.linspace(0.5, 4.5, 40001)
+    d = np.array([o.dpdrho(r, Tc) for r in rr])
+    k = int(np.argmin(d))
+    rc = rr[k]
+    assert abs(d[k]) < 1e-4 * Tc  # inflection: dp/drho ~ 0 at its minimum
+    Zc = o.p_eos(rc, Tc) / (rc * Tc)
+    assert abs(Zc - 0.3074) < 5e-4
+    assert abs((2 / 21) * rc - 0.2531) < 5e-4
+
+
+def test_dpdT_matches_central_difference():
+    o = _pr()
+    Tc = o.Tc()
+    for rho in (0.3, 1.0, 3.0, 6.5):
+        for T in (0.8 * Tc, 0.86 * Tc, Tc):
+            h = 1e-6 * T
+            fd = (o.p_eos(rho, T + h) - o.p_eos(rho, T - h)) / (2 * h)
+            assert abs(o.dpdT(rho, T) - fd) < 1e-7 * abs(fd)
+            hr = 1e-6 * rho
+            fdr = (o.p_eos(rho + hr, T) - o.p_eos(rho - hr, T)) / (2 * hr)
+            assert abs(o.dpdrho(rho, T) - fdr) < 1e-6 * max(abs(fdr), 1e-3)
+
+
+def _ln_phi_pr(o, rho, T, a, b):
+    """Peng-Robinson fugacity coefficient (textbook closed form)."""
+    p = o.p_eos(rho, T)
+    Z = p / (rho * T)
+    kappa = 0.37464 + 1.54226 * 0.344 - 0.26992 * 0.344**2
+    xi = (1 + kappa * (1 - math.sqrt(T / o.Tc()))) ** 2
+    A = a * xi * p / T**2
+    B = b * p / T
+    s2 = math.sqrt(2)
+    return Z - 1 - math.log(Z - B) - A / (2 * s2 * B) * math.log((Z + (1 + s2) * B) / (Z + (1 - s2) * B))
+
+
+@pytest.mark.parametrize("a", [2 / 49, 3 / 49])
+@pytest.mark.parametrize("Tr", [0.7, 0.86, 0.95])
+def test_maxwell_coexistence_equal_pressure_and_fugacity(a, Tr):
+    from scipy.integrate import quad
+
+    o = _pr(a)
+    T = Tr * o.Tc()
+    rv, rl, ps = o.maxwell(T)
+    assert rv < rl
+    assert abs(o.p_eos(rv, T) - ps) < 1e-12 * ps and abs(o.p_eos(rl, T) - ps) < 1e-12 * ps
+    # equal fugacity (independent textbook form of the phase-equilibrium condition)
+    assert abs(_ln_phi_pr(o, rv, T, a, 2 / 21) - _ln_phi_pr(o, rl, T, a, 2 / 21)) < 1e-9
+    # equal area by quadrature
+    area, _ = quad(lambda r: (o.p_eos(r, T) - ps) / r**2, rv, rl, limit=200, epsabs=1e-14)
+    assert abs(area) < 1e-9 * ps / rv
+
+
+def test_maxwell_values_at_086Tc_independent_of_a():
+    """Reduced coexistence densities depend only on b, omega and T/Tc, not on a."""
+    r2 = _pr(2 / 49).maxwell(0.86 * _pr(2 / 49).Tc())
+    r3 = _pr(3 / 49).maxwell(0.86 * _pr(3 / 49).Tc())
+    assert abs(r2[0] - r3[0]) < 1e-9 and abs(r2[1] - r3[1]) < 1e-9
+
+
+def test_acentric_factor_recovered_from_vapor_pressure():
+    """omega = -log10(p_sat(0.7 Tc)/p_c) - 1 by definition; the PR kappa(omega) fit reproduces it."""
+    o = _pr()
+    Tc = o.Tc()
+    pc = 0.0778 * Tc / (2 / 21)
+    _, _, ps = o.maxwell(0.7 * Tc)
+    omega = -math.log10(ps / pc) - 1
+    assert abs(omega - 0.344) < 0.02
+
+
+# -------------------------------------------------------------- Zou-He -----
+
+def test_zouhe_top_face_matches_printed_formulas():
+    gold = json.load(open(os.path.join(GOLD, "zouhe_top_face.json")))
+    p = W.base_params(3, 3, 3, face_kind=[0, 0, 0, 0, 2, 2], face_rho=[0, 0, 0, 0, 0.5, 0.43])
+    o = Oracle(p)
+    rng = np.random.default_rng(4)
+    f = W19 * 0.43 * (1 + 0.1 * rng.uniform(-1, 1, 19))
+    F = rng.uniform(-0.01, 0.01, 3)
+    out = o.zouhe(5, f, F)
+    rb = 0.43
+    uz = (sum(f[j] for j in gold["u_z"]["ones"]) + 2 * sum(f[j] for j in gold["u_z"]["twos"]) + 0.5 * F[2]) / rb - 1
+    for k, e in gold["unknowns"].items():
+        exp = f[e["base"]] + sum(c * f[int(j)] for j, c in e["f"].items()) + e["cFx"] * F[0] + e["cFy"] * F[1] \
+            + e["cFz"] * F[2] + e["c_rhouz"] * rb * uz
+        assert abs(out[int(k)] - exp) < 1e-15, k
+    known = [i for i in range(19) if C19[i, 2] != -1]
+    np.testing.assert_array_equal(out[known], f[known])
+
+
+@pytest.mark.parametrize("face", range(6))
+def test_zouhe_identities_every_face(face):
+    """After the boundary: sum f = rho_b, tangential (sum c f + F/2) = 0 (Eqs. 38-40 with u_t = 0)."""
+    p = W.base_params(3, 3, 3, face_kind=[2] * 6, face_rho=[0.41, 0.42, 0.43, 0.44, 0.45, 0.46])
+    o = Oracle(p)
+    rng = np.random.default_rng(10 + face)
+    f = W19 * 0.4 * (1 + 0.2 * rng.uniform(-1, 1, 19))
+    F = rng.uniform(-0.02, 0.02, 3)
+    out = o.zouhe(face, f, F)
+    rb = p["face_rho"][face]
+    assert abs(out.sum() - rb) < 1e-15
+    ax = face // 2
+    for t in range(3):
+        if t != ax:
+            assert abs(C19[:, t] @ out + F[t] / 2) < 1e-15
+    n = np.zeros(3)
+    n[ax] = 1 if face % 2 else -1
+    known = np.where(C19 @ n != -1)[0]
+    np.testing.assert_array_equal(out[known], f[known])
+
+
+# -------------------------------------------------------------- lattice -----
+
+def _rand_state(p, rho_b, T_b, amp, seed):
+    return W.random_populations(p["nx"], p["ny"], p["nz"], rho_b, T_b, W19, W.w7(p["wbar"]), amp, seed)
+
+
+def test_stream_map_periodic_is_translation():
+    p = W.base_params(5, 4, 3)
+    o = Oracle(p)
+    m = o.stream_map19().reshape(19, 3, 4, 5)
+    N = 60
+    for i in range(19):
+        for z in range(3):
+            for y in range(4):
+                for x in range(5):
+                    d = m[i, z, y, x]
+                    di, dc = divmod(int(d), N)
+                    dz, r = divmod(dc, 20)
+                    dy, dx = divmod(r, 5)
+                    assert di == i
+                    assert (dx, dy, dz) == ((x + C19[i, 0]) % 5, (y + C19[i, 1]) % 4, (z + C19[i, 2]) % 3)
+    assert len(set(m.reshape(-1).tolist())) == 19 * N
+
+
+def test_stream_map_walls_bounce_and_open_faces_drop():
+    p = W.base_params(4, 3, 5, face_kind=[0, 0, 1, 1, 2, 2])
+    with pytest.raises(ValueError):  # a wall face may not share an edge with an open face
+        Oracle(p)
+    for kinds in ([0, 0, 1, 1, 0, 0], [0, 0, 0, 0, 1, 2], [2, 2, 0, 0, 2, 2]):
+        p = W.base_params(4, 3, 5, face_kind=kinds)
+        o = Oracle(p)
+        m = o.stream_map19()
+        N = 60
+        valid = m[m >= 0]
+        assert len(set(valid.tolist())) == len(valid)  # no slot written twice
+        mm = m.reshape(19, 5, 3, 4)
+        dims = (4, 3, 5)
+        for i in range(19):
+            opp = [j for j in range(19) if (C19[j] == -C19[i]).all()][0]
+            for z in range(5):
+                for y in range(3):
+                    for x in range(4):
+                        q = [x + C19[i, 0], y + C19[i, 1], z + C19[i, 2]]
+                        kind = [kinds[2 * a + (q[a] >= dims[a])] if not (0 <= q[a] < dims[a]) else None
+                                for a in range(3)]
+                        d = mm[i, z, y, x]
+                        if 1 in kind:
+                            assert d == opp * N + x + 4 * (y + 3 * z)
+                        elif 2 in kind:
+                            assert d == -1
+                        else:
+                            qq = [int(q[a]) % dims[a] for a in range(3)]
+                            assert d == i * N + qq[0] + 4 * (qq[1] + 3 * qq[2])
+    p = W.base_params(4, 3, 5, face_kind=[2, 2, 0, 0, 2, 2])
+    cls = Oracle(p).node_class().reshape(5, 3, 4)
+    assert cls[0, 1, 1] == (1 << 4) and cls[4, 1, 1] == (1 << 5) and cls[2, 1, 0] == (1 << 0)
+    assert cls[0, 0, 0] == (1 << 4) | (1 << 0) and cls[2, 0, 2] == 0
+
+
+@pytest.mark.parametrize("kinds", [[0, 0, 0, 0, 1, 2], [2] * 6, [1] * 6, [0, 0, 1, 1, 0, 0]])
+def test_uniform_rest_state_is_a_fixed_point_with_all_boundary_kinds(kinds):
+    rho, Tm = 0.3797, 0.06271
+    p = W.base_params(4, 5, 6, face_kind=kinds, face_T=[Tm] * 6, face_rho=[rho] * 6, rho_v=0.38, rho_l=6.5,
+                      lambda_l=0.4, lambda_v=0.2)
+    o = Oracle(p)
+    f, g = o.init_state(np.full(120, rho), np.full(120, Tm))
+    st, f2, g2 = o.run(f, g, 200)
+    assert st == 0
+    np.testing.assert_allclose(f2, f, rtol=1e-13)
+    np.testing.assert_allclose(g2, g, rtol=1e-13)
+
+
+def test_mass_conserved_periodic_and_walls(thermo):
+    p, rho0, T0 = W.slab(thermo["Tc"], thermo["rho_v"], thermo["rho_l"], nx=3, ny=4, nz=12)
+    o = Oracle(p)
+    f, g = o.init_state(rho0, T0)
+    f = f * (1 + 1e-3 * W.uniform(5, f.size).reshape(f.shape))
+    m0 = f.sum()
+    st, f2, g2 = o.run(f, g, 300)
+    assert st == 0
+    assert abs(f2.sum() - m0) < 1e-12 * m0
+
+
+def test_total_momentum_conserved_periodic(thermo):
+    """Pairwise-antisymmetric interaction force: sum_x F = 0, so total momentum is invariant."""
+    p, rho0, T0 = W.droplet(thermo["Tc"], thermo["rho_v"], thermo["rho_l"], n=8, R=2.5, W=2.0, faces=0)
+    o = Oracle(p)
+    f, g = o.init_state(rho0, T0)
+    f = f * (1 + 1e-3 * W.uniform(6, f.size).reshape(f.shape))
+    j0 = C19.T @ f.sum(1)
+    st, f2, _ = o.run(f, g, 100)
+    assert st == 0
+    np.testing.assert_allclose(C19.T @ f2.sum(1), j0, atol=1e-12 * f.sum())
+
+
+def _perm_index(c, perm, flip):
+    """index map i -> i' with c_{i'} = flip * c_i[perm]"""
+    out = []
+    for i in range(len(c)):
+        ci = c[i][list(perm)] * np.array(flip)
+        out.append([j for j in range(len(c)) if (c[j] == ci).all()][0])
+    return np.array(out)
+
+
+@pytest.mark.parametrize("kinds", [[2, 2, 0, 0, 2, 2], [1, 1, 0, 0, 1, 1], [0, 0, 0, 0, 1, 2]])
+def test_cubic_symmetry_axis_permutation_and_reflection(kinds):
+    """Swapping x and z (with the faces swapped) and reflecting z commute with the step."""
+    nx, ny, nz = 4, 5, 6
+    base = dict(face_kind=kinds, face_T=[0.0615, 0.0625, 0.061, 0.063, 0.062, 0.064],
+                face_rho=[0.41, 0.42, 0.43, 0.44, 0.4, 0.39], rho_v=0.38, rho_l=6.5, lambda_l=0.4, lambda_v=0.2,
+                face_theta_deg=[90, 90, 70, 80, 100, 120])
+    p = W.base_params(nx, ny, nz, **base)
+    o = Oracle(p)
+    x, y, z = W.grid(nx, ny, nz)
+    rho0 = 0.38 + 3.0 * np.exp(-((x - 1.7) ** 2 + (y - 2.2) ** 2 + (z - 2.6) ** 2) / 3.0)
+    f, g = o.init_state(rho0, 0.0625 + 0.001 * np.sin(x + 2 * y + 3 * z))
+    f = f * (1 + 1e-3 * W.uniform(7, f.size).reshape(f.shape))
+    st, f1, g1 = o.run(f, g, 3)
+    assert st == 0
+    # x <-> z swap
+    def swap_faces(v):
+        return [v[4], v[5], v[2], v[3], v[0], v[1]]
+    q = W.base_params(nz, ny, nx, **{k: (swap_faces(v) if k.startswith("face_") else v) for k, v in base.items()})
+    oq = Oracle(q)
+    pi19 = _perm_index(C19, (2, 1, 0), (1, 1, 1))
+    pi7 = _perm_index(C7, (2, 1, 0), (1, 1, 1))
+    def tr(a, pi):
+        a = a.reshape(len(pi), nz, ny, nx).transpose(0, 3, 2, 1)  # [i, x, y, z] -> new (z'=x, y, x'=z)
+        out = np.empty_like(a)
+        out[pi] = a
+        return out.reshape(len(pi), -1)
+    st, fq, gq = oq.run(tr(f, pi19), tr(g, pi7), 3)
+    assert st == 0
+    np.testing.assert_allclose(fq, tr(f1, pi19), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(gq, tr(g1, pi7), rtol=1e-12, atol=1e-15)
+    # z reflection
+    r = W.base_params(nx, ny, nz, **{k: ([v[0], v[1], v[2], v[3], v[5], v[4]] if k.startswith("face_") else v)
+                                      for k, v in base.items()})
+    orf = Oracle(r)
+    ri19 = _perm_index(C19, (0, 1, 2), (1, 1, -1))
+    ri7 = _perm_index(C7, (0, 1, 2), (1, 1, -1))
+    def refl(a, pi):
+        a = a.reshape(len(pi), nz, ny, nx)[:, ::-1]
+        out = np.empty_like(a)
+        out[pi] = a
+        return out.reshape(len(pi), -1)
+    st, fr, gr = orf.run(refl(f, ri19), refl(g, ri7), 3)
+    np.testing.assert_allclose(fr, refl(f1, ri19), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(gr, refl(g1, ri7), rtol=1e-12, atol=1e-15)
+
+
+def test_nee_sets_boundary_temperature_and_open_faces_density(thermo):
+    nx, ny, nz = 5, 4, 6
+    p = W.base_params(nx, ny, nz, face_kind=[2, 2, 0, 0, 2, 2], face_T=[0.060, 0.061, 0, 0, 0.062, 0.063],
+                      face_rho=[0.40, 0.41, 0, 0, 0.42, 0.43], rho_v=thermo["rho_v"], rho_l=thermo["rho_l"])
+    o = Oracle(p)
+    tz = 0.0625 + 1e-3 * W.uniform(9, nx * ny).reshape(ny, nx)
+    o.set_face_T([None, None, None, None, tz, None])
+    f, g = _rand_state(p, 0.4, 0.0625, 0.02, 11)
+    st, f2, g2 = o.step(f, g)
+    assert st == 0
+    Tn = g2.sum(0).reshape(nz, ny, nx)
+    rn = f2.sum(0).reshape(nz, ny, nx)
+    np.testing.assert_allclose(Tn[0, :, 1:-1], tz[:, 1:-1], rtol=1e-14)
+    np.testing.assert_allclose(Tn[-1, :, 1:-1], 0.063, rtol=1e-14)
+    np.testing.assert_allclose(Tn[1:-1, :, 0], 0.060, rtol=1e-14)
+    np.testing.assert_allclose(Tn[0, :, 0], 0.5 * (0.060 + tz[:, 0]), rtol=1e-14)  # edge: mean of the faces
+    np.testing.assert_allclose(rn[-1, :, 1:-1], 0.43, rtol=1e-14)
+    np.testing.assert_allclose(rn[1:-1, :, -1], 0.41, rtol=1e-14)
+    assert np.isfinite(f2).all() and np.isfinite(g2).all()
+
+
+def test_psi_domain_error_is_reported():
+    o = Oracle(W.base_params(3, 3, 3))
+    Tc = o.Tc()
+    f, g = o.init_state(np.full(27, 9.5), np.full(27, 3 * Tc))  # p_EOS > rho/3 in a dense hot fluid
+    st, _, _ = o.step(f, g)
+    assert st == -4
+
+
+# -------------------------------------------------------------- physics -----
+
+def _mode(field, k, axis_vals):
+    return 2 * np.mean(field * np.sin(k * axis_vals)), 2 * np.mean(field * np.cos(k * axis_vals))
+
+
+def test_shear_wave_decays_at_kinematic_viscosity():
+    """u_x = U sin(kz) decays as exp(-nu k^2 t), nu = c_s^2 (1/s_v - 1/2) = 0.25 (Sec. 4)."""
+    nz = 32
+    p = W.base_params(1, 1, nz, eos_kind=1, eos_c0=0.2)
+    o = Oracle(p)
+    k = 2 * np.pi / nz
+    z = np.arange(nz, dtype=float)
+    f = np.stack([feq19(1.0, np.array([1e-3 * np.sin(k * zz), 0, 0])) for zz in z], axis=1)
+    g = np.outer(W.w7(0.75), np.full(nz, 0.06))
+    st, f, g = o.run(f, g, 100)
+    a1 = _mode(C19[:, 0] @ f, k, z)[0]
+    st, f, g = o.run(f, g, 400)
+    a2 = _mode(C19[:, 0] @ f, k, z)[0]
+    nu = -np.log(a2 / a1) / (400 * k * k)
+    assert abs(nu - 0.25) < 0.01 * 0.25
+
+
+def test_thermal_diffusion_rate_ideal_gas():
+    """With p = c0 rho (no T coupling) and u = 0, Eq. 12 is rho c_v dT/dt = lambda lap T."""
+    nz, lam, cv, rho = 64, 0.1, 2.0, 1.0
+    p = W.base_params(1, 1, nz, eos_kind=1, eos_c0=0.2, lambda_l=lam, lambda_v=lam, cv=cv)
+    o = Oracle(p)
+    k = 2 * np.pi / nz
+    z = np.arange(nz, dtype=float)
+    f, g = o.init_state(np.full(nz, rho), 1.0 + 1e-3 * np.sin(k * z))
+    st, f, g = o.run(f, g, 50)
+    a1 = _mode(g.sum(0) - 1.0, k, z)[0]
+    st, f, g = o.run(f, g, 500)
+    a2 = _mode(g.sum(0) - 1.0, k, z)[0]
+    alpha = -np.log(a2 / a1) / (500 * k * k)
+    assert abs(alpha - lam / (rho * cv)) < 0.01 * lam / (rho * cv)
+
+
+def test_temperature_advected_by_uniform_flow_ideal_gas():
+    """Fbar = rho c_v u.grad T with grad T from the local moments carries T at the flow speed."""
+    nx, U = 64, 0.04
+    p = W.base_params(nx, 1, 1, eos_kind=1, eos_c0=0.2, lambda_l=0.02, lambda_v=0.02, cv=2.0)
+    o = Oracle(p)
+    k = 2 * np.pi / nx
+    x = np.arange(nx, dtype=float)
+    f = np.stack([feq19(1.0, np.array([U, 0, 0])) for _ in x], axis=1)
+    g = np.outer(W.w7(0.75), 1.0 + 1e-3 * np.sin(k * x))
+    st, f, g = o.run(f, g, 20)
+    s1, c1 = _mode(g.sum(0) - 1.0, k, x)
+    st, f, g = o.run(f, g, 400)
+    s2, c2 = _mode(g.sum(0) - 1.0, k, x)
+    dphi = np.angle(s2 - 1j * c2) - np.angle(s1 - 1j * c1)
+    dphi = (dphi + np.pi) % (2 * np.pi) - np.pi
+    speed = dphi / (k * 400)
+    assert abs(speed - U) < 0.02 * U
+
+
+def test_adiabatic_temperature_follows_density_in_sound_wave(thermo):
+    """Without conduction the T source -T (dp/dT) div u gives dT = T (dp/dT) drho / (rho^2 c_v) (Eq. 12)."""
+    nz, cv = 128, 5.0
+    rl, Ts = thermo["rho_l"], thermo["Ts"]
+    p = W.base_params(1, 1, nz, lambda_l=1e-3, lambda_v=1e-3, cv=cv, rho_l=rl, rho_v=thermo["rho_v"])
+    o = Oracle(p)
+    k = 2 * np.pi / nz
+    z = np.arange(nz, dtype=float)
+    A = 1e-4 * rl
+    f, g = o.init_state(rl + A * np.sin(k * z), np.full(nz, Ts))
+    K = Ts * o.dpdT(rl, Ts) / (rl**2 * cv)
+    xs, ys = [], []
+    for _ in range(30):
+        st, f, g = o.run(f, g, 10)
+        dr = _mode(f.sum(0) - rl, k, z)[0]
+        dT = _mode(g.sum(0) - Ts, k, z)[0]
+        xs.append(dr - A)
+        ys.append(dT)
+    xs, ys = np.array(xs), np.array(ys)
+    assert np.ptp(xs) > 0.5 * A  # the wave actually oscillated
+    Kfit = (xs @ ys) / (xs @ xs)
+    assert abs(Kfit / K - 1) < 0.03
+
+
+@pytest.mark.slow
+def test_flat_interface_mechanical_equilibrium_and_coexistence(thermo):
+    """Steady flat interface (periodic, quasi-1D): bulk p_EOS equal on both sides; densities near Maxwell."""
+    p, rho0, T0 = W.slab(thermo["Tc"], thermo["rho_v"], thermo["rho_l"], nx=1, ny=1, nz=64)
+    p["face_kind"] = [0] * 6
+    p["lambda_l"] = p["lambda_v"] = 1.5
+    o = Oracle(p)
+    f, g = o.init_state(rho0, T0)
+    st, f, g = o.run(f, g, 30000)
+    assert st == 0
+    st, m = o.macros(f, g)
+    rho, Tm = m["rho"], m["T"]
+    assert np.ptp(Tm) < 1e-6 * Tm.mean() and np.abs(m["uz"]).max() < 1e-5
+    pl, pv = o.p_eos(rho[32], Tm[32]), o.p_eos(rho[0], Tm[0])
+    assert abs(pl - pv) < 1e-3 * pv
+    rv_m, rl_m, _ = o.maxwell(Tm.mean())
+    assert abs(rho[32] / rl_m - 1) < 0.01
+    assert abs(rho[0] / rv_m - 1) < 0.25
+
+
+def test_steady_conduction_between_dirichlet_walls_is_exactly_linear():
+    """Uniform conductor, no flow (ideal EOS, rest): the steady profile is T0 + (T1-T0) z/(nz-1) at every node,
+    wall nodes included (the extrapolated non-equilibrium part carries the flux, Eqs. 35-36)."""
+    nz = 12
+    p = W.base_params(1, 1, nz, eos_kind=1, eos_c0=0.2, lambda_l=0.3, lambda_v=0.3, cv=1.0,
+                      face_kind=[0, 0, 0, 0, 1, 1], face_T=[0, 0, 0, 0, 1.0, 1.2])
+    o = Oracle(p)
+    f, g = o.init_state(np.ones(nz), np.full(nz, 1.1))
+    st, f, g = o.run(f, g, 4000)
+    assert st == 0
+    np.testing.assert_allclose(g.sum(0), 1.0 + 0.2 * np.arange(nz) / (nz - 1), rtol=1e-10)
+
+
+@pytest.mark.parametrize("theta", [90.0, 120.0, 60.0])
+def test_wall_force_uses_the_wetting_ghost_layer(theta):
+    """At wall nodes the force (Eq. 6) sees the ghost layer of Eq. 36:
+    psi(x,y,-1) = psi(x,y,1) + sqrt((psi(x+1,y,0)-psi(x-1,y,0))^2 + (psi(x,y+1,0)-psi(x,y-1,0))^2) tan(pi/2 - theta)."""
+    nx, ny, nz = 5, 4, 6
+    p = W.base_params(nx, ny, nz, face_kind=[0, 0, 0, 0, 1, 1], face_T=[0, 0, 0, 0, 0.0627, 0.0627],
+                      face_theta_deg=[90, 90, 90, 90, theta, 90], rho_v=0.38, rho_l=6.5)
+    o = Oracle(p)
+    x, y, z = W.grid(nx, ny, nz)
+    rho0 = 0.4 + 2.0 * np.exp(-((x - 2.2) ** 2 + (y - 1.3) ** 2 + z**2) / 2.5)
+    f, g = o.init_state(rho0, np.full(rho0.shape, 0.0627))
+    st, m = o.macros(f, g)
+    psi = m["psi"].reshape(nz, ny, nx)
+    ext = np.zeros((nz + 2, ny, nx))
+    ext[1:-1] = psi
+    tn = math.tan(math.pi / 2 - math.radians(theta))
+    for yy in range(ny):
+        for xx in range(nx):
+            grad = math.hypot(psi[0, yy, (xx + 1) % nx] - psi[0, yy, (xx - 1) % nx],
+                              psi[0, (yy + 1) % ny, xx] - psi[0, (yy - 1) % ny, xx])
+            ext[0, yy, xx] = psi[1, yy, xx] + grad * tn
+            ext[-1, yy, xx] = psi[-2, yy, xx]
+    varpi = np.where((C19 ** 2).sum(1) == 1, 1 / 6, 1 / 12)
+    for yy in range(ny):
+        for xx in range(nx):
+            s = np.zeros(3)
+            for i in range(1, 19):
+                cx, cy, cz = C19[i].astype(int)
+                s += varpi[i] * ext[1 + cz, (yy + cy) % ny, (xx + cx) % nx] * C19[i]
+            Fexp = psi[0, yy, xx] * s  # -G psi sum(...) with G = -1
+            c = xx + nx * yy
+            np.testing.assert_allclose([m["Fx"][c], m["Fy"][c], m["Fz"][c]], Fexp, rtol=1e-12, atol=1e-15)
