@@ -1,0 +1,326 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused D3Q19 + D3Q7 time step (thermal pseudopotential MRT-LBM, arXiv 2206.00946).
+
+Workload (one "step" = one lattice-Boltzmann time step over the whole domain):
+d^2-law droplet on a 128^3 lattice, radius 15, seeded +-1e-4 density noise,
+constant-pressure faces on all six sides (rho_b = rho_v), T = T_c on the faces,
+FP32 populations.  Metric: million lattice updates per second (MLUPS), whole
+job, and the fraction of the measured HBM copy bandwidth that the 208 bytes of
+algorithmic traffic per lattice update reach.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun, one rank per GPU) runs N independent replicas of the domain
+(weak scaling, no collective on the data path).  --impl reference times the
+FP64 CPU oracle on host cores on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2206_00946_gb300 import workloads as W  # noqa: E402
+
+METRIC = "fused D3Q19+D3Q7 MLUPS"
+UNIT = "MLUPS"
+BYTES_PER_LU = 208  # f and g (19 + 7 FP32 populations) read once and written once per lattice update
+WORKLOAD = "d2-law droplet 128^3, R=15, W=5, open (Zou-He) faces rho_b=rho_v, T_faces=T_c, seed 2206"
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def src_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2206_00946_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_digest: str, n_cells: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic_k_fused.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("kernel_src_sha") != kernel_digest:
+        return None
+    return d["dram_bytes_per_cell"] * n_cells
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def thermo_product():
+    """T_c and the coexistence densities from the library's host helpers (not the oracle)."""
+    from paper_2206_00946_gb300 import lbm
+    p = W.base_params(4, 4, 4)
+    Tc = lbm.lbm_Tc(p)
+    rv, rl, _ = lbm.lbm_maxwell(p, 0.86 * Tc)
+    return Tc, rv, rl
+
+
+def cpu_oracle_sample(p, rho0, T0, steps: int):
+    """Oracle (FP64, single thread, as it stands) on the workload for `steps` steps; returns MLUPS."""
+    from oracle import Oracle
+    o = Oracle(p)
+    f, g = o.init_state(rho0, T0)
+    t0 = time.perf_counter()
+    st, f, g = o.run(f, g, steps)
+    dt = time.perf_counter() - t0
+    return p["nx"] * p["ny"] * p["nz"] * steps / dt / 1e6, dt
+
+
+def run_reference(args, rank, world):
+    """The oracle on host cores: each timed step one lattice update of a bounded sub-box of the workload."""
+    if rank != 0:
+        return 0
+    from oracle import Oracle
+    o0 = Oracle(W.base_params(4, 4, 4))
+    Tc = o0.Tc()
+    rv, rl, _ = o0.maxwell(0.86 * Tc)
+    p, rho0, T0 = W.droplet(Tc, rv, rl, n=128, R=15.0)
+    # sub-box around the droplet, sized so that warmup + steps take about two minutes
+    budget_s, us_per_lu = 120.0, 5.0
+    cells = max(8 ** 3, int(budget_s / (us_per_lu * 1e-6) / max(1, args.steps + args.warmup)))
+    s = int(round(cells ** (1.0 / 3.0)))
+    s = max(8, min(128, s))
+    lo = 64 - s // 2
+    sub = (slice(lo, lo + s),) * 3
+    q = dict(p, nx=s, ny=s, nz=s)
+    o = Oracle(q)
+    f, g = o.init_state(np.ascontiguousarray(rho0[sub]), np.ascontiguousarray(T0[sub]))
+    for _ in range(args.warmup):
+        _, f, g = o.step(f, g)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, f, g = o.step(f, g)
+    dt = time.perf_counter() - t0
+    mlups = s ** 3 * args.steps / dt / 1e6
+    sample = f"{s}^3 sub-box at the droplet centre of the 128^3 workload, one lattice update per timed step"
+    line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=128, help="lattice side (the workload is 128)")
+    ap.add_argument("--schedule", default="fused", choices=["fused", "phases"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    rank, world, local = dist_env()
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    from paper_2206_00946_gb300 import lbm
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    Tc, rv, rl = thermo_product()
+    p, rho0, T0 = W.droplet(Tc, rv, rl, n=args.n, R=15.0)
+    p["schedule"] = lbm.SCHED_FUSED if args.schedule == "fused" else lbm.SCHED_PHASES
+    N = p["nx"] * p["ny"] * p["nz"]
+    stream = torch.cuda.current_stream()
+    rho_d = torch.tensor(rho0.reshape(-1), dtype=torch.float32, device="cuda")
+    T_d = torch.tensor(T0.reshape(-1), dtype=torch.float32, device="cuda")
+    lat = lbm.Lattice(p, rho_d, T_d, stream=stream.cuda_stream)
+    launches = lat.lbm_launches_per_step()
+
+    # warm-up
+    lat.lbm_step(args.warmup)
+    torch.cuda.synchronize()
+    st = lat.lbm_sync()
+    if st != lbm.OK:
+        raise SystemExit(f"warm-up failed: {lbm.lbm_status_string(st)}")
+
+    # timed region: K steps, bracketed by barrier + synchronize, CUDA events on the launch stream
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        lat.lbm_step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    st = lat.lbm_sync()
+    if st != lbm.OK:
+        raise SystemExit(f"timed run failed: {lbm.lbm_status_string(st)}")
+    t_ms = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
+    ms_max = float(t_ms.item())
+    ms_step = ms_max / args.steps
+    value = world * N * args.steps / (ms_max * 1e-3) / 1e6
+
+    # per-launch duration of the step kernel (one launch per step in the fused schedule)
+    nl = min(args.steps, 200)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nl)]
+    for a, b in evs:
+        a.record(stream)
+        lat.lbm_step(1)
+        b.record(stream)
+    torch.cuda.synchronize()
+    per_launch_ms = statistics.mean(a.elapsed_time(b) for a, b in evs) / max(1, launches)
+    lat.close()
+
+    # end to end through the C ABI with host buffers: init from host fields, K steps, macros to host
+    rho_h = np.ascontiguousarray(rho0.reshape(-1), dtype=np.float32)
+    T_h = np.ascontiguousarray(T0.reshape(-1), dtype=np.float32)
+    outs = {k: np.empty(N, dtype=np.float32) for k in ("rho", "ux", "uy", "uz", "T")}
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    lat2 = lbm.Lattice(p, rho_h, T_h, stream=stream.cuda_stream)
+    lat2.lbm_step(args.steps)
+    st2 = lat2.lbm_macros(**outs)
+    e2e_s = time.perf_counter() - t0
+    lat2.close()
+    if st2 != lbm.OK:
+        raise SystemExit(f"e2e run failed: {lbm.lbm_status_string(st2)}")
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * N * args.steps / float(e2e_t.item()) / 1e6
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    pk = peaks()
+    peak = pk.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in pk else "fallback"
+    achieved = BYTES_PER_LU * N / (per_launch_ms * 1e-3) / 1e9 if launches == 1 else BYTES_PER_LU * N / (ms_step * 1e-3) / 1e9
+    digest = src_digest()
+    traffic = ncu_traffic(digest, N)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        steps_cpu = 2
+        mlups_cpu, dt = cpu_oracle_sample(p, rho0, T0, steps_cpu)
+        cpu = {"value": mlups_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{steps_cpu} full steps of the {args.n}^3 workload ({dt:.1f} s, single thread)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.n == 128 else WORKLOAD.replace("128^3", f"{args.n}^3"),
+                   "cells": N, "schedule": args.schedule, "parallelism": f"replicas x{world}",
+                   "l2": f"inputs larger than L2: {2 * 26 * 4 * N / 1e6:.0f} MB of double-buffered populations"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)",
+                     "bytes_per_lu": BYTES_PER_LU, "kernel": "k_fused" if launches == 1 else "step",
+                     "per_launch_ms": per_launch_ms, "kernel_src_sha": digest},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * N / args.steps,
+                "d2h_bytes_per_step": 5 * 4 * N / args.steps},
+        "gpu_launches": launches * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

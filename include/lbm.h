@@ -1,0 +1,148 @@
+/*
+ * liblbm: GB300 (sm_103a) hot path of the thermal pseudopotential MRT lattice
+ * Boltzmann method for 3D liquid-vapor phase change of Huang, Wang, He & Huang,
+ * "An efficient thermal lattice Boltzmann method for simulating
+ * three-dimensional liquid-vapor phase change" (arXiv 2206.00946).
+ *
+ * One time step updates every lattice cell:
+ *   (a) Peng-Robinson p_EOS(rho, T) (Sec. 4, Eq. 37) and the pseudopotential
+ *       psi = sqrt(2 (p_EOS - rho c_s^2) / G) (Sec. 2.1, Eq. 7);
+ *   (b) the 18-neighbour interaction force F = -G psi(x) sum w(|c|^2) psi(x+c) c (Eq. 6);
+ *   (c) the D3Q19 non-orthogonal MRT collision with the exact-difference forcing
+ *       (Eqs. 2-5, 8-10, appendix matrix M-hat), streaming, bounce-back walls
+ *       (Sec. 3.1) and the constant-pressure open boundary (Sec. 3.3);
+ *   (d) the D3Q7 MRT temperature collision with the source -w_i Fbar,
+ *       Fbar = rho c_v u.grad T + T (dp/dT)_rho div u (Eqs. 13-15, 27-29), the
+ *       relaxed streaming of Eq. 13 and the non-equilibrium extrapolation at
+ *       Dirichlet faces (Sec. 3.1).
+ *
+ * Conventions
+ *  - Lattice units, dx = dt = 1.  Cell index c = x + nx*(y + ny*z), x fastest.
+ *  - Population layout (state exchanged by lbm_set_state / lbm_get_state):
+ *    structure of arrays, f[i*N + c] for i = 0..18 and g[i*N + c] for i = 0..6,
+ *    N = nx*ny*nz, float32.  Velocity order: 0 rest, 1/2 +-x, 3/4 +-y, 5/6 +-z,
+ *    7 (1,1,0) 8 (-1,-1,0) 9 (1,-1,0) 10 (-1,1,0) 11 (1,0,1) 12 (-1,0,-1)
+ *    13 (1,0,-1) 14 (-1,0,1) 15 (0,1,1) 16 (0,-1,-1) 17 (0,1,-1) 18 (0,-1,1),
+ *    read off rows 1-3 of the appendix matrix; D3Q7: 0 rest, 1/2 +-x, 3/4 +-y, 5/6 +-z.
+ *  - Faces are numbered 0..5 = -x, +x, -y, +y, -z, +z.
+ *  - Every function returns an lbm_status; the library never aborts.  Work is
+ *    enqueued asynchronously on the stream given to lbm_init; device-side
+ *    error flags are read (and the stream synchronised) by lbm_sync,
+ *    lbm_reduce, lbm_macros and lbm_get_state.
+ *  - Pointer arguments marked "mem" are device pointers when mem ==
+ *    LBM_MEM_DEVICE and host pointers when mem == LBM_MEM_HOST; the caller owns
+ *    them.  The library owns the population and scratch buffers it allocates
+ *    in lbm_init and frees in lbm_destroy.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = -1,        /* invalid argument or unsupported parameter combination */
+  LBM_ERR_CUDA = -2,       /* a CUDA runtime call failed (allocation, launch, copy) */
+  LBM_ERR_NONFINITE = -3,  /* a population became NaN/Inf */
+  LBM_ERR_PSI_DOMAIN = -4, /* 2 (p_EOS - rho/3) / G < 0 somewhere: psi of Eq. 7 undefined */
+  LBM_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up */
+  LBM_ERR_STATE = -6       /* call out of order (e.g. step before any state was set) */
+} lbm_status;
+
+typedef enum { LBM_FACE_PERIODIC = 0, LBM_FACE_WALL = 1, LBM_FACE_OPEN = 2 } lbm_face_kind;
+typedef enum { LBM_STORE_F32 = 0, LBM_STORE_F16_SHIFTED = 1, LBM_STORE_BF16_SHIFTED = 2 } lbm_storage;
+typedef enum { LBM_MEM_DEVICE = 0, LBM_MEM_HOST = 1 } lbm_mem;
+typedef enum { LBM_SCHED_FUSED = 0, LBM_SCHED_PHASES = 1 } lbm_schedule;
+
+/* Problem statement.  Physical parameters follow the paper's notation. */
+typedef struct lbm_params {
+  int nx, ny, nz;                /* lattice size; >= 3 along an axis with non-periodic faces */
+  double a, b, R, omega;         /* Peng-Robinson EOS, Sec. 4 Eqs. 37-38 (T_c follows from a, b, R) */
+  double G;                      /* interaction strength of Eq. 6 (the paper uses -1) */
+  double s_e, s_v, s_q, s_pi;    /* D3Q19 relaxation rates of Lambda-hat, Eq. 10 */
+  double cv;                     /* specific heat at constant volume, Eq. 12 */
+  double wbar;                   /* D3Q7 weight parameter of Eq. 14, 0 < wbar < 1, c_s^2 = wbar/3 */
+  double lambda_l, lambda_v;     /* thermal conductivity of liquid / vapor; lambda is interpolated
+                                    linearly in the liquid fraction (rho-rho_v)/(rho_l-rho_v), and
+                                    varsigma_{1,2,3} = 1 / (lambda / c_s^2 + 1/2) (Sec. 2.2) */
+  double rho_l, rho_v;           /* coexistence densities used by that interpolation */
+  int vartheta;                  /* correction switch of Eq. 13; only 0 (the paper's choice) */
+  int meq_printed;               /* 0: m^eq = M-hat f^eq; 1: rows 16-18 exactly as printed in Eq. 9 */
+  int wall_ueq_zero;             /* 1: u^eq = 0 and u = 0 at bounce-back wall nodes (Sec. 3.1) */
+  int eos_kind;                  /* 0: Peng-Robinson; 1: ideal gas p = eos_c0 * rho (verification) */
+  double eos_c0;
+  int face_kind[6];              /* lbm_face_kind per face; periodic faces come in pairs; a wall face
+                                    may not share an edge with an open face */
+  double face_T[6];              /* Dirichlet temperature of every non-periodic face (Sec. 3.1) */
+  double face_rho[6];            /* prescribed density of an open face (Sec. 3.3) */
+  double face_theta_deg[6];      /* contact angle of a wall face, Eq. 36 */
+  int storage;                   /* lbm_storage */
+  int schedule;                  /* lbm_schedule: one fused launch per step, or one launch per phase */
+} lbm_params;
+
+/* Creates a context on the current CUDA device and, if rho0 and T0 are not
+ * NULL, initialises f = f^eq(rho0, u = 0) and g_i = w_i T0 (Sec. 4.2).
+ * rho0, T0: N floats each (mem).  stream: a cudaStream_t (NULL = legacy default).
+ * On error *out is NULL. */
+int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float* T0, int mem, void* stream);
+
+/* Replaces the populations: f 19*N floats, g 7*N floats, SoA layout above (mem). */
+int lbm_set_state(lbm_ctx* ctx, const float* f, const float* g, int mem);
+
+/* Copies the current populations out (mem); synchronises the stream. */
+int lbm_get_state(lbm_ctx* ctx, float* f, float* g, int mem);
+
+/* Per-node Dirichlet temperature of non-periodic face `face` (Sec. 3.1): an
+ * array over the face's two tangential coordinates, lower axis fastest
+ * (z faces: nx*ny, x faces: ny*nz, y faces: nx*nz floats) (mem).  Edge and
+ * corner nodes take the mean of the faces they lie on. */
+int lbm_set_face_T(lbm_ctx* ctx, int face, const float* T_face, int mem);
+
+/* Advances n >= 0 time steps; asynchronous on the context stream. */
+int lbm_step(lbm_ctx* ctx, int n);
+
+/* Macroscopic fields of the current state: rho = sum f (Eq. 3), the real
+ * velocity u = (sum c f + F/2) / rho (Eq. 5; 0 at wall nodes) and T = sum g.
+ * Each output N floats (mem) or NULL to skip.  Synchronises the stream. */
+int lbm_macros(lbm_ctx* ctx, float* rho, float* ux, float* uy, float* uz, float* T, int mem);
+
+/* FP64 reductions of the current state, host output:
+ * out[0] = sum rho (mass), out[1] = sum rho c_v T, out[2] = droplet volume
+ * sum clamp((rho - rho_v)/(rho_l - rho_v), 0, 1) (Sec. 4.2 d^2 law),
+ * out[3] = number of cells whose populations are not finite.  Synchronises. */
+int lbm_reduce(lbm_ctx* ctx, double out[4]);
+
+/* Synchronises the stream and returns the first error any kernel flagged. */
+int lbm_sync(lbm_ctx* ctx);
+
+/* Integer maps used by the kernels, host outputs (any may be NULL):
+ * map19[i*N + c] = destination slot i'*N + c' of population i leaving c
+ * (bounce-back gives the opposite direction at c), -1 if it leaves through an
+ * open face; map7 likewise for D3Q7 (-1 beyond any non-periodic face);
+ * node_class[c] has bit f set when c lies on non-periodic face f.
+ * Computed on the device by the same index code the step kernels use. */
+int lbm_stream_map(lbm_ctx* ctx, int32_t* map19, int32_t* map7, uint8_t* node_class);
+
+/* Frees everything the context owns; NULL is ignored. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Static description of a status code. */
+const char* lbm_status_string(int status);
+
+/* Host helpers of Sec. 4 (Eq. 38 and the Maxwell construction); no device work. */
+double lbm_Tc(const lbm_params* p);
+int lbm_maxwell(const lbm_params* p, double T, double* rho_v, double* rho_l, double* p_sat);
+
+/* Number of kernel launches one lbm_step(ctx, 1) enqueues. */
+int lbm_launches_per_step(const lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,606 @@
+// C ABI of liblbm (declared in include/lbm.h): context management, launches
+// of the step kernels on the caller's stream, FP64 reductions, host helpers.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "lbm.h"
+#include "lbm_fused.cuh"
+#include "lbm_phases.cuh"
+
+using namespace lbm;
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void k_init(Params P, const float* __restrict__ rho0, const float* __restrict__ T0, float* f, float* g) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x) {
+    float fe[19];
+    feq19(rho0[c], 0.f, 0.f, 0.f, fe);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) f[i * P.N + c] = fe[i];
+    const float T = T0[c];
+    g[c] = (1.f - P.wbar) * T;
+#pragma unroll
+    for (int i = 1; i < 7; ++i) g[i * P.N + c] = P.wbar * (1.f / 6.f) * T;
+  }
+}
+
+__global__ void k_phaseA(Params P, const float* __restrict__ f, const float* __restrict__ g, Aux X, float* Tout,
+                         int* err) {
+  int e = 0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x)
+    phaseA(P, c, f, g, X, Tout, e);
+  if (e) atomicOr(err, e);
+}
+
+__global__ void k_phaseB(Params P, Aux X) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x)
+    phaseB(P, c, X);
+}
+
+__global__ void k_phaseC(Params P, const float* __restrict__ fA, const float* __restrict__ gA, float* fB, float* gB,
+                         Aux X) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x)
+    phaseC(P, c, fA, gA, fB, gB, X);
+}
+
+// grid: (x over boundary candidates of a plane, y over planes)
+__global__ void k_phaseD(Params P, float* fB, float* gB, Aux X) {
+  const int z = blockIdx.y;
+  const int cnt = boundary_count(P, z);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+    int x, y;
+    boundary_xy(P, z, k, x, y);
+    const int m = node_faces(P, x, y, z);
+    if (m) phaseD(P, cell_of(P, x, y, z), x, y, z, m, fB, gB, X);
+  }
+}
+
+// FP64 block reduction: mass, sum rho cv T, droplet volume, non-finite count.
+__global__ void k_reduce(Params P, const float* __restrict__ f, const float* __restrict__ g, double* partial) {
+  double a[4] = {0, 0, 0, 0};
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x) {
+    float fl[19], gl[7];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) fl[i] = __ldg(f + i * P.N + c);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) gl[i] = __ldg(g + i * P.N + c);
+    float rho, jx, jy, jz;
+    sum19(fl, rho, jx, jy, jz);
+    const float T = sum7(gl);
+    bool fin = isfinite(rho) && isfinite(T);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) fin = fin && isfinite(fl[i]);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) fin = fin && isfinite(gl[i]);
+    if (fin) {
+      a[0] += (double)rho;
+      a[1] += (double)rho * (double)P.cv * (double)T;
+      double phi = ((double)rho - (double)P.rho_v) * (double)P.inv_drho;
+      a[2] += phi < 0 ? 0.0 : (phi > 1 ? 1.0 : phi);
+    } else {
+      a[3] += 1.0;
+    }
+  }
+  __shared__ double sh[4][kThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double v = a[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[k][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double v = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[threadIdx.x][w];
+    partial[blockIdx.x * 4 + threadIdx.x] = v;
+  }
+}
+
+// Sums the per-block partials in a fixed order (deterministic result).
+__global__ void k_reduce_final(const double* partial, int nblocks, double* out) {
+  if (threadIdx.x < 4) {
+    double v = 0;
+    for (int b = 0; b < nblocks; ++b) v += partial[b * 4 + threadIdx.x];
+    out[threadIdx.x] = v;
+  }
+}
+
+__global__ void k_maps(Params P, int* map19, int* map7, unsigned char* cls) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(P, c, x, y, z);
+    if (cls) cls[c] = (unsigned char)node_faces(P, x, y, z);
+    if (map19)
+      for (int i = 0; i < 19; ++i) map19[i * P.N + c] = (int)dest19(P, x, y, z, i);
+    if (map7)
+      for (int i = 0; i < 7; ++i) {
+        const int d = dest7_cell(P, x, y, z, i);
+        map7[i * P.N + c] = d < 0 ? -1 : (int)(i * P.N + d);
+      }
+  }
+}
+
+__global__ void k_fill(float* p, long long n, float v) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    p[k] = v;
+}
+
+__global__ void k_sumT(Params P, const float* __restrict__ g, float* T) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x) {
+    float gl[7];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) gl[i] = g[i * P.N + c];
+    T[c] = sum7(gl);
+  }
+}
+
+}  // namespace
+
+struct lbm_ctx {
+  lbm_params hp;
+  Params P;
+  cudaStream_t stream;
+  int device;
+  long long N;
+  float* f[2];
+  float* g[2];
+  int cur;
+  float* aux;
+  Aux X;
+  float* tface[6];
+  long long tface_n[6];
+  int* err_d;
+  int* err_h;
+  double* partial;
+  double* red_out;
+  double* red_h;
+  int red_blocks;
+  int grid;
+  bool has_state;
+  FusedPlan plan;
+};
+
+namespace {
+
+long long face_len(const lbm_params& p, int face) {
+  const int a = face / 2;
+  const int n[3] = {p.nx, p.ny, p.nz};
+  long long L = 1;
+  for (int b = 0; b < 3; ++b)
+    if (b != a) L *= n[b];
+  return L;
+}
+
+int check_params(const lbm_params* p) {
+  if (!p) return LBM_ERR_ARG;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return LBM_ERR_ARG;
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  if (N > (1LL << 31) - 1) return LBM_ERR_ARG;
+  if (p->vartheta != 0) return LBM_ERR_ARG;
+  if (p->storage != LBM_STORE_F32) return LBM_ERR_ARG;
+  if (p->schedule != LBM_SCHED_FUSED && p->schedule != LBM_SCHED_PHASES) return LBM_ERR_ARG;
+  if (p->eos_kind != 0 && p->eos_kind != 1) return LBM_ERR_ARG;
+  if (!(p->cv > 0) || !(p->wbar > 0 && p->wbar < 1) || !(p->lambda_l > 0) || !(p->lambda_v > 0)) return LBM_ERR_ARG;
+  if (p->lambda_l != p->lambda_v && !(p->rho_l > p->rho_v)) return LBM_ERR_ARG;
+  if (p->G == 0 || !std::isfinite(p->a) || !std::isfinite(p->b)) return LBM_ERR_ARG;
+  if (p->eos_kind == 0 && !(p->a > 0 && p->b > 0 && p->R > 0)) return LBM_ERR_ARG;
+  const int n[3] = {p->nx, p->ny, p->nz};
+  for (int a = 0; a < 3; ++a) {
+    const int k0 = p->face_kind[2 * a], k1 = p->face_kind[2 * a + 1];
+    if (k0 < 0 || k0 > 2 || k1 < 0 || k1 > 2) return LBM_ERR_ARG;
+    if ((k0 == LBM_FACE_PERIODIC) != (k1 == LBM_FACE_PERIODIC)) return LBM_ERR_ARG;
+    if (k0 != LBM_FACE_PERIODIC && n[a] < 3) return LBM_ERR_ARG;
+  }
+  for (int f1 = 0; f1 < 6; ++f1)
+    for (int f2 = 0; f2 < 6; ++f2)
+      if (f1 / 2 != f2 / 2 && p->face_kind[f1] == LBM_FACE_WALL && p->face_kind[f2] == LBM_FACE_OPEN)
+        return LBM_ERR_ARG;
+  for (int f = 0; f < 6; ++f)
+    if (p->face_kind[f] == LBM_FACE_OPEN && !(p->face_rho[f] > 0)) return LBM_ERR_ARG;
+  return LBM_OK;
+}
+
+Params make_device_params(const lbm_params& p) {
+  Params P;
+  std::memset(&P, 0, sizeof(P));
+  P.nx = p.nx;
+  P.ny = p.ny;
+  P.nz = p.nz;
+  P.N = (long long)p.nx * p.ny * p.nz;
+  fdiv_init((unsigned)p.nx, P.dnx_mul, P.dnx_shr);
+  fdiv_init((unsigned)p.ny, P.dny_mul, P.dny_shr);
+  P.meq_printed = p.meq_printed;
+  P.wall_ueq_zero = p.wall_ueq_zero;
+  P.eos_kind = p.eos_kind;
+  P.a = (float)p.a;
+  P.b = (float)p.b;
+  P.R = (float)p.R;
+  P.kappa = (float)(0.37464 + 1.54226 * p.omega - 0.26992 * p.omega * p.omega);
+  P.inv_Tc = p.eos_kind == 0 ? (float)(1.0 / lbm_Tc(&p)) : 1.f;
+  P.G = (float)p.G;
+  P.inv_G = (float)(1.0 / p.G);
+  P.eos_c0 = (float)p.eos_c0;
+  P.s_e = (float)p.s_e;
+  P.s_v = (float)p.s_v;
+  P.s_q = (float)p.s_q;
+  P.s_pi = (float)p.s_pi;
+  P.cv = (float)p.cv;
+  P.inv_cv = (float)(1.0 / p.cv);
+  P.wbar = (float)p.wbar;
+  P.inv_cs2t = (float)(3.0 / p.wbar);
+  P.lambda_l = (float)p.lambda_l;
+  P.lambda_v = (float)p.lambda_v;
+  P.rho_l = (float)p.rho_l;
+  P.rho_v = (float)p.rho_v;
+  P.inv_drho = (p.rho_l > p.rho_v) ? (float)(1.0 / (p.rho_l - p.rho_v)) : 0.f;
+  P.lam_uniform = p.lambda_l == p.lambda_v;
+  P.any_nonperiodic = 0;
+  for (int f = 0; f < 6; ++f) {
+    P.face_kind[f] = p.face_kind[f];
+    P.face_rho[f] = (float)p.face_rho[f];
+    const double th = p.face_theta_deg[f] * M_PI / 180.0;
+    const double tn = std::tan(M_PI / 2.0 - th);
+    P.tan_wet[f] = (p.face_theta_deg[f] == 90.0) ? 0.f : (float)tn;
+    if (p.face_kind[f] != LBM_FACE_PERIODIC) P.any_nonperiodic = 1;
+  }
+  return P;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; }
+
+int grid_for(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  if (b > 152LL * 64) b = 152LL * 64;
+  return (int)(b < 1 ? 1 : b);
+}
+
+#define LBM_TRY(expr)                           \
+  do {                                          \
+    cudaError_t _e = (expr);                    \
+    if (_e != cudaSuccess) return LBM_ERR_CUDA; \
+  } while (0)
+
+int copy_in(float* dst, const float* src, long long n, int mem, cudaStream_t s) {
+  LBM_TRY(cudaMemcpyAsync(dst, src, sizeof(float) * n, mem == LBM_MEM_HOST ? cudaMemcpyHostToDevice
+                                                                           : cudaMemcpyDeviceToDevice, s));
+  return LBM_OK;
+}
+
+int copy_out(float* dst, const float* src, long long n, int mem, cudaStream_t s) {
+  LBM_TRY(cudaMemcpyAsync(dst, src, sizeof(float) * n, mem == LBM_MEM_HOST ? cudaMemcpyDeviceToHost
+                                                                           : cudaMemcpyDeviceToDevice, s));
+  return LBM_OK;
+}
+
+int read_flags(lbm_ctx* c) {
+  LBM_TRY(cudaMemcpyAsync(c->err_h, c->err_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  LBM_TRY(cudaStreamSynchronize(c->stream));
+  const int e = *c->err_h;
+  if (e & ERRF_TIMEOUT) return LBM_ERR_TIMEOUT;
+  if (e & ERRF_NONFINITE) return LBM_ERR_NONFINITE;
+  if (e & ERRF_PSI) return LBM_ERR_PSI_DOMAIN;
+  return LBM_OK;
+}
+
+// Phases A and B on the current state (macros of time t); returns launch status.
+int run_macros(lbm_ctx* c, float* Tout) {
+  const float* f = c->f[c->cur];
+  const float* g = c->g[c->cur];
+  k_phaseA<<<c->grid, kThreads, 0, c->stream>>>(c->P, f, g, c->X, Tout, c->err_d);
+  k_phaseB<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->X);
+  return cuda_status(cudaGetLastError());
+}
+
+int step_phases(lbm_ctx* c) {
+  const int a = c->cur, b = 1 - c->cur;
+  k_phaseA<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->f[a], c->g[a], c->X, nullptr, c->err_d);
+  k_phaseB<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->X);
+  k_phaseC<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->f[a], c->g[a], c->f[b], c->g[b], c->X);
+  if (c->P.any_nonperiodic) {
+    const int plane = c->P.nx * c->P.ny;
+    dim3 gd((plane + kThreads - 1) / kThreads, c->P.nz);
+    k_phaseD<<<gd, kThreads, 0, c->stream>>>(c->P, c->f[b], c->g[b], c->X);
+  }
+  c->cur = b;
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_status_string(int s) {
+  switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_ARG: return "invalid argument";
+    case LBM_ERR_CUDA: return "CUDA runtime error";
+    case LBM_ERR_NONFINITE: return "non-finite population";
+    case LBM_ERR_PSI_DOMAIN: return "psi undefined: 2(p_EOS - rho/3)/G < 0";
+    case LBM_ERR_TIMEOUT: return "bounded device wait gave up";
+    case LBM_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+double lbm_Tc(const lbm_params* p) { return 0.0778 * p->a / (0.45724 * p->b * p->R); }
+
+// Maxwell equal-area construction for the PR EOS (Sec. 4.2): bisection on
+// p_sat between the spinodal pressures, the area by composite Simpson rule.
+int lbm_maxwell(const lbm_params* p, double T, double* rho_v, double* rho_l, double* p_sat) {
+  if (!p || p->eos_kind != 0) return LBM_ERR_ARG;
+  const double Tc = lbm_Tc(p);
+  if (!(T > 0 && T < Tc)) return LBM_ERR_ARG;
+  const double k = 0.37464 + 1.54226 * p->omega - 0.26992 * p->omega * p->omega;
+  const double s = 1.0 + k * (1.0 - std::sqrt(T / Tc));
+  const double axi = p->a * s * s, b = p->b, R = p->R;
+  auto pr = [&](double r) { return r * R * T / (1.0 - b * r) - axi * r * r / (1.0 + 2.0 * b * r - b * b * r * r); };
+  // spinodals by a scan of p on (0, 1/b)
+  const int n = 100000;
+  const double h = (1.0 / b) / n;
+  double rmax = -1, rmin = -1;
+  for (int i = 1; i < n - 1; ++i) {
+    const double r = i * h;
+    const double d0 = pr(r + h) - pr(r), d1 = pr(r + 2 * h) - pr(r + h);
+    if (rmax < 0 && d0 > 0 && d1 <= 0) rmax = r + h;
+    if (rmax > 0 && d0 < 0 && d1 >= 0) {
+      rmin = r + h;
+      break;
+    }
+  }
+  if (rmax < 0 || rmin < 0) return LBM_ERR_ARG;
+  auto root = [&](double ps, double lo, double hi) {
+    const bool inc = pr(hi) > pr(lo);
+    for (int it = 0; it < 120; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if ((pr(mid) < ps) == inc)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    return 0.5 * (lo + hi);
+  };
+  double lo = std::fmax(pr(rmin), 1e-14), hi = pr(rmax), rv = 0, rl = 0, ps = 0;
+  for (int it = 0; it < 100; ++it) {
+    ps = 0.5 * (lo + hi);
+    rv = root(ps, 1e-12, rmax);
+    rl = root(ps, rmin, (1.0 / b) * (1 - 1e-9));
+    // area of (p - ps)/rho^2 from rv to rl, Simpson with 4000 panels
+    const int m = 4000;
+    const double hh = (rl - rv) / m;
+    double acc = 0;
+    for (int j = 0; j <= m; ++j) {
+      const double r = rv + j * hh;
+      const double w = (j == 0 || j == m) ? 1 : ((j & 1) ? 4 : 2);
+      acc += w * (pr(r) - ps) / (r * r);
+    }
+    const double area = acc * hh / 3.0;
+    if (area > 0)
+      lo = ps;
+    else
+      hi = ps;
+  }
+  if (rho_v) *rho_v = rv;
+  if (rho_l) *rho_l = rl;
+  if (p_sat) *p_sat = ps;
+  return LBM_OK;
+}
+
+int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float* T0, int mem, void* stream) {
+  if (!out) return LBM_ERR_ARG;
+  *out = nullptr;
+  int st = check_params(p);
+  if (st) return st;
+  if ((rho0 == nullptr) != (T0 == nullptr)) return LBM_ERR_ARG;
+  lbm_ctx* c = new (std::nothrow) lbm_ctx;
+  if (!c) return LBM_ERR_ARG;
+  std::memset(c, 0, sizeof(*c));
+  c->hp = *p;
+  c->P = make_device_params(*p);
+  c->stream = (cudaStream_t)stream;
+  c->N = c->P.N;
+  c->grid = grid_for(c->N);
+  cudaGetDevice(&c->device);
+  const long long N = c->N;
+  bool ok = true;
+  for (int k = 0; k < 2; ++k) {
+    ok = ok && cudaMalloc(&c->f[k], sizeof(float) * 19 * N) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->g[k], sizeof(float) * 7 * N) == cudaSuccess;
+  }
+  ok = ok && cudaMalloc(&c->aux, sizeof(float) * 11 * N) == cudaSuccess;
+  ok = ok && cudaMalloc(&c->err_d, sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&c->err_h, sizeof(int)) == cudaSuccess;
+  c->red_blocks = grid_for(N) < 1024 ? grid_for(N) : 1024;
+  ok = ok && cudaMalloc(&c->partial, sizeof(double) * 4 * c->red_blocks) == cudaSuccess;
+  ok = ok && cudaMalloc(&c->red_out, sizeof(double) * 4) == cudaSuccess;
+  ok = ok && cudaMallocHost(&c->red_h, sizeof(double) * 4) == cudaSuccess;
+  for (int f = 0; f < 6 && ok; ++f) {
+    if (p->face_kind[f] == LBM_FACE_PERIODIC) continue;
+    c->tface_n[f] = face_len(*p, f);
+    ok = cudaMalloc(&c->tface[f], sizeof(float) * c->tface_n[f]) == cudaSuccess;
+    if (ok) {
+      k_fill<<<grid_for(c->tface_n[f]), kThreads, 0, c->stream>>>(c->tface[f], c->tface_n[f], (float)p->face_T[f]);
+      c->P.Tface[f] = c->tface[f];
+    }
+  }
+  if (!ok) {
+    lbm_destroy(c);
+    return LBM_ERR_CUDA;
+  }
+  float* a = c->aux;
+  c->X = Aux{a, a + N, a + 2 * N, a + 3 * N, a + 4 * N, a + 5 * N, a + 6 * N, a + 7 * N, a + 8 * N, a + 9 * N, a + 10 * N};
+  if (cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream) != cudaSuccess) {
+    lbm_destroy(c);
+    return LBM_ERR_CUDA;
+  }
+  st = fused_plan(c->P, &c->plan);
+  if (st == LBM_OK && p->schedule == LBM_SCHED_FUSED) st = fused_alloc(&c->plan, c->P, c->stream);
+  if (st != LBM_OK) st = st == -1 ? LBM_ERR_ARG : LBM_ERR_CUDA;
+  if (st != LBM_OK) {
+    lbm_destroy(c);
+    return st;
+  }
+  if (rho0) {
+    float *r = nullptr, *t = nullptr;
+    if (mem == LBM_MEM_HOST) {
+      r = c->aux;  // stage through the scratch area
+      t = c->aux + N;
+      if (copy_in(r, rho0, N, mem, c->stream) || copy_in(t, T0, N, mem, c->stream)) {
+        lbm_destroy(c);
+        return LBM_ERR_CUDA;
+      }
+    } else {
+      r = (float*)rho0;
+      t = (float*)T0;
+    }
+    k_init<<<c->grid, kThreads, 0, c->stream>>>(c->P, r, t, c->f[0], c->g[0]);
+    if (cudaGetLastError() != cudaSuccess) {
+      lbm_destroy(c);
+      return LBM_ERR_CUDA;
+    }
+    c->has_state = true;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+int lbm_set_state(lbm_ctx* c, const float* f, const float* g, int mem) {
+  if (!c || !f || !g) return LBM_ERR_ARG;
+  int st = copy_in(c->f[c->cur], f, 19 * c->N, mem, c->stream);
+  if (!st) st = copy_in(c->g[c->cur], g, 7 * c->N, mem, c->stream);
+  if (!st && mem == LBM_MEM_HOST) st = cuda_status(cudaStreamSynchronize(c->stream));
+  if (!st && fused_reset(&c->plan, c->P, c->stream)) st = LBM_ERR_CUDA;
+  if (!st) st = cuda_status(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream));
+  if (!st) c->has_state = true;
+  return st;
+}
+
+int lbm_get_state(lbm_ctx* c, float* f, float* g, int mem) {
+  if (!c) return LBM_ERR_ARG;
+  if (!c->has_state) return LBM_ERR_STATE;
+  int st = LBM_OK;
+  if (f) st = copy_out(f, c->f[c->cur], 19 * c->N, mem, c->stream);
+  if (!st && g) st = copy_out(g, c->g[c->cur], 7 * c->N, mem, c->stream);
+  if (st) return st;
+  return read_flags(c);
+}
+
+int lbm_set_face_T(lbm_ctx* c, int face, const float* T_face, int mem) {
+  if (!c || face < 0 || face > 5 || !T_face) return LBM_ERR_ARG;
+  if (!c->tface[face]) return LBM_ERR_ARG;
+  int st = copy_in(c->tface[face], T_face, c->tface_n[face], mem, c->stream);
+  if (!st && mem == LBM_MEM_HOST) st = cuda_status(cudaStreamSynchronize(c->stream));
+  return st;
+}
+
+int lbm_step(lbm_ctx* c, int n) {
+  if (!c || n < 0) return LBM_ERR_ARG;
+  if (!c->has_state) return LBM_ERR_STATE;
+  for (int s = 0; s < n; ++s) {
+    int st;
+    if (c->hp.schedule == LBM_SCHED_FUSED) {
+      st = fused_step(&c->plan, c->P, c->f[c->cur], c->g[c->cur], c->f[1 - c->cur], c->g[1 - c->cur], c->X,
+                      c->err_d, c->stream);
+      c->cur = 1 - c->cur;
+    } else {
+      st = step_phases(c);
+    }
+    if (st) return st;
+  }
+  return LBM_OK;
+}
+
+int lbm_launches_per_step(const lbm_ctx* c) {
+  if (!c) return 0;
+  if (c->hp.schedule == LBM_SCHED_FUSED) return fused_launches(&c->plan);
+  return c->P.any_nonperiodic ? 4 : 3;
+}
+
+int lbm_macros(lbm_ctx* c, float* rho, float* ux, float* uy, float* uz, float* T, int mem) {
+  if (!c) return LBM_ERR_ARG;
+  if (!c->has_state) return LBM_ERR_STATE;
+  // T is summed into the ux slot of the scratch first when requested, then copied
+  float* Tscratch = c->aux + 5 * c->N;  // Fx slot, rewritten by phase B below
+  if (T) {
+    k_sumT<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->g[c->cur], Tscratch);
+    int st = copy_out(T, Tscratch, c->N, mem, c->stream);
+    if (st) return st;
+  }
+  int st = run_macros(c, nullptr);
+  if (st) return st;
+  if (rho) st = copy_out(rho, c->X.rho, c->N, mem, c->stream);
+  if (!st && ux) st = copy_out(ux, c->X.ux, c->N, mem, c->stream);
+  if (!st && uy) st = copy_out(uy, c->X.uy, c->N, mem, c->stream);
+  if (!st && uz) st = copy_out(uz, c->X.uz, c->N, mem, c->stream);
+  if (st) return st;
+  return read_flags(c);
+}
+
+int lbm_reduce(lbm_ctx* c, double out[4]) {
+  if (!c || !out) return LBM_ERR_ARG;
+  if (!c->has_state) return LBM_ERR_STATE;
+  k_reduce<<<c->red_blocks, kThreads, 0, c->stream>>>(c->P, c->f[c->cur], c->g[c->cur], c->partial);
+  k_reduce_final<<<1, 32, 0, c->stream>>>(c->partial, c->red_blocks, c->red_out);
+  LBM_TRY(cudaGetLastError());
+  LBM_TRY(cudaMemcpyAsync(c->red_h, c->red_out, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream));
+  const int st = read_flags(c);
+  for (int k = 0; k < 4; ++k) out[k] = c->red_h[k];
+  return st;
+}
+
+int lbm_sync(lbm_ctx* c) {
+  if (!c) return LBM_ERR_ARG;
+  return read_flags(c);
+}
+
+int lbm_stream_map(lbm_ctx* c, int32_t* map19, int32_t* map7, uint8_t* node_class) {
+  if (!c) return LBM_ERR_ARG;
+  if (19 * c->N > (1LL << 31) - 1) return LBM_ERR_ARG;
+  const long long N = c->N;
+  int *m19 = nullptr, *m7 = nullptr;
+  unsigned char* cl = nullptr;
+  int st = LBM_OK;
+  if (map19 && cudaMalloc(&m19, sizeof(int) * 19 * N) != cudaSuccess) st = LBM_ERR_CUDA;
+  if (!st && map7 && cudaMalloc(&m7, sizeof(int) * 7 * N) != cudaSuccess) st = LBM_ERR_CUDA;
+  if (!st && node_class && cudaMalloc(&cl, N) != cudaSuccess) st = LBM_ERR_CUDA;
+  if (!st) {
+    k_maps<<<c->grid, kThreads, 0, c->stream>>>(c->P, m19, m7, cl);
+    st = cuda_status(cudaGetLastError());
+  }
+  if (!st && m19) st = cuda_status(cudaMemcpyAsync(map19, m19, sizeof(int) * 19 * N, cudaMemcpyDeviceToHost, c->stream));
+  if (!st && m7) st = cuda_status(cudaMemcpyAsync(map7, m7, sizeof(int) * 7 * N, cudaMemcpyDeviceToHost, c->stream));
+  if (!st && cl) st = cuda_status(cudaMemcpyAsync(node_class, cl, N, cudaMemcpyDeviceToHost, c->stream));
+  if (!st) st = cuda_status(cudaStreamSynchronize(c->stream));
+  cudaFree(m19);
+  cudaFree(m7);
+  cudaFree(cl);
+  return st;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(c->f[k]);
+    cudaFree(c->g[k]);
+  }
+  cudaFree(c->aux);
+  cudaFree(c->err_d);
+  cudaFreeHost(c->err_h);
+  cudaFree(c->partial);
+  cudaFree(c->red_out);
+  cudaFreeHost(c->red_h);
+  for (int f = 0; f < 6; ++f) cudaFree(c->tface[f]);
+  fused_free(&c->plan);
+  delete c;
+}
+
+}  // extern "C"

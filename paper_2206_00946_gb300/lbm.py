@@ -1,0 +1,214 @@
+"""Thin ctypes binding of liblbm.so (include/lbm.h): same function names,
+argument marshalling only.  Every step of the lattice update runs in the
+library's CUDA kernels; nothing here computes on the host.
+
+Device arrays are passed as torch CUDA tensors (their data_ptr()) or raw
+integer pointers; host arrays as numpy arrays.  The library must have been
+built (``python -m paper_2206_00946_gb300.build``); loading fails loudly if it
+is missing.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblbm.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_PSI_DOMAIN, ERR_TIMEOUT, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+FACE_PERIODIC, FACE_WALL, FACE_OPEN = 0, 1, 2
+STORE_F32, STORE_F16_SHIFTED, STORE_BF16_SHIFTED = 0, 1, 2
+MEM_DEVICE, MEM_HOST = 0, 1
+SCHED_FUSED, SCHED_PHASES = 0, 1
+
+_D = ct.c_double
+
+
+class lbm_params(ct.Structure):
+    _fields_ = [
+        ("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int),
+        ("a", _D), ("b", _D), ("R", _D), ("omega", _D), ("G", _D),
+        ("s_e", _D), ("s_v", _D), ("s_q", _D), ("s_pi", _D),
+        ("cv", _D), ("wbar", _D), ("lambda_l", _D), ("lambda_v", _D),
+        ("rho_l", _D), ("rho_v", _D),
+        ("vartheta", ct.c_int), ("meq_printed", ct.c_int), ("wall_ueq_zero", ct.c_int),
+        ("eos_kind", ct.c_int), ("eos_c0", _D),
+        ("face_kind", ct.c_int * 6), ("face_T", _D * 6), ("face_rho", _D * 6), ("face_theta_deg", _D * 6),
+        ("storage", ct.c_int), ("schedule", ct.c_int),
+    ]
+
+
+# every symbol declared in include/lbm.h
+EXPORTS = ["lbm_init", "lbm_set_state", "lbm_get_state", "lbm_set_face_T", "lbm_step", "lbm_macros",
+           "lbm_reduce", "lbm_sync", "lbm_stream_map", "lbm_destroy", "lbm_status_string", "lbm_Tc",
+           "lbm_maxwell", "lbm_launches_per_step"]
+
+_lib = None
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__(f"{where}: {lbm_status_string(status)} ({status})")
+
+
+def load(path: str = LIB_PATH):
+    """Loads liblbm.so; raises if the CUDA library was not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"liblbm.so not built at {path}; run python -m paper_2206_00946_gb300.build")
+    L = ct.CDLL(path)
+    vp, P = ct.c_void_p, ct.POINTER(lbm_params)
+    L.lbm_init.argtypes = [ct.POINTER(vp), P, vp, vp, ct.c_int, vp]
+    L.lbm_set_state.argtypes = [vp, vp, vp, ct.c_int]
+    L.lbm_get_state.argtypes = [vp, vp, vp, ct.c_int]
+    L.lbm_set_face_T.argtypes = [vp, ct.c_int, vp, ct.c_int]
+    L.lbm_step.argtypes = [vp, ct.c_int]
+    L.lbm_macros.argtypes = [vp, vp, vp, vp, vp, vp, ct.c_int]
+    L.lbm_reduce.argtypes = [vp, ct.POINTER(_D)]
+    L.lbm_sync.argtypes = [vp]
+    L.lbm_stream_map.argtypes = [vp, vp, vp, vp]
+    L.lbm_destroy.argtypes = [vp]
+    L.lbm_destroy.restype = None
+    L.lbm_status_string.argtypes = [ct.c_int]
+    L.lbm_status_string.restype = ct.c_char_p
+    L.lbm_Tc.argtypes = [P]
+    L.lbm_Tc.restype = _D
+    L.lbm_maxwell.argtypes = [P, _D, ct.POINTER(_D), ct.POINTER(_D), ct.POINTER(_D)]
+    L.lbm_launches_per_step.argtypes = [vp]
+    _lib = L
+    return L
+
+
+def make_params(d: dict) -> lbm_params:
+    p = lbm_params()
+    for name, _ in lbm_params._fields_:
+        if name not in d:
+            continue
+        v = d[name]
+        if name.startswith("face_"):
+            arr = getattr(p, name)
+            for k in range(6):
+                arr[k] = v[k]
+        else:
+            setattr(p, name, v)
+    return p
+
+
+def _ptr(x):
+    """Device/host pointer of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    raise TypeError(type(x))
+
+
+def _mem_of(*xs):
+    for x in xs:
+        if x is None:
+            continue
+        if isinstance(x, np.ndarray):
+            return MEM_HOST
+        if hasattr(x, "is_cuda"):
+            return MEM_DEVICE if x.is_cuda else MEM_HOST
+    return MEM_DEVICE
+
+
+def _check(st, where):
+    if st != OK:
+        raise LBMError(st, where)
+
+
+def lbm_status_string(st: int) -> str:
+    return load().lbm_status_string(int(st)).decode()
+
+
+def lbm_Tc(params: dict) -> float:
+    return load().lbm_Tc(ct.byref(make_params(params)))
+
+
+def lbm_maxwell(params: dict, T: float):
+    rv, rl, ps = _D(), _D(), _D()
+    _check(load().lbm_maxwell(ct.byref(make_params(params)), T, ct.byref(rv), ct.byref(rl), ct.byref(ps)),
+           "lbm_maxwell")
+    return rv.value, rl.value, ps.value
+
+
+class Lattice:
+    """Owns one lbm_ctx.  Methods mirror the C functions one to one."""
+
+    def __init__(self, params: dict, rho0=None, T0=None, stream: int | None = None):
+        L = load()
+        self.params = dict(params)
+        self._p = make_params(self.params)
+        self.N = self._p.nx * self._p.ny * self._p.nz
+        self._ctx = ct.c_void_p()
+        mem = _mem_of(rho0, T0)
+        self._keep = (rho0, T0)
+        st = L.lbm_init(ct.byref(self._ctx), ct.byref(self._p), _ptr(rho0), _ptr(T0), mem, stream)
+        _check(st, "lbm_init")
+
+    def close(self):
+        if self._ctx:
+            load().lbm_destroy(self._ctx)
+            self._ctx = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def lbm_set_state(self, f, g):
+        _check(load().lbm_set_state(self._ctx, _ptr(f), _ptr(g), _mem_of(f, g)), "lbm_set_state")
+
+    def lbm_get_state(self, f, g):
+        st = load().lbm_get_state(self._ctx, _ptr(f), _ptr(g), _mem_of(f, g))
+        return st
+
+    def lbm_set_face_T(self, face, T_face):
+        _check(load().lbm_set_face_T(self._ctx, int(face), _ptr(T_face), _mem_of(T_face)), "lbm_set_face_T")
+
+    def lbm_step(self, n=1):
+        _check(load().lbm_step(self._ctx, int(n)), "lbm_step")
+
+    def lbm_macros(self, rho=None, ux=None, uy=None, uz=None, T=None):
+        return load().lbm_macros(self._ctx, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(uz), _ptr(T),
+                                 _mem_of(rho, ux, uy, uz, T))
+
+    def lbm_reduce(self):
+        out = (_D * 4)()
+        st = load().lbm_reduce(self._ctx, out)
+        return st, [out[k] for k in range(4)]
+
+    def lbm_sync(self):
+        return load().lbm_sync(self._ctx)
+
+    def lbm_stream_map(self, map19=None, map7=None, node_class=None):
+        return load().lbm_stream_map(self._ctx, _ptr(map19), _ptr(map7), _ptr(node_class))
+
+    def lbm_launches_per_step(self):
+        return load().lbm_launches_per_step(self._ctx)
+
+    # numpy conveniences (host copies through the same C calls)
+    def state(self):
+        f = np.empty((19, self.N), dtype=np.float32)
+        g = np.empty((7, self.N), dtype=np.float32)
+        st = self.lbm_get_state(f, g)
+        return st, f, g
+
+    def macros(self):
+        out = {k: np.empty(self.N, dtype=np.float32) for k in ("rho", "ux", "uy", "uz", "T")}
+        st = self.lbm_macros(**out)
+        return st, out

@@ -150,8 +150,13 @@ def sessile(Tc, rho_v, rho_l, nx=256, ny=256, nz=128, R=30.0, W=5.0, dTw=0.1, Ts
 def random_populations(nx, ny, nz, rho_base, T_base, w19, w7, amp, seed):
     """Populations w_i * base * (1 + uniform(-amp, amp)), seeded; rho_base/T_base scalars or fields."""
     N = nx * ny * nz
-    rb = np.broadcast_to(np.asarray(rho_base, dtype=np.float64), (nz, ny, nx)).reshape(-1)
-    tb = np.broadcast_to(np.asarray(T_base, dtype=np.float64), (nz, ny, nx)).reshape(-1)
+    def field(v):
+        v = np.asarray(v, dtype=np.float64)
+        if v.size == N:
+            return v.reshape(-1)
+        return np.broadcast_to(v, (nz, ny, nx)).reshape(-1)
+
+    rb, tb = field(rho_base), field(T_base)
     rf = uniform(seed, 19 * N, stream=7).reshape(19, N)
     rg = uniform(seed, 7 * N, stream=8).reshape(7, N)
     f = np.asarray(w19)[:, None] * rb[None, :] * (1.0 + amp * (2.0 * rf - 1.0))

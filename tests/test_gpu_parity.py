@@ -1,0 +1,245 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (FP32 arithmetic against FP64):
+  - populations after one step: max relative error 1e-5, each population's error
+    taken relative to max(|oracle value|, w_i rho_v) for f and max(|oracle value|,
+    w_i T_s / 2) for g -- the floor is the smallest physical population scale of the
+    workloads; without it the constant-pressure boundary, which on random states can
+    produce populations near zero, would turn round-off into large ratios;
+  - rho and T after 1000 steps: max relative error 1e-3;
+  - streaming maps and node classes: bit-exact.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle, tables
+from paper_2206_00946_gb300 import lbm, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+T = tables()
+W7 = W.w7(0.75)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lbm.load()
+
+
+def f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def droplet_state(p, thermo, seed, amp=0.02, R=None):
+    """Populations around a tanh droplet with seeded noise (non-zero force and velocity everywhere)."""
+    nx, ny, nz = p["nx"], p["ny"], p["nz"]
+    x, y, z = W.grid(nx, ny, nz)
+    R = R if R is not None else 0.3 * min(nx, ny, nz) + 1.0
+    r = np.sqrt((x - 0.45 * nx) ** 2 + (y - 0.55 * ny) ** 2 + (z - 0.5 * nz) ** 2)
+    rho = W.tanh_profile(r - R, thermo["rho_v"], thermo["rho_l"], 3.0)
+    Tm = thermo["Ts"] * (1 + 0.01 * np.sin(0.3 * x + 0.2 * y + 0.1 * z))
+    f, g = W.random_populations(nx, ny, nz, rho.reshape(-1), Tm.reshape(-1), W.W19, W7, amp, seed)
+    return f32(f), f32(g)
+
+
+def relerr(a, b):
+    return float(np.max(np.abs(a.astype(np.float64) - b) / np.abs(b)))
+
+
+def pop_err(a, b, thermo):
+    """Max population error relative to max(|b|, floor_i) (see the module docstring)."""
+    q = a.shape[0]
+    floor = (W.W19 * thermo["rho_v"]) if q == 19 else (W7 * 0.5 * thermo["Ts"])
+    den = np.maximum(np.abs(b), floor[:, None])
+    return float(np.max(np.abs(a.astype(np.float64) - b) / den))
+
+
+def gpu_step(p, f, g, n=1, schedule=lbm.SCHED_FUSED, tface=None):
+    q = dict(p, schedule=schedule)
+    lat = lbm.Lattice(q)
+    lat.lbm_set_state(f, g)
+    if tface:
+        for face, arr in tface.items():
+            lat.lbm_set_face_T(face, f32(arr))
+    lat.lbm_step(n)
+    st, fo, go = lat.state()
+    lat.close()
+    return st, fo, go
+
+
+CASES = {
+    "periodic": dict(shape=(12, 10, 9), face_kind=[0] * 6),
+    "walls_z": dict(shape=(8, 9, 10), face_kind=[0, 0, 0, 0, 1, 1]),
+    "open_all": dict(shape=(9, 8, 10), face_kind=[2] * 6),
+    "wall_bottom_open_top": dict(shape=(10, 9, 8), face_kind=[0, 0, 0, 0, 1, 2]),
+    "walls_xy_theta": dict(shape=(7, 8, 9), face_kind=[1, 1, 1, 1, 0, 0], theta=[70, 110, 60, 120, 90, 90]),
+    "ragged_open_x": dict(shape=(13, 7, 11), face_kind=[2, 2, 0, 0, 0, 0]),
+    "column_1x1": dict(shape=(1, 1, 40), face_kind=[0, 0, 0, 0, 1, 1]),
+    "multi_tile_plane": dict(shape=(40, 30, 6), face_kind=[0, 0, 2, 2, 0, 0]),
+}
+
+
+def case_params(name, thermo):
+    c = CASES[name]
+    nx, ny, nz = c["shape"]
+    Ts = thermo["Ts"]
+    return W.base_params(nx, ny, nz, rho_l=thermo["rho_l"], rho_v=thermo["rho_v"], lambda_l=0.4, lambda_v=0.2,
+                         face_kind=c["face_kind"], face_T=[Ts * (1 + 0.01 * k) for k in range(6)],
+                         face_rho=[thermo["rho_v"] * (1 + 0.02 * k) for k in range(6)],
+                         face_theta_deg=c.get("theta", [90] * 6))
+
+
+@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_PHASES])
+@pytest.mark.parametrize("name", list(CASES))
+def test_one_step_populations_match_oracle(name, schedule, thermo):
+    p = case_params(name, thermo)
+    f, g = droplet_state(p, thermo, seed=11)
+    o = Oracle(p)
+    st_o, fo, go = o.step(f.astype(np.float64), g.astype(np.float64))
+    assert st_o == 0
+    st, fg, gg = gpu_step(p, f, g, 1, schedule)
+    assert st == lbm.OK
+    assert pop_err(fg, fo, thermo) < 1e-5
+    assert pop_err(gg, go, thermo) < 1e-5
+
+
+@pytest.mark.parametrize("name", ["walls_z", "open_all", "wall_bottom_open_top", "periodic"])
+def test_fused_and_phase_schedules_are_bit_identical(name, thermo):
+    p = case_params(name, thermo)
+    f, g = droplet_state(p, thermo, seed=12)
+    _, f1, g1 = gpu_step(p, f, g, 5, lbm.SCHED_FUSED)
+    _, f2, g2 = gpu_step(p, f, g, 5, lbm.SCHED_PHASES)
+    np.testing.assert_array_equal(f1, f2)
+    np.testing.assert_array_equal(g1, g2)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_stream_maps_and_node_classes_bit_exact(name, thermo):
+    p = case_params(name, thermo)
+    o = Oracle(p)
+    lat = lbm.Lattice(p)
+    N = lat.N
+    m19 = np.empty(19 * N, np.int32)
+    m7 = np.empty(7 * N, np.int32)
+    cls = np.empty(N, np.uint8)
+    assert lat.lbm_stream_map(m19, m7, cls) == lbm.OK
+    lat.close()
+    np.testing.assert_array_equal(m19, o.stream_map19())
+    np.testing.assert_array_equal(m7, o.stream_map7())
+    np.testing.assert_array_equal(cls, o.node_class())
+
+
+def test_per_node_face_temperature_field(thermo):
+    p = case_params("wall_bottom_open_top", thermo)
+    f, g = droplet_state(p, thermo, seed=13)
+    tz = thermo["Ts"] * (1.05 + 0.01 * W.uniform(3, p["nx"] * p["ny"]).reshape(p["ny"], p["nx"]))
+    o = Oracle(p)
+    o.set_face_T([None, None, None, None, tz, None])
+    _, fo, go = o.step(f.astype(np.float64), g.astype(np.float64))
+    st, fg, gg = gpu_step(p, f, g, 1, lbm.SCHED_FUSED, tface={4: tz})
+    assert st == 0 and pop_err(gg, go, thermo) < 1e-5 and pop_err(fg, fo, thermo) < 1e-5
+
+
+def test_macros_and_reductions_match_oracle(thermo):
+    p = case_params("open_all", thermo)
+    f, g = droplet_state(p, thermo, seed=14)
+    lat = lbm.Lattice(p)
+    lat.lbm_set_state(f, g)
+    st, m = lat.macros()
+    assert st == 0
+    st2, red = lat.lbm_reduce()
+    lat.close()
+    o = Oracle(p)
+    _, mo = o.macros(f.astype(np.float64), g.astype(np.float64))
+    assert relerr(m["rho"], mo["rho"]) < 1e-6 and relerr(m["T"], mo["T"]) < 1e-6
+    for k in ("ux", "uy", "uz"):
+        assert np.max(np.abs(m[k] - mo[k])) < 1e-6 * max(1e-3, np.abs(mo[k]).max())
+    assert st2 == 0
+    rho = mo["rho"]
+    assert abs(red[0] - rho.sum()) < 1e-6 * rho.sum()
+    assert abs(red[1] - (rho * p["cv"] * mo["T"]).sum()) < 1e-6 * (rho * p["cv"] * mo["T"]).sum()
+    vol = np.clip((rho - p["rho_v"]) / (p["rho_l"] - p["rho_v"]), 0, 1).sum()
+    assert abs(red[2] - vol) < 1e-5 * max(vol, 1.0)
+    assert red[3] == 0
+
+
+_SLAB = {}
+
+
+def _slab_oracle(thermo):
+    if not _SLAB:
+        p, rho0, T0 = W.slab(thermo["Tc"], thermo["rho_v"], thermo["rho_l"], nx=16, ny=16, nz=64)
+        rho0 = W.perturb(rho0, 1e-3, seed=5)
+        o = Oracle(p)
+        f0, g0 = o.init_state(rho0, T0)
+        f0, g0 = f32(f0), f32(g0)
+        st, fo, go = o.run(f0.astype(np.float64), g0.astype(np.float64), 1000)
+        assert st == 0
+        _SLAB.update(p=p, f0=f0, g0=g0, fo=fo, go=go)
+    return _SLAB
+
+
+@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_PHASES])
+def test_slab_1000_steps_rho_T_match_oracle(schedule, thermo):
+    """16x16x64 flat slab between bounce-back walls (bottom T_s + 0.02 T_c, top T_s), W = 2."""
+    s = _slab_oracle(thermo)
+    p, f0, g0, fo, go = s["p"], s["f0"], s["g0"], s["fo"], s["go"]
+    _, fg, gg = gpu_step(p, f0, g0, 1000, schedule)
+    assert relerr(fg.sum(0), fo.sum(0)) < 1e-3
+    assert relerr(gg.sum(0), go.sum(0)) < 1e-3
+
+
+def test_open_droplet_1000_steps_rho_T_match_oracle(thermo):
+    """Evaporating droplet with constant-pressure faces on all six sides (20^3, R = 5)."""
+    p, rho0, T0 = W.droplet(thermo["Tc"], thermo["rho_v"], thermo["rho_l"], n=20, R=5.0, W=3.0, seed=2206)
+    o = Oracle(p)
+    f0, g0 = o.init_state(rho0, T0)
+    f0, g0 = f32(f0), f32(g0)
+    st, fo, go = o.run(f0.astype(np.float64), g0.astype(np.float64), 1000)
+    assert st == 0
+    _, fg, gg = gpu_step(p, f0, g0, 1000)
+    assert relerr(fg.sum(0), fo.sum(0)) < 1e-3
+    assert relerr(gg.sum(0), go.sum(0)) < 1e-3
+
+
+@pytest.mark.parametrize("cfg", ["d2_128", "sessile_256"])
+def test_full_size_one_step_matches_oracle(cfg, thermo):
+    """One step at the benchmark sizes, in the fused launch the benchmark times."""
+    if cfg == "d2_128":
+        p, rho0, T0 = W.droplet(thermo["Tc"], thermo["rho_v"], thermo["rho_l"], n=128, R=15.0)
+    else:
+        p, rho0, T0 = W.sessile(thermo["Tc"], thermo["rho_v"], thermo["rho_l"])
+    o = Oracle(p)
+    f0, g0 = o.init_state(rho0, T0)
+    # a few steps of evolution first so that velocities and forces are developed
+    st, f0, g0 = o.run(f0, g0, 2) if cfg == "d2_128" else (0, f0, g0)
+    f0, g0 = f32(f0), f32(g0)
+    st, fo, go = o.step(f0.astype(np.float64), g0.astype(np.float64))
+    assert st == 0
+    _, fg, gg = gpu_step(p, f0, g0, 1)
+    assert pop_err(fg, fo, thermo) < 1e-5
+    assert pop_err(gg, go, thermo) < 1e-5
+
+
+def test_psi_domain_error_status(thermo):
+    p = W.base_params(8, 8, 8, rho_l=thermo["rho_l"], rho_v=thermo["rho_v"])
+    lat = lbm.Lattice(p, f32(np.full(512, 9.5)), f32(np.full(512, 3 * thermo["Tc"])))
+    lat.lbm_step(1)
+    assert lat.lbm_sync() == lbm.ERR_PSI_DOMAIN
+    lat.close()
+
+
+def test_nonfinite_population_error_status(thermo):
+    p = case_params("periodic", thermo)
+    f, g = droplet_state(p, thermo, seed=15)
+    f[3, 17] = np.nan
+    lat = lbm.Lattice(p)
+    lat.lbm_set_state(f, g)
+    lat.lbm_step(2)
+    assert lat.lbm_sync() == lbm.ERR_NONFINITE
+    st, red = lat.lbm_reduce()
+    assert red[3] >= 1
+    lat.close()
