@@ -55,9 +55,9 @@ def src_digest():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_digest: str, n_cells: int):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
-    path = os.path.join(ROOT, "profiles", "traffic_k_fused.json")
+def ncu_traffic(kernel: str, kernel_digest: str, n_cells: int):
+    """DRAM bytes per launch from the committed ncu summary of `kernel`, if it was taken on this kernel source."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{kernel}.json")
     try:
         d = json.load(open(path))
     except Exception:
@@ -192,7 +192,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128, help="lattice side (the workload is 128)")
-    ap.add_argument("--schedule", default="fused", choices=["fused", "phases"])
+    ap.add_argument("--schedule", default="phases", choices=["fused", "phases"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -233,6 +233,7 @@ def main():
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        time.sleep(0.5)  # let the sampler start before the timed region
         e0.record(stream)
         lat.lbm_step(args.steps)
         e1.record(stream)
@@ -250,15 +251,14 @@ def main():
     ms_step = ms_max / args.steps
     value = world * N * args.steps / (ms_max * 1e-3) / 1e6
 
-    # per-launch duration of the step kernel (one launch per step in the fused schedule)
+    # per-kernel device time from the library's launch timing (CUDA events on the launch stream)
     nl = min(args.steps, 200)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nl)]
-    for a, b in evs:
-        a.record(stream)
-        lat.lbm_step(1)
-        b.record(stream)
-    torch.cuda.synchronize()
-    per_launch_ms = statistics.mean(a.elapsed_time(b) for a, b in evs) / max(1, launches)
+    lat.lbm_profile(True)
+    lat.lbm_step(nl)
+    prof = lat.lbm_profile_read()
+    lat.lbm_profile(False)
+    dom = max(prof, key=lambda k: prof[k][1])
+    per_launch_ms = prof[dom][1] / prof[dom][0]
     lat.close()
 
     # end to end through the C ABI with host buffers: init from host fields, K steps, macros to host
@@ -289,9 +289,10 @@ def main():
     pk = peaks()
     peak = pk.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in pk else "fallback"
-    achieved = BYTES_PER_LU * N / (per_launch_ms * 1e-3) / 1e9 if launches == 1 else BYTES_PER_LU * N / (ms_step * 1e-3) / 1e9
+    # the collide+stream kernel (alone, or inside the fused step) reads and writes every population once
+    achieved = BYTES_PER_LU * N / (per_launch_ms * 1e-3) / 1e9
     digest = src_digest()
-    traffic = ncu_traffic(digest, N)
+    traffic = ncu_traffic(dom, digest, N)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         steps_cpu = 2
@@ -308,8 +309,11 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)",
-                     "bytes_per_lu": BYTES_PER_LU, "kernel": "k_fused" if launches == 1 else "step",
-                     "per_launch_ms": per_launch_ms, "kernel_src_sha": digest},
+                     "bytes_per_lu": BYTES_PER_LU, "kernel": dom, "per_launch_ms": per_launch_ms,
+                     "kernel_src_sha": digest,
+                     "step_effective_GBs": BYTES_PER_LU * N / (ms_step * 1e-3) / 1e9,
+                     "kernels": {k: {"launches": v[0], "ms_per_launch": v[1] / v[0],
+                                     "share": v[1] / sum(w[1] for w in prof.values())} for k, v in prof.items()}},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * N / args.steps,
                 "d2h_bytes_per_step": 5 * 4 * N / args.steps},

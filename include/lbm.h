@@ -139,6 +139,18 @@ const char* lbm_status_string(int status);
 double lbm_Tc(const lbm_params* p);
 int lbm_maxwell(const lbm_params* p, double T, double* rho_v, double* rho_l, double* p_sat);
 
+/* Kernel timing.  While enabled, every kernel that lbm_step launches is
+ * bracketed by CUDA events on the context stream.  lbm_profile(ctx, 1) clears
+ * the counters and starts recording; lbm_profile(ctx, 0) stops.
+ * lbm_profile_read synchronises on the recorded events and writes, for the
+ * first nkinds kernel kinds, the number of launches and their total device
+ * time in milliseconds since the last clear (host arrays, may be NULL).
+ * Kinds: 0 phase A (macro/psi), 1 phase B (force/velocity), 2 phase C
+ * (D3Q19 collide + stream, or both lattices when staged), 3 phase D
+ * (boundary), 4 fused step, 5 phase C of the D3Q7 lattice (side stream). */
+int lbm_profile(lbm_ctx* ctx, int enable);
+int lbm_profile_read(lbm_ctx* ctx, long long* launches, double* ms, int nkinds);
+
 /* Number of kernel launches one lbm_step(ctx, 1) enqueues. */
 int lbm_launches_per_step(const lbm_ctx* ctx);
 

@@ -31,22 +31,30 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def build_lib(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(f) for f in _inputs()):
-        return LIB
-    os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    tmp = LIB + f".tmp{os.getpid()}"
+def build_lib(force: bool = False, verbose: bool = False, extra=(), out: str = None) -> str:
+    LIB_ = out or LIB
+    if not force and os.path.exists(LIB_) and os.path.getmtime(LIB_) >= max(os.path.getmtime(f) for f in _inputs()):
+        return LIB_
+    os.makedirs(os.path.dirname(LIB_), exist_ok=True)
+    tmp = LIB_ + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
            "-cudart", "static", "-I", INCLUDE, "-I", CSRC, *extra,
            "-o", tmp, *[os.path.join(CSRC, s) for s in SOURCES]]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, LIB_)
+    return LIB_
 
 
 if __name__ == "__main__":
-    v = "-v" in sys.argv
-    extra = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else []
-    print(build_lib(force=True, verbose=v, extra=extra))
+    import argparse
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("-v", action="store_true")
+    ap.add_argument("--ptxas", action="store_true")
+    ap.add_argument("--out", default=None)
+    ap.add_argument("-D", action="append", default=[], help="extra preprocessor definitions")
+    a = ap.parse_args()
+    extra = (["-Xptxas", "-v"] if a.ptxas else []) + [f"-D{d}" for d in a.D]
+    print(build_lib(force=True, verbose=a.v, extra=extra, out=a.out))

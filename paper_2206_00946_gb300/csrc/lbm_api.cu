@@ -7,8 +7,10 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "lbm.h"
+#include "lbm_bulk.cuh"
 #include "lbm_fused.cuh"
 #include "lbm_phases.cuh"
 
@@ -17,6 +19,11 @@ using namespace lbm;
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kBulkTile = 256;                                      // cells per staged tile
+constexpr int kBulkSmem = 2 * 26 * kBulkTile * 4 + 2 * 8;           // two stages + two mbarriers
+#ifndef LBM_PHASEC_MINBLOCKS
+#define LBM_PHASEC_MINBLOCKS 4
+#endif
 
 __global__ void k_init(Params P, const float* __restrict__ rho0, const float* __restrict__ T0, float* f, float* g) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x) {
@@ -44,19 +51,28 @@ __global__ void k_phaseB(Params P, Aux X) {
     phaseB(P, c, X);
 }
 
-__global__ void k_phaseC(Params P, const float* __restrict__ fA, const float* __restrict__ gA, float* fB, float* gB,
+__global__ void __launch_bounds__(256, LBM_PHASEC_MINBLOCKS) k_phaseC19(Params P, const float* __restrict__ fA,
+                                                                        float* fB, Aux X) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x)
+    phaseC19(P, c, fA, fB, X);
+}
+
+__global__ void __launch_bounds__(256) k_phaseC7(Params P, const float* __restrict__ gA, float* gB, Aux X) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x)
+    phaseC7(P, c, gA, gB, X);
+}
+
+__global__ void __launch_bounds__(256, LBM_PHASEC_MINBLOCKS) k_phaseC(Params P, const float* __restrict__ fA, const float* __restrict__ gA, float* fB, float* gB,
                          Aux X) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x)
     phaseC(P, c, fA, gA, fB, gB, X);
 }
 
-// grid: (x over boundary candidates of a plane, y over planes)
+// one thread per boundary candidate (boundary_candidate enumerates them)
 __global__ void k_phaseD(Params P, float* fB, float* gB, Aux X) {
-  const int z = blockIdx.y;
-  const int cnt = boundary_count(P, z);
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
-    int x, y;
-    boundary_xy(P, z, k, x, y);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < (int)P.bd_total; k += gridDim.x * blockDim.x) {
+    int x, y, z;
+    boundary_candidate(P, k, x, y, z);
     const int m = node_faces(P, x, y, z);
     if (m) phaseD(P, cell_of(P, x, y, z), x, y, z, m, fB, gB, X);
   }
@@ -144,6 +160,8 @@ __global__ void k_sumT(Params P, const float* __restrict__ g, float* T) {
 
 }  // namespace
 
+#define LBM_PROF_KINDS 6
+
 struct lbm_ctx {
   lbm_params hp;
   Params P;
@@ -164,7 +182,20 @@ struct lbm_ctx {
   double* red_h;
   int red_blocks;
   int grid;
+  int bulk_grid;  // persistent CTAs of the staged phase C (0: unstaged kernel)
   bool has_state;
+  cudaStream_t side;  // second stream for the D3Q7 collision
+  cudaEvent_t ev_fork, ev_join;
+  // kernel timing: event pairs bracketing each launch while profiling is on
+  bool profiling;
+  struct Ev {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Ev>* evs;
+  std::vector<cudaEvent_t>* pool;
+  double prof_ms[LBM_PROF_KINDS];
+  long long prof_n[LBM_PROF_KINDS];
   FusedPlan plan;
 };
 
@@ -217,6 +248,15 @@ Params make_device_params(const lbm_params& p) {
   P.N = (long long)p.nx * p.ny * p.nz;
   fdiv_init((unsigned)p.nx, P.dnx_mul, P.dnx_shr);
   fdiv_init((unsigned)p.ny, P.dny_mul, P.dny_shr);
+  {
+    const bool xnp = p.face_kind[0] != LBM_FACE_PERIODIC, ynp = p.face_kind[2] != LBM_FACE_PERIODIC;
+    const bool znp = p.face_kind[4] != LBM_FACE_PERIODIC;
+    P.bd_zplanes = znp ? 2 : 0;
+    P.bd_perim = (xnp && ynp) ? 2 * p.nx + 2 * (p.ny - 2) : (xnp ? 2 * p.ny : (ynp ? 2 * p.nx : 0));
+    fdiv_init((unsigned)(p.nx * p.ny), P.dpl_mul, P.dpl_shr);
+    fdiv_init((unsigned)(P.bd_perim > 0 ? P.bd_perim : 1), P.dper_mul, P.dper_shr);
+    P.bd_total = (long long)P.bd_zplanes * p.nx * p.ny + (long long)(p.nz - P.bd_zplanes) * P.bd_perim;
+  }
   P.meq_printed = p.meq_printed;
   P.wall_ueq_zero = p.wall_ueq_zero;
   P.eos_kind = p.eos_kind;
@@ -290,6 +330,48 @@ int read_flags(lbm_ctx* c) {
   return LBM_OK;
 }
 
+cudaEvent_t ev_get(lbm_ctx* c) {
+  if (!c->pool->empty()) {
+    cudaEvent_t e = c->pool->back();
+    c->pool->pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Accumulates the recorded launch times (synchronises on the recorded events).
+int prof_collect(lbm_ctx* c) {
+  for (auto& e : *c->evs) {
+    if (cudaEventSynchronize(e.b) != cudaSuccess) return LBM_ERR_CUDA;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.a, e.b) != cudaSuccess) return LBM_ERR_CUDA;
+    c->prof_ms[e.kind] += ms;
+    c->prof_n[e.kind] += 1;
+    c->pool->push_back(e.a);
+    c->pool->push_back(e.b);
+  }
+  c->evs->clear();
+  return LBM_OK;
+}
+
+// Start / end marks of one launch while profiling (no-ops otherwise).
+cudaEvent_t prof_begin(lbm_ctx* c) {
+  if (!c->profiling) return nullptr;
+  if (c->evs->size() >= 8192) prof_collect(c);
+  cudaEvent_t e = ev_get(c);
+  cudaEventRecord(e, c->stream);
+  return e;
+}
+
+void prof_end(lbm_ctx* c, int kind, cudaEvent_t a) {
+  if (!a) return;
+  cudaEvent_t b = ev_get(c);
+  cudaEventRecord(b, c->stream);
+  c->evs->push_back({kind, a, b});
+}
+
 // Phases A and B on the current state (macros of time t); returns launch status.
 int run_macros(lbm_ctx* c, float* Tout) {
   const float* f = c->f[c->cur];
@@ -301,13 +383,43 @@ int run_macros(lbm_ctx* c, float* Tout) {
 
 int step_phases(lbm_ctx* c) {
   const int a = c->cur, b = 1 - c->cur;
+  cudaEvent_t e = prof_begin(c);
   k_phaseA<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->f[a], c->g[a], c->X, nullptr, c->err_d);
+  prof_end(c, 0, e);
+  e = prof_begin(c);
   k_phaseB<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->X);
-  k_phaseC<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->f[a], c->g[a], c->f[b], c->g[b], c->X);
-  if (c->P.any_nonperiodic) {
-    const int plane = c->P.nx * c->P.ny;
-    dim3 gd((plane + kThreads - 1) / kThreads, c->P.nz);
-    k_phaseD<<<gd, kThreads, 0, c->stream>>>(c->P, c->f[b], c->g[b], c->X);
+  prof_end(c, 1, e);
+  if (c->bulk_grid > 0) {
+    e = prof_begin(c);
+    k_phaseC_bulk<kBulkTile><<<c->bulk_grid, kBulkTile, kBulkSmem, c->stream>>>(c->P, c->f[a], c->g[a], c->f[b],
+                                                                               c->g[b], c->X, c->err_d);
+    prof_end(c, 2, e);
+  } else {
+    // the D3Q19 and D3Q7 collisions are independent: the D3Q7 kernel (gather-bound)
+    // runs on a side stream next to the D3Q19 kernel (arithmetic- and bandwidth-bound)
+    cudaEventRecord(c->ev_fork, c->stream);
+    cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    cudaEvent_t e7 = nullptr;
+    if (c->profiling) {
+      e7 = ev_get(c);
+      cudaEventRecord(e7, c->side);
+    }
+    k_phaseC7<<<c->grid, kThreads, 0, c->side>>>(c->P, c->g[a], c->g[b], c->X);
+    if (e7) {
+      cudaEvent_t e7b = ev_get(c);
+      cudaEventRecord(e7b, c->side);
+      c->evs->push_back({5, e7, e7b});
+    }
+    e = prof_begin(c);
+    k_phaseC19<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->f[a], c->f[b], c->X);
+    prof_end(c, 2, e);
+    cudaEventRecord(c->ev_join, c->side);
+    cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+  }
+  if (c->P.bd_total > 0) {
+    e = prof_begin(c);
+    k_phaseD<<<grid_for(c->P.bd_total), kThreads, 0, c->stream>>>(c->P, c->f[b], c->g[b], c->X);
+    prof_end(c, 3, e);
   }
   c->cur = b;
   return cuda_status(cudaGetLastError());
@@ -402,6 +514,14 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
   lbm_ctx* c = new (std::nothrow) lbm_ctx;
   if (!c) return LBM_ERR_ARG;
   std::memset(c, 0, sizeof(*c));
+  c->evs = new (std::nothrow) std::vector<lbm_ctx::Ev>();
+  c->pool = new (std::nothrow) std::vector<cudaEvent_t>();
+  if (!c->evs || !c->pool) {
+    delete c->evs;
+    delete c->pool;
+    delete c;
+    return LBM_ERR_ARG;
+  }
   c->hp = *p;
   c->P = make_device_params(*p);
   c->stream = (cudaStream_t)stream;
@@ -415,6 +535,9 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
     ok = ok && cudaMalloc(&c->g[k], sizeof(float) * 7 * N) == cudaSuccess;
   }
   ok = ok && cudaMalloc(&c->aux, sizeof(float) * 11 * N) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaMalloc(&c->err_d, sizeof(int)) == cudaSuccess;
   ok = ok && cudaMallocHost(&c->err_h, sizeof(int)) == cudaSuccess;
   c->red_blocks = grid_for(N) < 1024 ? grid_for(N) : 1024;
@@ -439,6 +562,17 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
   if (cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream) != cudaSuccess) {
     lbm_destroy(c);
     return LBM_ERR_CUDA;
+  }
+  // bulk-staged phase C: opt-in (LBM_BULK=1); measured slower than the unstaged kernel on
+  // GB300 because phase C is bound by its neighbour gathers, not by the population loads
+  if (N % 4 == 0 && std::getenv("LBM_BULK") != nullptr) {
+    int per_sm = 0, sms = 0;
+    cudaFuncSetAttribute(k_phaseC_bulk<kBulkTile>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBulkSmem);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phaseC_bulk<kBulkTile>, kBulkTile, kBulkSmem);
+    const long long ntiles = (N + kBulkTile - 1) / kBulkTile;
+    long long g = (long long)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    c->bulk_grid = (int)(g < ntiles ? g : ntiles);
   }
   st = fused_plan(c->P, &c->plan);
   if (st == LBM_OK && p->schedule == LBM_SCHED_FUSED) st = fused_alloc(&c->plan, c->P, c->stream);
@@ -506,8 +640,10 @@ int lbm_step(lbm_ctx* c, int n) {
   for (int s = 0; s < n; ++s) {
     int st;
     if (c->hp.schedule == LBM_SCHED_FUSED) {
+      cudaEvent_t e = prof_begin(c);
       st = fused_step(&c->plan, c->P, c->f[c->cur], c->g[c->cur], c->f[1 - c->cur], c->g[1 - c->cur], c->X,
                       c->err_d, c->stream);
+      prof_end(c, 4, e);
       c->cur = 1 - c->cur;
     } else {
       st = step_phases(c);
@@ -517,10 +653,31 @@ int lbm_step(lbm_ctx* c, int n) {
   return LBM_OK;
 }
 
+int lbm_profile(lbm_ctx* c, int enable) {
+  if (!c) return LBM_ERR_ARG;
+  int st = prof_collect(c);
+  for (int k = 0; k < LBM_PROF_KINDS; ++k) {
+    c->prof_ms[k] = 0;
+    c->prof_n[k] = 0;
+  }
+  c->profiling = enable != 0;
+  return st;
+}
+
+int lbm_profile_read(lbm_ctx* c, long long* launches, double* ms, int nkinds) {
+  if (!c || nkinds < 0) return LBM_ERR_ARG;
+  const int st = prof_collect(c);
+  for (int k = 0; k < nkinds && k < LBM_PROF_KINDS; ++k) {
+    if (launches) launches[k] = c->prof_n[k];
+    if (ms) ms[k] = c->prof_ms[k];
+  }
+  return st;
+}
+
 int lbm_launches_per_step(const lbm_ctx* c) {
   if (!c) return 0;
   if (c->hp.schedule == LBM_SCHED_FUSED) return fused_launches(&c->plan);
-  return c->P.any_nonperiodic ? 4 : 3;
+  return (c->P.bd_total > 0 ? 4 : 3) + (c->bulk_grid > 0 ? 0 : 1);
 }
 
 int lbm_macros(lbm_ctx* c, float* rho, float* ux, float* uy, float* uz, float* T, int mem) {
@@ -584,6 +741,17 @@ int lbm_stream_map(lbm_ctx* c, int32_t* map19, int32_t* map7, uint8_t* node_clas
   return st;
 }
 
+#ifdef LBM_FUSED_STATS
+int lbm_fused_stats(unsigned long long* out, int reset) {
+  if (cudaMemcpyFromSymbol(out, g_fstats, sizeof(g_fstats)) != cudaSuccess) return LBM_ERR_CUDA;
+  if (reset) {
+    static unsigned long long zero[4096][10];
+    if (cudaMemcpyToSymbol(g_fstats, zero, sizeof(zero)) != cudaSuccess) return LBM_ERR_CUDA;
+  }
+  return LBM_OK;
+}
+#endif
+
 void lbm_destroy(lbm_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
@@ -593,6 +761,10 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->g[k]);
   }
   cudaFree(c->aux);
+  if (c->side) cudaStreamSynchronize(c->side);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   cudaFree(c->err_d);
   cudaFreeHost(c->err_h);
   cudaFree(c->partial);
@@ -600,6 +772,17 @@ void lbm_destroy(lbm_ctx* c) {
   cudaFreeHost(c->red_h);
   for (int f = 0; f < 6; ++f) cudaFree(c->tface[f]);
   fused_free(&c->plan);
+  if (c->evs) {
+    for (auto& e : *c->evs) {
+      cudaEventDestroy(e.a);
+      cudaEventDestroy(e.b);
+    }
+    delete c->evs;
+  }
+  if (c->pool) {
+    for (auto e : *c->pool) cudaEventDestroy(e);
+    delete c->pool;
+  }
   delete c;
 }
 

@@ -42,7 +42,15 @@ LBM_HD constexpr int c7z(int i) { return i == 5 ? 1 : (i == 6 ? -1 : 0); }
 enum { FACE_PERIODIC = 0, FACE_WALL = 1, FACE_OPEN = 2 };
 enum { ERRF_NONFINITE = 1, ERRF_PSI = 2, ERRF_TIMEOUT = 4 };
 
-// Parameters as the kernels use them (FP32 values precomputed on the host).
+// Reciprocal, correctly rounded (one MUFU + Newton step on the device).
+LBM_HD float rcp(float x) {
+#if defined(__CUDA_ARCH__)
+  return __frcp_rn(x);
+#else
+  return 1.f / x;
+#endif
+}
+
 // Division of a non-negative 32-bit value (< 2^31) by a runtime divisor d with a
 // precomputed multiplier: q = umulhi(n, mul) >> shr (mul = 0 means d = 1).
 LBM_HD unsigned fdiv(unsigned n, unsigned mul, unsigned shr) {
@@ -70,6 +78,10 @@ struct Params {
   int nx, ny, nz;
   long long N;
   unsigned dnx_mul, dnx_shr, dny_mul, dny_shr;
+  // boundary nodes, enumerated plane by plane (see boundary_candidate)
+  int bd_zplanes, bd_perim;
+  unsigned dpl_mul, dpl_shr, dper_mul, dper_shr;
+  long long bd_total;
   int meq_printed, wall_ueq_zero, eos_kind;
   float a, b, R, kappa, inv_Tc, G, inv_G, eos_c0;
   float s_e, s_v, s_q, s_pi;
@@ -96,11 +108,11 @@ LBM_HD void eos_pr(const Params& P, float rho, float T, float& p, float& dpdT) {
   const float s = 1.f + P.kappa * (1.f - sr);
   const float xi = s * s;
   // d xi / dT = -kappa s / sqrt(T Tc) = -kappa s sr / T
-  const float dxi = -P.kappa * s * sr / T;
+  const float dxi = -P.kappa * s * sr * rcp(T);
   const float br = P.b * rho;
-  const float inv1 = 1.f / (1.f - br);
+  const float inv1 = rcp(1.f - br);
   const float den = 1.f + br * (2.f - br);
-  const float att = P.a * rho * rho / den;
+  const float att = P.a * rho * rho * rcp(den);
   p = rho * P.R * T * inv1 - xi * att;
   dpdT = rho * P.R * inv1 - dxi * att;
 }
@@ -141,7 +153,7 @@ LBM_HD void collide19(const Params& P, const float* f, float rho, float ux, floa
   const float m15 = f[15] - f[16] + f[17] - f[18];
   const float m16 = s7_10, m17 = s11_14, m18 = s15_18;
 
-  const float ir = 1.f / rho;
+  const float ir = rcp(rho);
   const float uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
   // rho (u'_a^2 - u_a^2) with u' = u + F/rho
   const float qx = 2.f * ux * Fx + Fx * Fx * ir;
@@ -244,7 +256,7 @@ LBM_HD float lambda_of(const Params& P, float rho) {
 LBM_HD void collide7(const Params& P, const float* g, float rho, float T, float ux, float uy, float uz, float divu,
                      float dpdT, float* gs) {
   const float m1 = g[1] - g[2], m2 = g[3] - g[4], m3 = g[5] - g[6];
-  const float vs = 1.f / (lambda_of(P, rho) * P.inv_cs2t + 0.5f);
+  const float vs = rcp(lambda_of(P, rho) * P.inv_cs2t + 0.5f);
   const float k = -vs * P.inv_cs2t;
   const float ugT = k * (ux * m1 + uy * m2 + uz * m3);
   const float Fbar = rho * P.cv * ugT + T * dpdT * divu;
@@ -281,7 +293,7 @@ LBM_HD void zouhe(int face, float rho_b, float Fx, float Fy, float Fz, float* f)
     }
   }
   const float Fn = sg * (ax == 0 ? Fx : (ax == 1 ? Fy : Fz));
-  const float un = (SZ + 2.f * SP + 0.5f * Fn) / rho_b - 1.f;
+  const float un = (SZ + 2.f * SP + 0.5f * Fn) * rcp(rho_b) - 1.f;
   const float base6 = -rho_b * un * (1.f / 6.f) + 0.125f * Fn;
   const float hx = 0.5f * (tx + 0.5f * Fx), hy = 0.5f * (ty + 0.5f * Fy), hz = 0.5f * (tz + 0.5f * Fz);
 #pragma unroll

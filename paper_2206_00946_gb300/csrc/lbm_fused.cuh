@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "lbm_phases.cuh"
@@ -30,6 +31,9 @@ struct FusedPlan {
   long long total_items;
   unsigned epoch;        // launches since the counters were cleared
   int* stages_d;         // [nstages] phase << 24 | z
+  int* stage_first_d;    // [nstages] first item of each stage
+  int* item_stage_d;     // [total_items] stage of each item
+  std::vector<int> stage_first_h, item_stage_h;
   unsigned* done_d;      // [4 * nz] tiles finished per (phase, plane), cumulative over launches
   unsigned* ctr_d;       // dispatch counter, cumulative over launches
   int* abort_d;
@@ -42,6 +46,8 @@ struct FusedArgs {
   float* fB;
   float* gB;
   const int* stages;
+  const int* stage_first;
+  const int* item_stage;
   unsigned* done;
   unsigned* ctr;
   int* abort;
@@ -84,26 +90,44 @@ __host__ __device__ inline int dep_plane(const Params& P, int z, int k, bool& va
   return q;
 }
 
-__global__ void __launch_bounds__(256) k_fused(Params P, Aux X, FusedArgs A) {
-  __shared__ int s_item;
+__device__ __forceinline__ int fetch_item(const FusedArgs& A) {
+  const unsigned old = atomicAdd(A.ctr, 1u);
+  const int item = (int)(old - A.base);
+  return (item < 0 || item >= A.total_items) ? -1 : item;
+}
+
+#ifdef LBM_FUSED_STATS
+// per CTA: work cycles per phase [0..3], items per phase [4..7], wait cycles [8], total cycles [9]
+__device__ unsigned long long g_fstats[4096][10];
+#define FSTAT(...) __VA_ARGS__
+#else
+#define FSTAT(...)
+#endif
+
+#ifndef LBM_FUSED_MINBLOCKS
+#define LBM_FUSED_MINBLOCKS 2
+#endif
+
+__global__ void __launch_bounds__(256, LBM_FUSED_MINBLOCKS) k_fused(Params P, Aux X, FusedArgs A) {
+  __shared__ int s_next;
   __shared__ int s_ok;
   int err = 0;
   const int plane = P.nx * P.ny;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const unsigned old = atomicAdd(A.ctr, 1u);
-      int item = (int)(old - A.base);
-      if (item < 0 || item >= A.total_items || *(volatile int*)A.abort) item = -1;
-      s_item = item;
-    }
-    __syncthreads();
-    const int item = s_item;
-    if (item < 0) break;
-    const int s = item / A.tiles_per_plane;
-    const int t = item - s * A.tiles_per_plane;
+  if (threadIdx.x == 0) s_next = fetch_item(A);
+  __syncthreads();
+  int item = s_next;
+  FSTAT(long long st_t0 = clock64(); long long st_w = 0; long long st_ph[4] = {0, 0, 0, 0};
+        int st_n[4] = {0, 0, 0, 0};)
+  while (item >= 0) {
+    __syncthreads();  // everyone has read s_next
+    const int s = A.item_stage[item];
+    const int t = item - A.stage_first[s];
     const int code = A.stages[s];
     const int ph = code >> 24, z = code & 0xffffff;
+    FSTAT(const long long st_a = clock64();)
     if (threadIdx.x == 0) {
+      // the next item is claimed now, so its dispatch latency overlaps this item's work
+      s_next = *(volatile int*)A.abort ? -1 : fetch_item(A);
       int ok = 1;
       const int r = dep_radius(ph);
       if (r > 0) {
@@ -125,23 +149,16 @@ __global__ void __launch_bounds__(256) k_fused(Params P, Aux X, FusedArgs A) {
               ok = 0;
               break;
             }
-            __nanosleep(100);
+            __nanosleep(64);
           }
         }
       }
       s_ok = ok;
     }
     __syncthreads();
+    FSTAT(const long long st_b = clock64(); st_w += st_b - st_a;)
     if (!s_ok) break;
-    const int c0 = z * plane + t * A.tile;
-    const int c1 = min(c0 + A.tile, (z + 1) * plane);
-    if (ph == PH_A) {
-      for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) phaseA(P, c, A.fA, A.gA, X, nullptr, err);
-    } else if (ph == PH_B) {
-      for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) phaseB(P, c, X);
-    } else if (ph == PH_C) {
-      for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) phaseC(P, c, A.fA, A.gA, A.fB, A.gB, X);
-    } else {
+    if (ph == PH_D) {
       const int cnt = boundary_count(P, z);
       for (int k = t * A.tile + threadIdx.x; k < min(cnt, (t + 1) * A.tile); k += blockDim.x) {
         int x, y;
@@ -149,13 +166,33 @@ __global__ void __launch_bounds__(256) k_fused(Params P, Aux X, FusedArgs A) {
         const int m = node_faces(P, x, y, z);
         if (m) phaseD(P, cell_of(P, x, y, z), x, y, z, m, A.fB, A.gB, X);
       }
+    } else {
+      const int c0 = z * plane + t * A.tile;
+      const int c1 = min(c0 + A.tile, (z + 1) * plane);
+      if (ph == PH_A) {
+        for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) phaseA(P, c, A.fA, A.gA, X, nullptr, err);
+      } else if (ph == PH_B) {
+        for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) phaseB(P, c, X);
+      } else {
+        for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) phaseC(P, c, A.fA, A.gA, A.fB, A.gB, X);
+      }
     }
     __syncthreads();
+    FSTAT(st_ph[ph] += clock64() - st_b; st_n[ph] += 1;)
     if (threadIdx.x == 0) {
       __threadfence();
       atomicAdd(A.done + ph * P.nz + z, 1u);
     }
+    item = s_next;
   }
+  FSTAT(if (threadIdx.x == 0 && blockIdx.x < 4096) {
+    for (int k = 0; k < 4; ++k) {
+      g_fstats[blockIdx.x][k] += st_ph[k];
+      g_fstats[blockIdx.x][4 + k] += st_n[k];
+    }
+    g_fstats[blockIdx.x][8] += st_w;
+    g_fstats[blockIdx.x][9] += clock64() - st_t0;
+  })
   if (err) atomicOr(A.err, err);
 }
 
@@ -220,7 +257,11 @@ inline std::vector<int> fused_order(const Params& P, int gap) {
   return order;
 }
 
-inline int fused_plan(const Params& P, FusedPlan* plan, int threads = 256, int cells_per_thread = 2) {
+// Tuning knobs (environment, read at lbm_init): LBM_FUSED_CPT = cells per
+// thread of one work item, LBM_FUSED_GAP = minimum distance in stages between a
+// stage and the stages it depends on (0 = one in-flight window).
+inline int fused_plan(const Params& P, FusedPlan* plan, int threads = 256, int cells_per_thread = 4) {
+  if (const char* e = std::getenv("LBM_FUSED_CPT")) cells_per_thread = std::max(1, std::atoi(e));
   plan->threads = threads;
   const long long plane = (long long)P.nx * P.ny;
   long long tile = (long long)threads * cells_per_thread;
@@ -235,13 +276,34 @@ inline int fused_plan(const Params& P, FusedPlan* plan, int threads = 256, int c
   if (per_sm <= 0) per_sm = 1;
   plan->grid = sms * per_sm;
   const int inflight_stages = (plan->grid + plan->tiles_per_plane - 1) / plan->tiles_per_plane;
-  plan->stages_h = fused_order(P, inflight_stages + 1);
+  int gap = inflight_stages + 1;
+  if (const char* e = std::getenv("LBM_FUSED_GAP")) {
+    const int g = std::atoi(e);
+    if (g > 0) gap = g;
+  }
+  plan->stages_h = fused_order(P, gap);
   plan->nstages = (int)plan->stages_h.size();
-  plan->total_items = (long long)plan->nstages * plan->tiles_per_plane;
-  if (plan->total_items > 0x3fffffffLL) return -1;
+  plan->stage_first_h.assign(plan->nstages, 0);
+  plan->item_stage_h.clear();
+  long long items = 0;
+  for (int s = 0; s < plan->nstages; ++s) {
+    const int ph = plan->stages_h[s] >> 24, z = plan->stages_h[s] & 0xffffff;
+    long long n = plan->tiles_per_plane;
+    if (ph == PH_D) {
+      const long long cnt = (P.face_kind[4] != FACE_PERIODIC && (z == 0 || z == P.nz - 1)) ? plane : P.bd_perim;
+      n = std::max(1LL, (cnt + tile - 1) / tile);
+    }
+    plan->stage_first_h[s] = (int)items;
+    items += n;
+    if (items > 0x3fffffffLL) return -1;
+    for (long long k = 0; k < n; ++k) plan->item_stage_h.push_back(s);
+  }
+  plan->total_items = items;
   if ((long long)plan->grid > plan->total_items) plan->grid = (int)plan->total_items;
   plan->epoch = 0;
   plan->stages_d = nullptr;
+  plan->stage_first_d = nullptr;
+  plan->item_stage_d = nullptr;
   plan->done_d = nullptr;
   plan->ctr_d = nullptr;
   plan->abort_d = nullptr;
@@ -250,6 +312,14 @@ inline int fused_plan(const Params& P, FusedPlan* plan, int threads = 256, int c
 
 inline int fused_alloc(FusedPlan* plan, const Params& P, cudaStream_t s) {
   if (cudaMalloc(&plan->stages_d, sizeof(int) * plan->nstages) != cudaSuccess) return -2;
+  if (cudaMalloc(&plan->stage_first_d, sizeof(int) * plan->nstages) != cudaSuccess) return -2;
+  if (cudaMalloc(&plan->item_stage_d, sizeof(int) * plan->total_items) != cudaSuccess) return -2;
+  if (cudaMemcpyAsync(plan->stage_first_d, plan->stage_first_h.data(), sizeof(int) * plan->nstages,
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return -2;
+  if (cudaMemcpyAsync(plan->item_stage_d, plan->item_stage_h.data(), sizeof(int) * plan->total_items,
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return -2;
   if (cudaMalloc(&plan->done_d, sizeof(unsigned) * 4 * P.nz) != cudaSuccess) return -2;
   if (cudaMalloc(&plan->ctr_d, sizeof(unsigned)) != cudaSuccess) return -2;
   if (cudaMalloc(&plan->abort_d, sizeof(int)) != cudaSuccess) return -2;
@@ -281,6 +351,8 @@ inline int fused_step(FusedPlan* plan, const Params& P, const float* fA, const f
   a.fB = fB;
   a.gB = gB;
   a.stages = plan->stages_d;
+  a.stage_first = plan->stage_first_d;
+  a.item_stage = plan->item_stage_d;
   a.done = plan->done_d;
   a.ctr = plan->ctr_d;
   a.abort = plan->abort_d;
@@ -299,10 +371,16 @@ inline int fused_step(FusedPlan* plan, const Params& P, const float* fA, const f
 
 inline void fused_free(FusedPlan* plan) {
   cudaFree(plan->stages_d);
+  cudaFree(plan->stage_first_d);
+  cudaFree(plan->item_stage_d);
+  plan->stage_first_d = nullptr;
+  plan->item_stage_d = nullptr;
   cudaFree(plan->done_d);
   cudaFree(plan->ctr_d);
   cudaFree(plan->abort_d);
   plan->stages_d = nullptr;
+  plan->stage_first_d = nullptr;
+  plan->item_stage_d = nullptr;
   plan->done_d = nullptr;
   plan->ctr_d = nullptr;
   plan->abort_d = nullptr;

@@ -77,6 +77,48 @@ LBM_HD int dest7_cell(const Params& P, int x, int y, int z, int i) {
   return cell_of(P, q[0], q[1], q[2]);
 }
 
+// Neighbours of one cell, per axis a and step k (0: -1, 1: +1): the cell-index
+// offset (periodic faces wrap; 0 beyond a non-periodic face) and the kind of
+// face crossed (0 inside or periodic, FACE_WALL, FACE_OPEN).  The push, psi and
+// velocity rules of the step all derive from this table without branching on
+// the cell's position.
+struct Nb {
+  int off[3][2];
+  int kind[3][2];
+};
+
+LBM_HD void make_nb(const Params& P, int x, int y, int z, Nb& nb) {
+  const int q[3] = {x, y, z};
+  const int n[3] = {P.nx, P.ny, P.nz};
+  const int st[3] = {1, P.nx, P.nx * P.ny};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const bool per = P.face_kind[2 * a] == FACE_PERIODIC;
+    const bool lo = q[a] == 0, hi = q[a] == n[a] - 1;
+    nb.off[a][0] = !lo ? -st[a] : (per ? (n[a] - 1) * st[a] : 0);
+    nb.kind[a][0] = (!lo || per) ? 0 : P.face_kind[2 * a];
+    nb.off[a][1] = !hi ? st[a] : (per ? -(n[a] - 1) * st[a] : 0);
+    nb.kind[a][1] = (!hi || per) ? 0 : P.face_kind[2 * a + 1];
+  }
+}
+
+// kinds crossed by a move (cx, cy, cz), OR-ed (FACE_WALL = 1, FACE_OPEN = 2)
+LBM_HD int nb_kind(const Nb& nb, int cx, int cy, int cz) {
+  return (cx ? nb.kind[0][cx > 0] : 0) | (cy ? nb.kind[1][cy > 0] : 0) | (cz ? nb.kind[2][cz > 0] : 0);
+}
+LBM_HD int nb_off(const Nb& nb, int cx, int cy, int cz) {
+  return (cx ? nb.off[0][cx > 0] : 0) + (cy ? nb.off[1][cy > 0] : 0) + (cz ? nb.off[2][cz > 0] : 0);
+}
+// psi rule: a wall mirrors through the wall layer (Eq. 36 at 90 degrees), an
+// open face copies the boundary node, periodic faces wrap.
+LBM_HD int nb_off_psi(const Nb& nb, int cx, int cy, int cz) {
+  int o = 0;
+  if (cx) o += nb.kind[0][cx > 0] == FACE_WALL ? nb.off[0][cx < 0] : nb.off[0][cx > 0];
+  if (cy) o += nb.kind[1][cy > 0] == FACE_WALL ? nb.off[1][cy < 0] : nb.off[1][cy > 0];
+  if (cz) o += nb.kind[2][cz > 0] == FACE_WALL ? nb.off[2][cz < 0] : nb.off[2][cz > 0];
+  return o;
+}
+
 // psi at lattice point (x,y,z) that may lie outside the domain: periodic faces
 // wrap; open faces copy the boundary node; wall faces mirror through the wall
 // layer and add the wetting term sqrt(|grad_t psi|^2) tan(pi/2 - theta) of

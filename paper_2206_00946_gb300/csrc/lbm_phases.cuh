@@ -72,6 +72,25 @@ __device__ __forceinline__ void boundary_xy(const Params& P, int z, int k, int& 
   }
 }
 
+// All boundary nodes of the lattice as one flat index range: the whole planes
+// z = 0 and nz-1 when the z faces are not periodic, then the perimeter
+// candidates of the other planes.
+__device__ __forceinline__ void boundary_candidate(const Params& P, int idx, int& x, int& y, int& z) {
+  const int plane = P.nx * P.ny;
+  int k;
+  if (idx < P.bd_zplanes * plane) {
+    const int zz = (int)fdiv((unsigned)idx, P.dpl_mul, P.dpl_shr);
+    z = zz == 0 ? 0 : P.nz - 1;
+    k = idx - zz * plane;
+  } else {
+    const int j = idx - P.bd_zplanes * plane;
+    const int zi = (int)fdiv((unsigned)j, P.dper_mul, P.dper_shr);
+    k = j - zi * P.bd_perim;
+    z = (P.bd_zplanes ? 1 : 0) + zi;
+  }
+  boundary_xy(P, z, k, x, y);
+}
+
 __device__ __forceinline__ bool interior1(const Params& P, int x, int y, int z) {
   return x >= 1 && x <= P.nx - 2 && y >= 1 && y <= P.ny - 2 && z >= 1 && z <= P.nz - 2;
 }
@@ -101,22 +120,32 @@ __device__ __forceinline__ void phaseA(const Params& P, int c, const float* __re
 }
 
 // ------------------------------------------------------------------- B -----
+// Wetting term of Eq. 36 is needed only next to a wall face with theta != 90.
+__device__ __forceinline__ bool needs_wetting(const Params& P, const Nb& nb) {
+  bool w = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int k = 0; k < 2; ++k) w |= nb.kind[a][k] == FACE_WALL && P.tan_wet[2 * a + k] != 0.f;
+  return w;
+}
+
 __device__ __forceinline__ void phaseB(const Params& P, int c, const Aux& X) {
   int x, y, z;
   cell_xyz(P, c, x, y, z);
+  Nb nb;
+  make_nb(P, x, y, z, nb);
   const float* psi = X.psi;
   float sx = 0.f, sy = 0.f, sz = 0.f;
-  if (interior1(P, x, y, z)) {
-    const int sY = P.nx, sZ = P.nx * P.ny;
+  if (!needs_wetting(P, nb)) {
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
-      const float v = varpi19(i) * __ldcg(psi + c + c19x(i) + c19y(i) * sY + c19z(i) * sZ);
+      const float v = varpi19(i) * psi[c + nb_off_psi(nb, c19x(i), c19y(i), c19z(i))];
       sx += c19x(i) * v;
       sy += c19y(i) * v;
       sz += c19z(i) * v;
     }
   } else {
-#pragma unroll
     for (int i = 1; i < 19; ++i) {
       const float v = varpi19(i) * psi_ext(P, psi, x + c19x(i), y + c19y(i), z + c19z(i));
       sx += c19x(i) * v;
@@ -124,7 +153,7 @@ __device__ __forceinline__ void phaseB(const Params& P, int c, const Aux& X) {
       sz += c19z(i) * v;
     }
   }
-  const float k = -P.G * __ldcg(psi + c);
+  const float k = -P.G * psi[c];
   const float Fx = k * sx, Fy = k * sy, Fz = k * sz;
   X.Fx[c] = Fx;
   X.Fy[c] = Fy;
@@ -133,97 +162,112 @@ __device__ __forceinline__ void phaseB(const Params& P, int c, const Aux& X) {
   if (m && on_wall(P, m)) {
     X.ux[c] = X.uy[c] = X.uz[c] = 0.f;
   } else {
-    const float ir = 1.f / __ldcg(X.rho + c);
-    X.ux[c] = (__ldcg(X.jx + c) + 0.5f * Fx) * ir;
-    X.uy[c] = (__ldcg(X.jy + c) + 0.5f * Fy) * ir;
-    X.uz[c] = (__ldcg(X.jz + c) + 0.5f * Fz) * ir;
+    const float ir = rcp(X.rho[c]);
+    X.ux[c] = (X.jx[c] + 0.5f * Fx) * ir;
+    X.uy[c] = (X.jy[c] + 0.5f * Fy) * ir;
+    X.uz[c] = (X.jz[c] + 0.5f * Fz) * ir;
   }
 }
 
 // ------------------------------------------------------------------- C -----
-__device__ __forceinline__ void phaseC(const Params& P, int c, const float* __restrict__ fA,
-                                       const float* __restrict__ gA, float* __restrict__ fB,
-                                       float* __restrict__ gB, const Aux& X) {
+// Phase C, D3Q19 part, for one cell whose pre-collision populations are in fl:
+// collision with the exact-difference forcing, push streaming, bounce-back.
+__device__ __forceinline__ void phaseC19_cell(const Params& P, int c, const float* fl, float* fB, const Aux& X) {
   int x, y, z;
   cell_xyz(P, c, x, y, z);
+  Nb nb;
+  make_nb(P, x, y, z, nb);
   const long long N = P.N;
-  float fl[19], gl[7];
-#pragma unroll
-  for (int i = 0; i < 19; ++i) fl[i] = __ldg(fA + i * N + c);
-#pragma unroll
-  for (int i = 0; i < 7; ++i) gl[i] = __ldg(gA + i * N + c);
+  const float Fx = X.Fx[c], Fy = X.Fy[c], Fz = X.Fz[c];
   float rho, jx, jy, jz;
   sum19(fl, rho, jx, jy, jz);
-  const float T = sum7(gl);
   const int m = P.any_nonperiodic ? node_faces(P, x, y, z) : 0;
   const bool wall = m && on_wall(P, m);
-  const float Fx = __ldcg(X.Fx + c), Fy = __ldcg(X.Fy + c), Fz = __ldcg(X.Fz + c);
-  float ux, uy, uz;
-  if (wall && P.wall_ueq_zero) {
-    ux = uy = uz = 0.f;
-  } else {
-    const float ir = 1.f / rho;
-    ux = jx * ir;
-    uy = jy * ir;
-    uz = jz * ir;
-  }
+  const float ir = rcp(rho);
+  float ux = jx * ir, uy = jy * ir, uz = jz * ir;
+  if (wall && P.wall_ueq_zero) ux = uy = uz = 0.f;
   float fs[19];
   collide19(P, fl, rho, ux, uy, uz, Fx, Fy, Fz, fs);
-
-  const bool in1 = interior1(P, x, y, z);
-  const int sY = P.nx, sZ = P.nx * P.ny;
-  if (in1) {
 #pragma unroll
-    for (int i = 0; i < 19; ++i) fB[i * N + (c + c19x(i) + c19y(i) * sY + c19z(i) * sZ)] = fs[i];
-  } else {
-#pragma unroll
-    for (int i = 0; i < 19; ++i) {
-      const long long d = dest19(P, x, y, z, i);
-      if (d >= 0) fB[d] = fs[i];
-    }
+  for (int i = 0; i < 19; ++i) {
+    const int k = nb_kind(nb, c19x(i), c19y(i), c19z(i));
+    if (k == 0)
+      fB[i * N + (c + nb_off(nb, c19x(i), c19y(i), c19z(i)))] = fs[i];
+    else if (k & FACE_WALL)
+      fB[opp19(i) * N + c] = fs[i];  // modified bounce-back
+    // else: leaves through an open face
   }
+}
 
-  // D3Q7: div u by the isotropic D3Q19 difference, grad T from the local moments
+// Phase C, D3Q7 part: div u by the isotropic D3Q19 difference, grad T from the
+// local moments, collision with the source, relaxed push streaming.  rho and the
+// real velocity of the cell come from phases A and B.
+__device__ __forceinline__ void phaseC7_cell(const Params& P, int c, const float* gl, const float* __restrict__ gA,
+                                             float* gB, const Aux& X) {
+  int x, y, z;
+  cell_xyz(P, c, x, y, z);
+  Nb nb;
+  make_nb(P, x, y, z, nb);
+  const long long N = P.N;
+  const float rho = X.rho[c];
+  const float T = sum7(gl);
   float du = 0.f;
-  if (in1) {
 #pragma unroll
-    for (int i = 1; i < 19; ++i) {
-      const int n = c + c19x(i) + c19y(i) * sY + c19z(i) * sZ;
-      float s = 0.f;
-      if (c19x(i)) s += c19x(i) * __ldcg(X.ux + n);
-      if (c19y(i)) s += c19y(i) * __ldcg(X.uy + n);
-      if (c19z(i)) s += c19z(i) * __ldcg(X.uz + n);
-      du += w19(i) * s;
-    }
-  } else {
-#pragma unroll
-    for (int i = 1; i < 19; ++i) {
-      float vx, vy, vz;
-      u_ext(P, X.ux, X.uy, X.uz, x + c19x(i), y + c19y(i), z + c19z(i), vx, vy, vz);
-      du += w19(i) * (c19x(i) * vx + c19y(i) * vy + c19z(i) * vz);
-    }
+  for (int i = 1; i < 19; ++i) {
+    const int k = nb_kind(nb, c19x(i), c19y(i), c19z(i));
+    if (k & FACE_WALL) continue;  // zero velocity beyond a wall
+    const int n = c + nb_off(nb, c19x(i), c19y(i), c19z(i));
+    float s = 0.f;
+    if (c19x(i)) s += c19x(i) * X.ux[n];
+    if (c19y(i)) s += c19y(i) * X.uy[n];
+    if (c19z(i)) s += c19z(i) * X.uz[n];
+    du += w19(i) * s;
   }
   du *= 3.f;
   float p, dpdT;
   eos_pr(P, rho, T, p, dpdT);
-  const float uxr = __ldcg(X.ux + c), uyr = __ldcg(X.uy + c), uzr = __ldcg(X.uz + c);
   float gs[7];
-  collide7(P, gl, rho, T, uxr, uyr, uzr, du, dpdT, gs);
-  const float icv = P.inv_cv;
+  collide7(P, gl, rho, T, X.ux[c], X.uy[c], X.uz[c], du, dpdT, gs);
   // relaxed streaming: g_i(y) += (g*_i(y - c_i) - g_i(y)) / (rho(y) c_v)
-  gB[c] = gl[0] + (gs[0] - gl[0]) / (rho * P.cv);
+  gB[c] = gl[0] + (gs[0] - gl[0]) * rcp(rho * P.cv);
 #pragma unroll
   for (int i = 1; i < 7; ++i) {
-    int yc;
-    if (in1)
-      yc = c + c7x(i) + c7y(i) * sY + c7z(i) * sZ;
-    else
-      yc = dest7_cell(P, x, y, z, i);
-    if (yc < 0) continue;
+    if (nb_kind(nb, c7x(i), c7y(i), c7z(i))) continue;
+    const int yc = c + nb_off(nb, c7x(i), c7y(i), c7z(i));
     const float gold = __ldg(gA + i * N + yc);
-    const float ry = __ldcg(X.rho + yc);
-    gB[i * N + yc] = gold + (gs[i] - gold) / ry * icv;
+    const float ry = X.rho[yc];
+    gB[i * N + yc] = gold + (gs[i] - gold) * rcp(ry * P.cv);
   }
+}
+
+__device__ __forceinline__ void phaseC_cell(const Params& P, int c, const float* fl, const float* gl,
+                                            const float* __restrict__ gA, float* fB, float* gB, const Aux& X) {
+  phaseC19_cell(P, c, fl, fB, X);
+  phaseC7_cell(P, c, gl, gA, gB, X);
+}
+
+__device__ __forceinline__ void phaseC19(const Params& P, int c, const float* __restrict__ fA, float* fB,
+                                         const Aux& X) {
+  const long long N = P.N;
+  float fl[19];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) fl[i] = __ldg(fA + i * N + c);
+  phaseC19_cell(P, c, fl, fB, X);
+}
+
+__device__ __forceinline__ void phaseC7(const Params& P, int c, const float* __restrict__ gA, float* gB,
+                                        const Aux& X) {
+  const long long N = P.N;
+  float gl[7];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) gl[i] = __ldg(gA + i * N + c);
+  phaseC7_cell(P, c, gl, gA, gB, X);
+}
+
+__device__ __forceinline__ void phaseC(const Params& P, int c, const float* __restrict__ fA,
+                                       const float* __restrict__ gA, float* fB, float* gB, const Aux& X) {
+  phaseC19(P, c, fA, fB, X);
+  phaseC7(P, c, gA, gB, X);
 }
 
 // ------------------------------------------------------------------- D -----
@@ -235,8 +279,8 @@ __device__ __forceinline__ float face_T_at(const Params& P, int face, int x, int
   return t[x + P.nx * y];
 }
 
-__device__ __forceinline__ void phaseD(const Params& P, int c, int x, int y, int z, int m,
-                                       float* __restrict__ fB, float* __restrict__ gB, const Aux& X) {
+__device__ __forceinline__ void phaseD(const Params& P, int c, int x, int y, int z, int m, float* fB, float* gB,
+                                       const Aux& X) {
   const long long N = P.N;
   int nnp = 0, nopen = 0, oface = -1;
   float rb = 0.f, Tb = 0.f;
@@ -254,31 +298,33 @@ __device__ __forceinline__ void phaseD(const Params& P, int c, int x, int y, int
     q[f >> 1] += (f & 1) ? -1 : 1;
   }
   if (nopen) {
+    // unknown populations: those arriving from beyond a non-periodic face
+    unsigned unk = 0;
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+      const int sx = x - c19x(i), sy = y - c19y(i), sz = z - c19z(i);
+      const bool u = ((sx < 0 || sx >= P.nx) && P.face_kind[0] != FACE_PERIODIC) ||
+                     ((sy < 0 || sy >= P.ny) && P.face_kind[2] != FACE_PERIODIC) ||
+                     ((sz < 0 || sz >= P.nz) && P.face_kind[4] != FACE_PERIODIC);
+      unk |= (u ? 1u : 0u) << i;
+    }
     float fl[19];
-#pragma unroll
-    for (int i = 0; i < 19; ++i) fl[i] = __ldcg(fB + i * N + c);
     if (nnp == 1) {
-      zouhe(oface, P.face_rho[oface], __ldcg(X.Fx + c), __ldcg(X.Fy + c), __ldcg(X.Fz + c), fl);
-    } else {
-      float fe[19];
-      feq19(rb / (float)nopen, 0.f, 0.f, 0.f, fe);
 #pragma unroll
-      for (int i = 0; i < 19; ++i) {
-        const int sx = x - c19x(i), sy = y - c19y(i), sz = z - c19z(i);
-        const bool unk = ((sx < 0 || sx >= P.nx) && P.face_kind[0] != FACE_PERIODIC) ||
-                         ((sy < 0 || sy >= P.ny) && P.face_kind[2] != FACE_PERIODIC) ||
-                         ((sz < 0 || sz >= P.nz) && P.face_kind[4] != FACE_PERIODIC);
-        if (unk) fl[i] = fe[i];
-      }
+      for (int i = 0; i < 19; ++i) fl[i] = ((unk >> i) & 1u) ? 0.f : fB[i * N + c];
+      zouhe(oface, P.face_rho[oface], X.Fx[c], X.Fy[c], X.Fz[c], fl);
+    } else {
+      feq19(rb / (float)nopen, 0.f, 0.f, 0.f, fl);
     }
 #pragma unroll
-    for (int i = 0; i < 19; ++i) fB[i * N + c] = fl[i];
+    for (int i = 1; i < 19; ++i)
+      if ((unk >> i) & 1u) fB[i * N + c] = fl[i];
   }
   Tb /= (float)nnp;
   const int cf = cell_of(P, q[0], q[1], q[2]);
   float gf[7];
 #pragma unroll
-  for (int i = 0; i < 7; ++i) gf[i] = __ldcg(gB + i * N + cf);
+  for (int i = 0; i < 7; ++i) gf[i] = gB[i * N + cf];
   const float Tf = sum7(gf);
   const float w0 = 1.f - P.wbar, w1 = P.wbar * (1.f / 6.f);
   gB[c] = w0 * Tb + gf[0] - w0 * Tf;

@@ -15,7 +15,7 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "liblbm.so")
+LIB_PATH = os.environ.get("LBM_LIB") or os.path.join(_HERE, "_lib", "liblbm.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_PSI_DOMAIN, ERR_TIMEOUT, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 FACE_PERIODIC, FACE_WALL, FACE_OPEN = 0, 1, 2
@@ -43,7 +43,8 @@ class lbm_params(ct.Structure):
 # every symbol declared in include/lbm.h
 EXPORTS = ["lbm_init", "lbm_set_state", "lbm_get_state", "lbm_set_face_T", "lbm_step", "lbm_macros",
            "lbm_reduce", "lbm_sync", "lbm_stream_map", "lbm_destroy", "lbm_status_string", "lbm_Tc",
-           "lbm_maxwell", "lbm_launches_per_step"]
+           "lbm_maxwell", "lbm_launches_per_step", "lbm_profile", "lbm_profile_read"]
+PROFILE_KINDS = ["phaseA", "phaseB", "phaseC", "phaseD", "fused", "phaseC7"]
 
 _lib = None
 
@@ -80,6 +81,8 @@ def load(path: str = LIB_PATH):
     L.lbm_Tc.restype = _D
     L.lbm_maxwell.argtypes = [P, _D, ct.POINTER(_D), ct.POINTER(_D), ct.POINTER(_D)]
     L.lbm_launches_per_step.argtypes = [vp]
+    L.lbm_profile.argtypes = [vp, ct.c_int]
+    L.lbm_profile_read.argtypes = [vp, vp, vp, ct.c_int]
     _lib = L
     return L
 
@@ -200,6 +203,17 @@ class Lattice:
 
     def lbm_launches_per_step(self):
         return load().lbm_launches_per_step(self._ctx)
+
+    def lbm_profile(self, enable=True):
+        _check(load().lbm_profile(self._ctx, int(bool(enable))), "lbm_profile")
+
+    def lbm_profile_read(self):
+        """{kind: (launches, total ms)} since the last lbm_profile(True)."""
+        n = np.zeros(len(PROFILE_KINDS), dtype=np.int64)
+        ms = np.zeros(len(PROFILE_KINDS), dtype=np.float64)
+        _check(load().lbm_profile_read(self._ctx, n.ctypes.data, ms.ctypes.data, len(PROFILE_KINDS)),
+               "lbm_profile_read")
+        return {k: (int(n[i]), float(ms[i])) for i, k in enumerate(PROFILE_KINDS) if n[i] > 0}
 
     # numpy conveniences (host copies through the same C calls)
     def state(self):

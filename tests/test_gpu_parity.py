@@ -107,13 +107,22 @@ def test_one_step_populations_match_oracle(name, schedule, thermo):
 
 
 @pytest.mark.parametrize("name", ["walls_z", "open_all", "wall_bottom_open_top", "periodic"])
-def test_fused_and_phase_schedules_are_bit_identical(name, thermo):
+def test_fused_and_phase_schedules_agree(name, thermo):
+    """Same per-cell code in both schedules; they differ only in how the compiler contracts FMAs.
+
+    Starts from equilibrium: vapor with a 3 % density bump (a droplet in these
+    tiny boxes would touch the constant-pressure faces, and imposing rho_v on a
+    liquid node is not a well-posed flow)."""
     p = case_params(name, thermo)
-    f, g = droplet_state(p, thermo, seed=12)
-    _, f1, g1 = gpu_step(p, f, g, 5, lbm.SCHED_FUSED)
-    _, f2, g2 = gpu_step(p, f, g, 5, lbm.SCHED_PHASES)
-    np.testing.assert_array_equal(f1, f2)
-    np.testing.assert_array_equal(g1, g2)
+    x, y, z = W.grid(p["nx"], p["ny"], p["nz"])
+    r2 = (x - 0.45 * p["nx"]) ** 2 + (y - 0.55 * p["ny"]) ** 2 + (z - 0.5 * p["nz"]) ** 2
+    rho0 = W.perturb(thermo["rho_v"] * (1.0 + 0.03 * np.exp(-r2 / 4.0)), 1e-3, seed=12)
+    f, g = Oracle(p).init_state(rho0, np.full(rho0.shape, thermo["Ts"]))
+    f, g = f32(f), f32(g)
+    _, f1, g1 = gpu_step(p, f, g, 20, lbm.SCHED_FUSED)
+    _, f2, g2 = gpu_step(p, f, g, 20, lbm.SCHED_PHASES)
+    ef, eg = pop_err(f1, f2.astype(np.float64), thermo), pop_err(g1, g2.astype(np.float64), thermo)
+    assert ef < 1e-5 and eg < 1e-5, (ef, eg)
 
 
 @pytest.mark.parametrize("name", list(CASES))
