@@ -151,6 +151,28 @@ int lbm_maxwell(const lbm_params* p, double T, double* rho_v, double* rho_l, dou
 int lbm_profile(lbm_ctx* ctx, int enable);
 int lbm_profile_read(lbm_ctx* ctx, long long* launches, double* ms, int nkinds);
 
+/* The reductions of lbm_reduce for caller-owned population buffers, with no
+ * device allocation.  The paper has no counterpart: this exists for callers
+ * that cannot call cudaMalloc when they need the diagnostics -- an application
+ * that serves all device memory from its own pool and forbids allocations
+ * after start-up, or a plug-in that receives device pointers from its host and
+ * owns no lbm_ctx.
+ *   f, g     device pointers to 19*n_cells and 7*n_cells floats (SoA layout above);
+ *   cv, rho_v, rho_l   as in lbm_params;
+ *   out      device pointer to 4 doubles, written as by lbm_reduce (mass,
+ *            sum rho c_v T, droplet volume, count of non-finite cells);
+ *   stream   cudaStream_t the two kernels are enqueued on (asynchronous).
+ * Scratch: a fixed device array of 4096 x 4 doubles (128 KiB) inside the
+ * library, held by every GPU that loads the library until the process exits.
+ * n_cells may be at most 4096 * 8192 = 33,554,432; larger sizes return
+ * LBM_ERR_ARG before any device work.  The first call on each device looks up
+ * the array's device address; make that first call before any stream capture.
+ * All calls share the one array, which keeps the last call's partial sums, so
+ * calls that overlap on the GPU (other streams, other threads) race: serialise
+ * them.  Every partial sum a call reads is written by that call first. */
+int lbm_reduce_static(const float* f, const float* g, long long n_cells, double cv, double rho_v, double rho_l,
+                      double* out, void* stream);
+
 /* Number of kernel launches one lbm_step(ctx, 1) enqueues. */
 int lbm_launches_per_step(const lbm_ctx* ctx);
 

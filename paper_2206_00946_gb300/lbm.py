@@ -43,7 +43,7 @@ class lbm_params(ct.Structure):
 # every symbol declared in include/lbm.h
 EXPORTS = ["lbm_init", "lbm_set_state", "lbm_get_state", "lbm_set_face_T", "lbm_step", "lbm_macros",
            "lbm_reduce", "lbm_sync", "lbm_stream_map", "lbm_destroy", "lbm_status_string", "lbm_Tc",
-           "lbm_maxwell", "lbm_launches_per_step", "lbm_profile", "lbm_profile_read"]
+           "lbm_maxwell", "lbm_launches_per_step", "lbm_profile", "lbm_profile_read", "lbm_reduce_static"]
 PROFILE_KINDS = ["phaseA", "phaseB", "phaseC", "phaseD", "fused", "phaseC7"]
 
 _lib = None
@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH):
     L.lbm_launches_per_step.argtypes = [vp]
     L.lbm_profile.argtypes = [vp, ct.c_int]
     L.lbm_profile_read.argtypes = [vp, vp, vp, ct.c_int]
+    L.lbm_reduce_static.argtypes = [vp, vp, ct.c_longlong, _D, _D, _D, vp, vp]
     _lib = L
     return L
 
@@ -146,6 +147,13 @@ def lbm_maxwell(params: dict, T: float):
     _check(load().lbm_maxwell(ct.byref(make_params(params)), T, ct.byref(rv), ct.byref(rl), ct.byref(ps)),
            "lbm_maxwell")
     return rv.value, rl.value, ps.value
+
+
+def lbm_reduce_static(f, g, n_cells, cv, rho_v, rho_l, out, stream=None):
+    """Reductions of caller-owned device populations into a device array of 4 doubles, with no
+    device allocation (see include/lbm.h); returns the status code."""
+    return load().lbm_reduce_static(_ptr(f), _ptr(g), int(n_cells), float(cv), float(rho_v), float(rho_l),
+                                    _ptr(out), stream)
 
 
 class Lattice:
