@@ -192,7 +192,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128, help="lattice side (the workload is 128)")
-    ap.add_argument("--schedule", default="phases", choices=["fused", "phases"])
+    ap.add_argument("--schedule", default="slabs", choices=["fused", "phases", "slabs"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -212,7 +212,7 @@ def main():
 
     Tc, rv, rl = thermo_product()
     p, rho0, T0 = W.droplet(Tc, rv, rl, n=args.n, R=15.0)
-    p["schedule"] = lbm.SCHED_FUSED if args.schedule == "fused" else lbm.SCHED_PHASES
+    p["schedule"] = {"fused": lbm.SCHED_FUSED, "phases": lbm.SCHED_PHASES, "slabs": lbm.SCHED_SLABS}[args.schedule]
     N = p["nx"] * p["ny"] * p["nz"]
     stream = torch.cuda.current_stream()
     rho_d = torch.tensor(rho0.reshape(-1), dtype=torch.float32, device="cuda")

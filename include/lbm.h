@@ -58,7 +58,7 @@ typedef enum {
 typedef enum { LBM_FACE_PERIODIC = 0, LBM_FACE_WALL = 1, LBM_FACE_OPEN = 2 } lbm_face_kind;
 typedef enum { LBM_STORE_F32 = 0, LBM_STORE_F16_SHIFTED = 1, LBM_STORE_BF16_SHIFTED = 2 } lbm_storage;
 typedef enum { LBM_MEM_DEVICE = 0, LBM_MEM_HOST = 1 } lbm_mem;
-typedef enum { LBM_SCHED_FUSED = 0, LBM_SCHED_PHASES = 1 } lbm_schedule;
+typedef enum { LBM_SCHED_FUSED = 0, LBM_SCHED_PHASES = 1, LBM_SCHED_SLABS = 2 } lbm_schedule;
 
 /* Problem statement.  Physical parameters follow the paper's notation. */
 typedef struct lbm_params {
@@ -83,7 +83,9 @@ typedef struct lbm_params {
   double face_rho[6];            /* prescribed density of an open face (Sec. 3.3) */
   double face_theta_deg[6];      /* contact angle of a wall face, Eq. 36 */
   int storage;                   /* lbm_storage */
-  int schedule;                  /* lbm_schedule: one fused launch per step, or one launch per phase */
+  int schedule;                  /* lbm_schedule: one persistent launch per step (FUSED), one launch
+                                    per phase (PHASES), or per phase and z-slab on several streams,
+                                    replayed from a CUDA graph (SLABS) */
 } lbm_params;
 
 /* Creates a context on the current CUDA device and, if rho0 and T0 are not

@@ -38,34 +38,29 @@ __global__ void k_init(Params P, const float* __restrict__ rho0, const float* __
   }
 }
 
+// Phase kernels over the cell range [c0, c1) (whole planes) with grid-stride loops.
 __global__ void k_phaseA(Params P, const float* __restrict__ f, const float* __restrict__ g, Aux X, float* Tout,
-                         int* err) {
+                         int* err, int c0, int c1) {
   int e = 0;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x)
+  for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x)
     phaseA(P, c, f, g, X, Tout, e);
   if (e) atomicOr(err, e);
 }
 
-__global__ void k_phaseB(Params P, Aux X) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x)
-    phaseB(P, c, X);
+__global__ void k_phaseB(Params P, Aux X, int c0, int c1) {
+  for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x) phaseB(P, c, X);
 }
 
 __global__ void __launch_bounds__(256, LBM_PHASEC_MINBLOCKS) k_phaseC19(Params P, const float* __restrict__ fA,
-                                                                        float* fB, Aux X) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x)
+                                                                        float* fB, Aux X, int c0, int c1) {
+  for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x)
     phaseC19(P, c, fA, fB, X);
 }
 
-__global__ void __launch_bounds__(256) k_phaseC7(Params P, const float* __restrict__ gA, float* gB, Aux X) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x)
+__global__ void __launch_bounds__(256) k_phaseC7(Params P, const float* __restrict__ gA, float* gB, Aux X, int c0,
+                                                 int c1) {
+  for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x)
     phaseC7(P, c, gA, gB, X);
-}
-
-__global__ void __launch_bounds__(256, LBM_PHASEC_MINBLOCKS) k_phaseC(Params P, const float* __restrict__ fA, const float* __restrict__ gA, float* fB, float* gB,
-                         Aux X) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x)
-    phaseC(P, c, fA, gA, fB, gB, X);
 }
 
 // one thread per boundary candidate (boundary_candidate enumerates them)
@@ -73,6 +68,18 @@ __global__ void k_phaseD(Params P, float* fB, float* gB, Aux X) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < (int)P.bd_total; k += gridDim.x * blockDim.x) {
     int x, y, z;
     boundary_candidate(P, k, x, y, z);
+    const int m = node_faces(P, x, y, z);
+    if (m) phaseD(P, cell_of(P, x, y, z), x, y, z, m, fB, gB, X);
+  }
+}
+
+// boundary nodes of planes z0 + blockIdx.y
+__global__ void k_phaseD_planes(Params P, float* fB, float* gB, Aux X, int z0) {
+  const int z = z0 + blockIdx.y;
+  const int cnt = boundary_count(P, z);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+    int x, y;
+    boundary_xy(P, z, k, x, y);
     const int m = node_faces(P, x, y, z);
     if (m) phaseD(P, cell_of(P, x, y, z), x, y, z, m, fB, gB, X);
   }
@@ -162,6 +169,31 @@ __global__ void k_sumT(Params P, const float* __restrict__ g, float* T) {
 
 #define LBM_PROF_KINDS 6
 
+// Slab-pipelined schedule: the lattice is cut into slabs of whole z-planes and
+// every phase kernel runs per slab.  Stage (phase, slab) waits only for the
+// stages of neighbouring slabs it reads, through events on a few streams, so
+// the phases of different slabs overlap on the GPU and a slab's populations are
+// read again (phase C) shortly after phase A read them, from L2.  Dependencies
+// (s = slab): B(s) <- A(s-1..s+1); C19(s) <- B(s); C7(s) <- B(s-1..s+1);
+// D(s) <- C19, C7 (s-2..s+2); and across steps A(s) <- D(s-2..s+2) of the
+// previous step (C19, C7 (s-1..s+1) when no slab has boundary nodes).  A run
+// of steps is captured once into a CUDA graph per buffer parity and replayed.
+enum { SPH_A = 0, SPH_B = 1, SPH_C19 = 2, SPH_C7 = 3, SPH_D = 4, SPH_N = 5 };
+constexpr int kMaxSlabStreams = 8;
+
+struct SlabPlan {
+  int nslab = 0;
+  std::vector<int> zb;                 // plane bounds of the slabs (nslab + 1)
+  std::vector<int> order;              // stage codes phase * nslab + slab, topological
+  std::vector<char> has_d;             // slab has boundary nodes
+  int nstreams = 0;
+  cudaStream_t st[kMaxSlabStreams] = {};
+  std::vector<cudaEvent_t> ev;         // per stage code
+  cudaEvent_t fork = nullptr, join[kMaxSlabStreams] = {};
+  int graph_steps = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
 struct lbm_ctx {
   lbm_params hp;
   Params P;
@@ -186,6 +218,7 @@ struct lbm_ctx {
   bool has_state;
   cudaStream_t side;  // second stream for the D3Q7 collision
   cudaEvent_t ev_fork, ev_join;
+  SlabPlan* slabs;    // slab-pipelined schedule (LBM_SCHED_SLABS)
   // kernel timing: event pairs bracketing each launch while profiling is on
   bool profiling;
   struct Ev {
@@ -217,7 +250,8 @@ int check_params(const lbm_params* p) {
   if (N > (1LL << 31) - 1) return LBM_ERR_ARG;
   if (p->vartheta != 0) return LBM_ERR_ARG;
   if (p->storage != LBM_STORE_F32) return LBM_ERR_ARG;
-  if (p->schedule != LBM_SCHED_FUSED && p->schedule != LBM_SCHED_PHASES) return LBM_ERR_ARG;
+  if (p->schedule != LBM_SCHED_FUSED && p->schedule != LBM_SCHED_PHASES && p->schedule != LBM_SCHED_SLABS)
+    return LBM_ERR_ARG;
   if (p->eos_kind != 0 && p->eos_kind != 1) return LBM_ERR_ARG;
   if (!(p->cv > 0) || !(p->wbar > 0 && p->wbar < 1) || !(p->lambda_l > 0) || !(p->lambda_v > 0)) return LBM_ERR_ARG;
   if (p->lambda_l != p->lambda_v && !(p->rho_l > p->rho_v)) return LBM_ERR_ARG;
@@ -376,18 +410,18 @@ void prof_end(lbm_ctx* c, int kind, cudaEvent_t a) {
 int run_macros(lbm_ctx* c, float* Tout) {
   const float* f = c->f[c->cur];
   const float* g = c->g[c->cur];
-  k_phaseA<<<c->grid, kThreads, 0, c->stream>>>(c->P, f, g, c->X, Tout, c->err_d);
-  k_phaseB<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->X);
+  k_phaseA<<<c->grid, kThreads, 0, c->stream>>>(c->P, f, g, c->X, Tout, c->err_d, 0, (int)c->N);
+  k_phaseB<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->X, 0, (int)c->N);
   return cuda_status(cudaGetLastError());
 }
 
 int step_phases(lbm_ctx* c) {
   const int a = c->cur, b = 1 - c->cur;
   cudaEvent_t e = prof_begin(c);
-  k_phaseA<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->f[a], c->g[a], c->X, nullptr, c->err_d);
+  k_phaseA<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->f[a], c->g[a], c->X, nullptr, c->err_d, 0, (int)c->N);
   prof_end(c, 0, e);
   e = prof_begin(c);
-  k_phaseB<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->X);
+  k_phaseB<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->X, 0, (int)c->N);
   prof_end(c, 1, e);
   if (c->bulk_grid > 0) {
     e = prof_begin(c);
@@ -404,14 +438,14 @@ int step_phases(lbm_ctx* c) {
       e7 = ev_get(c);
       cudaEventRecord(e7, c->side);
     }
-    k_phaseC7<<<c->grid, kThreads, 0, c->side>>>(c->P, c->g[a], c->g[b], c->X);
+    k_phaseC7<<<c->grid, kThreads, 0, c->side>>>(c->P, c->g[a], c->g[b], c->X, 0, (int)c->N);
     if (e7) {
       cudaEvent_t e7b = ev_get(c);
       cudaEventRecord(e7b, c->side);
       c->evs->push_back({5, e7, e7b});
     }
     e = prof_begin(c);
-    k_phaseC19<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->f[a], c->f[b], c->X);
+    k_phaseC19<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->f[a], c->f[b], c->X, 0, (int)c->N);
     prof_end(c, 2, e);
     cudaEventRecord(c->ev_join, c->side);
     cudaStreamWaitEvent(c->stream, c->ev_join, 0);
@@ -425,6 +459,256 @@ int step_phases(lbm_ctx* c) {
   return cuda_status(cudaGetLastError());
 }
 
+
+// ----------------------------------------------------------- slab pipeline --
+int slab_of_wrap(const SlabPlan& S, bool zper, int q, bool& ok) {
+  ok = true;
+  if (q < 0 || q >= S.nslab) {
+    if (!zper) {
+      ok = false;
+      return 0;
+    }
+    q = (q % S.nslab + S.nslab) % S.nslab;
+  }
+  return q;
+}
+
+// stage codes this stage waits for within one step
+void slab_deps_within(const SlabPlan& S, bool zper, int ph, int s, std::vector<int>& d) {
+  d.clear();
+  auto add = [&](int p, int q) {
+    bool ok;
+    const int w = slab_of_wrap(S, zper, q, ok);
+    if (!ok) return;
+    if (p == SPH_D && !S.has_d[w]) return;
+    d.push_back(p * S.nslab + w);
+  };
+  if (ph == SPH_B)
+    for (int k = -1; k <= 1; ++k) add(SPH_A, s + k);
+  if (ph == SPH_C19) add(SPH_B, s);
+  if (ph == SPH_C7)
+    for (int k = -1; k <= 1; ++k) add(SPH_B, s + k);
+  if (ph == SPH_D)
+    for (int k = -2; k <= 2; ++k) {
+      add(SPH_C19, s + k);
+      add(SPH_C7, s + k);
+    }
+}
+
+// stages of the previous step that phase A of slab s waits for
+void slab_deps_prev(const SlabPlan& S, bool zper, int s, std::vector<int>& d) {
+  d.clear();
+  for (int k = -2; k <= 2; ++k) {
+    bool ok;
+    const int w = slab_of_wrap(S, zper, s + k, ok);
+    if (!ok) continue;
+    if (S.has_d[w]) {
+      d.push_back(SPH_D * S.nslab + w);
+    } else {
+      d.push_back(SPH_C19 * S.nslab + w);
+      d.push_back(SPH_C7 * S.nslab + w);
+    }
+  }
+}
+
+int env_int(const char* name, int dflt) {
+  const char* e = std::getenv(name);
+  return e ? std::atoi(e) : dflt;
+}
+
+void slab_plan_destroy(SlabPlan* S) {
+  if (!S) return;
+  for (int k = 0; k < 2; ++k)
+    if (S->graph[k]) cudaGraphExecDestroy(S->graph[k]);
+  for (auto e : S->ev)
+    if (e) cudaEventDestroy(e);
+  if (S->fork) cudaEventDestroy(S->fork);
+  for (int i = 0; i < S->nstreams; ++i) {
+    if (S->join[i]) cudaEventDestroy(S->join[i]);
+    if (S->st[i]) {
+      cudaStreamSynchronize(S->st[i]);
+      cudaStreamDestroy(S->st[i]);
+    }
+  }
+  delete S;
+}
+
+int slab_plan_create(lbm_ctx* c) {
+  SlabPlan* S = new (std::nothrow) SlabPlan();
+  if (!S) return LBM_ERR_ARG;
+  const int nz = c->P.nz, plane = c->P.nx * c->P.ny;
+  int sp = env_int("LBM_SLAB_PLANES", 0);
+  if (sp <= 0) sp = std::max(3, (262144 + plane - 1) / plane);  // about 256 Ki cells per slab kernel
+  sp = std::max(3, std::min(sp, nz));
+  S->nslab = std::max(1, nz / sp);
+  for (int s = 0; s <= S->nslab; ++s) S->zb.push_back((int)((long long)nz * s / S->nslab));
+  S->has_d.assign(S->nslab, 0);
+  for (int s = 0; s < S->nslab; ++s)
+    for (int z = S->zb[s]; z < S->zb[s + 1]; ++z)
+      if (plane_has_boundary(c->P, z)) S->has_d[s] = 1;
+  const bool zper = c->P.face_kind[4] == FACE_PERIODIC;
+  // topological order along the diagonal wavefront slab + lag(phase)
+  const int lag[SPH_N] = {0, 1, 2, 2, 4};
+  const int n = S->nslab;
+  std::vector<char> placed(SPH_N * n, 0), exists(SPH_N * n, 1);
+  for (int s = 0; s < n; ++s) exists[SPH_D * n + s] = S->has_d[s];
+  int total = 0;
+  for (int k = 0; k < SPH_N * n; ++k) total += exists[k];
+  std::vector<int> d;
+  while ((int)S->order.size() < total) {
+    int best = -1, bestkey = 1 << 30;
+    for (int ph = SPH_N - 1; ph >= 0; --ph)
+      for (int s = 0; s < n; ++s) {
+        const int id = ph * n + s;
+        if (!exists[id] || placed[id]) continue;
+        slab_deps_within(*S, zper, ph, s, d);
+        bool ready = true;
+        for (int q : d) ready = ready && placed[q];
+        if (!ready) continue;
+        const int key = s + lag[ph];
+        if (key < bestkey) {
+          bestkey = key;
+          best = id;
+        }
+      }
+    if (best < 0) {
+      slab_plan_destroy(S);
+      return LBM_ERR_ARG;  // not reachable: the dependency graph is acyclic
+    }
+    placed[best] = 1;
+    S->order.push_back(best);
+  }
+  S->nstreams = std::max(1, std::min(kMaxSlabStreams, env_int("LBM_SLAB_STREAMS", 8)));
+  bool ok = cudaEventCreateWithFlags(&S->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < S->nstreams && ok; ++i) {
+    ok = cudaStreamCreateWithFlags(&S->st[i], cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&S->join[i], cudaEventDisableTiming) == cudaSuccess;
+  }
+  S->ev.assign(SPH_N * n, nullptr);
+  for (int k = 0; k < SPH_N * n && ok; ++k)
+    if (exists[k]) ok = cudaEventCreateWithFlags(&S->ev[k], cudaEventDisableTiming) == cudaSuccess;
+  S->graph_steps = std::max(0, env_int("LBM_GRAPH_STEPS", 8));
+  if (S->graph_steps & 1) S->graph_steps += 1;  // even: the buffers return to their parity
+  c->slabs = S;
+  return ok ? LBM_OK : LBM_ERR_CUDA;
+}
+
+// Enqueues one time step (buffers cur -> 1-cur) on the slab streams.  `first`:
+// the previous step's per-slab events are not waited for (the caller forked
+// all slab streams from the main stream after that step).
+int slab_enqueue_step(lbm_ctx* c, bool first) {
+  SlabPlan& S = *c->slabs;
+  const int a = c->cur, b = 1 - c->cur;
+  const bool zper = c->P.face_kind[4] == FACE_PERIODIC;
+  const int n = S.nslab, plane = c->P.nx * c->P.ny;
+  std::vector<int> d;
+  for (int code : S.order) {
+    const int ph = code / n, s = code % n;
+    cudaStream_t st = S.st[s % S.nstreams];
+    if (ph == SPH_A) {
+      if (!first) slab_deps_prev(S, zper, s, d);
+      else d.clear();
+    } else {
+      slab_deps_within(S, zper, ph, s, d);
+    }
+    for (int q : d) cudaStreamWaitEvent(st, S.ev[q], 0);
+    const int z0 = S.zb[s], z1 = S.zb[s + 1];
+    const int c0 = z0 * plane, c1 = z1 * plane;
+    const int blocks = std::min(grid_for((long long)(c1 - c0)), 152 * 8);
+    switch (ph) {
+      case SPH_A:
+        k_phaseA<<<blocks, kThreads, 0, st>>>(c->P, c->f[a], c->g[a], c->X, nullptr, c->err_d, c0, c1);
+        break;
+      case SPH_B:
+        k_phaseB<<<blocks, kThreads, 0, st>>>(c->P, c->X, c0, c1);
+        break;
+      case SPH_C19:
+        k_phaseC19<<<blocks, kThreads, 0, st>>>(c->P, c->f[a], c->f[b], c->X, c0, c1);
+        break;
+      case SPH_C7:
+        k_phaseC7<<<blocks, kThreads, 0, st>>>(c->P, c->g[a], c->g[b], c->X, c0, c1);
+        break;
+      default: {
+        int maxcnt = 0;
+        for (int z = z0; z < z1; ++z) {
+          const bool zb = c->P.face_kind[4] != FACE_PERIODIC && (z == 0 || z == c->P.nz - 1);
+          maxcnt = std::max(maxcnt, zb ? plane : c->P.bd_perim);
+        }
+        dim3 gd((unsigned)std::max(1, (maxcnt + kThreads - 1) / kThreads), (unsigned)(z1 - z0));
+        k_phaseD_planes<<<gd, kThreads, 0, st>>>(c->P, c->f[b], c->g[b], c->X, z0);
+      }
+    }
+    cudaEventRecord(S.ev[code], st);
+  }
+  c->cur = b;
+  return cuda_status(cudaGetLastError());
+}
+
+// every slab stream waits for `main`
+void slab_fork(lbm_ctx* c, cudaStream_t main) {
+  SlabPlan& S = *c->slabs;
+  cudaEventRecord(S.fork, main);
+  for (int i = 0; i < S.nstreams; ++i)
+    if (S.st[i] != main) cudaStreamWaitEvent(S.st[i], S.fork, 0);
+}
+
+// `main` waits for every slab stream
+void slab_join(lbm_ctx* c, cudaStream_t main) {
+  SlabPlan& S = *c->slabs;
+  for (int i = 0; i < S.nstreams; ++i) {
+    if (S.st[i] == main) continue;
+    cudaEventRecord(S.join[i], S.st[i]);
+    cudaStreamWaitEvent(main, S.join[i], 0);
+  }
+}
+
+// Captures graph_steps steps starting from the current parity into a graph.
+// The capture runs on the first slab stream (the caller's stream may be the
+// legacy default stream, which cannot be captured); the graph is then launched
+// on the caller's stream.
+int slab_capture(lbm_ctx* c) {
+  SlabPlan& S = *c->slabs;
+  const int parity = c->cur;
+  cudaStream_t cs = S.st[0];
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LBM_ERR_CUDA;
+  slab_fork(c, cs);
+  int st = LBM_OK;
+  for (int k = 0; k < S.graph_steps && st == LBM_OK; ++k) st = slab_enqueue_step(c, k == 0);
+  slab_join(c, cs);
+  const cudaError_t e = cudaStreamEndCapture(cs, &g);
+  c->cur = parity;  // capture recorded the steps without running them
+  if (st != LBM_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return LBM_ERR_CUDA;
+  }
+  const cudaError_t ie = cudaGraphInstantiate(&S.graph[parity], g, 0);
+  cudaGraphDestroy(g);
+  return ie == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+int step_slabs(lbm_ctx* c, int n) {
+  SlabPlan& S = *c->slabs;
+  cudaEvent_t e = prof_begin(c);
+  int st = LBM_OK;
+  int done = 0;
+  if (S.graph_steps > 0) {
+    while (n - done >= S.graph_steps && st == LBM_OK) {
+      if (!S.graph[c->cur]) st = slab_capture(c);
+      if (st != LBM_OK) break;
+      if (cudaGraphLaunch(S.graph[c->cur], c->stream) != cudaSuccess) st = LBM_ERR_CUDA;
+      done += S.graph_steps;  // parity unchanged: graph_steps is even
+    }
+  }
+  if (st == LBM_OK && done < n) {
+    slab_fork(c, c->stream);
+    for (int k = 0; done < n && st == LBM_OK; ++done, ++k) st = slab_enqueue_step(c, k == 0);
+    slab_join(c, c->stream);
+  }
+  prof_end(c, 4, e);
+  return st;
+}
 }  // namespace
 
 extern "C" {
@@ -574,6 +858,13 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
     long long g = (long long)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
     c->bulk_grid = (int)(g < ntiles ? g : ntiles);
   }
+  if (p->schedule == LBM_SCHED_SLABS) {
+    st = slab_plan_create(c);
+    if (st != LBM_OK) {
+      lbm_destroy(c);
+      return st;
+    }
+  }
   st = fused_plan(c->P, &c->plan);
   if (st == LBM_OK && p->schedule == LBM_SCHED_FUSED) st = fused_alloc(&c->plan, c->P, c->stream);
   if (st != LBM_OK) st = st == -1 ? LBM_ERR_ARG : LBM_ERR_CUDA;
@@ -637,6 +928,7 @@ int lbm_set_face_T(lbm_ctx* c, int face, const float* T_face, int mem) {
 int lbm_step(lbm_ctx* c, int n) {
   if (!c || n < 0) return LBM_ERR_ARG;
   if (!c->has_state) return LBM_ERR_STATE;
+  if (c->hp.schedule == LBM_SCHED_SLABS) return n > 0 ? step_slabs(c, n) : LBM_OK;
   for (int s = 0; s < n; ++s) {
     int st;
     if (c->hp.schedule == LBM_SCHED_FUSED) {
@@ -676,6 +968,7 @@ int lbm_profile_read(lbm_ctx* c, long long* launches, double* ms, int nkinds) {
 
 int lbm_launches_per_step(const lbm_ctx* c) {
   if (!c) return 0;
+  if (c->hp.schedule == LBM_SCHED_SLABS) return (int)c->slabs->order.size();
   if (c->hp.schedule == LBM_SCHED_FUSED) return fused_launches(&c->plan);
   return (c->P.bd_total > 0 ? 4 : 3) + (c->bulk_grid > 0 ? 0 : 1);
 }
@@ -772,6 +1065,7 @@ void lbm_destroy(lbm_ctx* c) {
   cudaFreeHost(c->red_h);
   for (int f = 0; f < 6; ++f) cudaFree(c->tface[f]);
   fused_free(&c->plan);
+  slab_plan_destroy(c->slabs);
   if (c->evs) {
     for (auto& e : *c->evs) {
       cudaEventDestroy(e.a);

@@ -18,6 +18,49 @@ struct Aux {
   float *Fx, *Fy, *Fz, *ux, *uy, *uz;  // phase B
 };
 
+// L2 residency: population loads stream through once per kernel (evict-first),
+// while the 44 B/cell of scratch written by phases A and B and read by the
+// next phases (92 MB at 128^3) is kept (evict-last), so that it is served from
+// L2 instead of making a round trip to HBM between kernels.
+struct Hint {
+  unsigned long long stream, keep;
+};
+
+__device__ __forceinline__ Hint make_hint() {
+  Hint h;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(h.stream));
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(h.keep));
+  return h;
+}
+
+// Population stores keep the default policy: a push-streamed warp store is shifted
+// by one cell for x-moving directions and so covers two sectors partially; evicting
+// early would write each sector twice and force an ECC read-modify-write in HBM.
+__device__ __forceinline__ void st_pop(float* a, float v, const Hint&) { *a = v; }
+
+#if defined(LBM_NO_L2HINT)
+__device__ __forceinline__ float ld_pop(const float* a, const Hint&) { return __ldg(a); }
+__device__ __forceinline__ float ld_aux(const float* a, const Hint&) { return *a; }
+__device__ __forceinline__ void st_aux(float* a, float v, const Hint&) { *a = v; }
+#else
+// populations of the previous time step (read-only during the step)
+__device__ __forceinline__ float ld_pop(const float* a, const Hint& h) {
+  float v;
+  asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(h.stream));
+  return v;
+}
+
+// scratch written and read within the step
+__device__ __forceinline__ float ld_aux(const float* a, const Hint& h) {
+  float v;
+  asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(h.keep));
+  return v;
+}
+__device__ __forceinline__ void st_aux(float* a, float v, const Hint& h) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(h.keep));
+}
+#endif
+
 __device__ __forceinline__ void sum19(const float* f, float& rho, float& jx, float& jy, float& jz) {
   rho = ((f[0] + (f[1] + f[2])) + ((f[3] + f[4]) + (f[5] + f[6]))) +
         (((f[7] + f[8]) + (f[9] + f[10])) + ((f[11] + f[12]) + (f[13] + f[14]))) + ((f[15] + f[16]) + (f[17] + f[18]));
@@ -99,11 +142,12 @@ __device__ __forceinline__ bool interior1(const Params& P, int x, int y, int z) 
 __device__ __forceinline__ void phaseA(const Params& P, int c, const float* __restrict__ f,
                                        const float* __restrict__ g, const Aux& X, float* __restrict__ Tout,
                                        int& err) {
+  const Hint h = make_hint();
   float fl[19], gl[7];
 #pragma unroll
-  for (int i = 0; i < 19; ++i) fl[i] = __ldg(f + i * P.N + c);
+  for (int i = 0; i < 19; ++i) fl[i] = ld_pop(f + i * P.N + c, h);
 #pragma unroll
-  for (int i = 0; i < 7; ++i) gl[i] = __ldg(g + i * P.N + c);
+  for (int i = 0; i < 7; ++i) gl[i] = ld_pop(g + i * P.N + c, h);
   float rho, jx, jy, jz;
   sum19(fl, rho, jx, jy, jz);
   const float T = sum7(gl);
@@ -111,11 +155,11 @@ __device__ __forceinline__ void phaseA(const Params& P, int c, const float* __re
   float p, dpdT, psi;
   eos_pr(P, rho, T, p, dpdT);
   if (!psi_of(P, rho, p, psi)) err |= ERRF_PSI;
-  X.rho[c] = rho;
-  X.jx[c] = jx;
-  X.jy[c] = jy;
-  X.jz[c] = jz;
-  X.psi[c] = psi;
+  st_aux(X.rho + c, rho, h);
+  st_aux(X.jx + c, jx, h);
+  st_aux(X.jy + c, jy, h);
+  st_aux(X.jz + c, jz, h);
+  st_aux(X.psi + c, psi, h);
   if (Tout) Tout[c] = T;
 }
 
@@ -136,11 +180,12 @@ __device__ __forceinline__ void phaseB(const Params& P, int c, const Aux& X) {
   Nb nb;
   make_nb(P, x, y, z, nb);
   const float* psi = X.psi;
+  const Hint h = make_hint();
   float sx = 0.f, sy = 0.f, sz = 0.f;
   if (!needs_wetting(P, nb)) {
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
-      const float v = varpi19(i) * psi[c + nb_off_psi(nb, c19x(i), c19y(i), c19z(i))];
+      const float v = varpi19(i) * ld_aux(psi + c + nb_off_psi(nb, c19x(i), c19y(i), c19z(i)), h);
       sx += c19x(i) * v;
       sy += c19y(i) * v;
       sz += c19z(i) * v;
@@ -153,20 +198,22 @@ __device__ __forceinline__ void phaseB(const Params& P, int c, const Aux& X) {
       sz += c19z(i) * v;
     }
   }
-  const float k = -P.G * psi[c];
+  const float k = -P.G * ld_aux(psi + c, h);
   const float Fx = k * sx, Fy = k * sy, Fz = k * sz;
-  X.Fx[c] = Fx;
-  X.Fy[c] = Fy;
-  X.Fz[c] = Fz;
+  st_aux(X.Fx + c, Fx, h);
+  st_aux(X.Fy + c, Fy, h);
+  st_aux(X.Fz + c, Fz, h);
   const int m = P.any_nonperiodic ? node_faces(P, x, y, z) : 0;
-  if (m && on_wall(P, m)) {
-    X.ux[c] = X.uy[c] = X.uz[c] = 0.f;
-  } else {
-    const float ir = rcp(X.rho[c]);
-    X.ux[c] = (X.jx[c] + 0.5f * Fx) * ir;
-    X.uy[c] = (X.jy[c] + 0.5f * Fy) * ir;
-    X.uz[c] = (X.jz[c] + 0.5f * Fz) * ir;
+  float ux = 0.f, uy = 0.f, uz = 0.f;
+  if (!(m && on_wall(P, m))) {
+    const float ir = rcp(ld_aux(X.rho + c, h));
+    ux = (ld_aux(X.jx + c, h) + 0.5f * Fx) * ir;
+    uy = (ld_aux(X.jy + c, h) + 0.5f * Fy) * ir;
+    uz = (ld_aux(X.jz + c, h) + 0.5f * Fz) * ir;
   }
+  st_aux(X.ux + c, ux, h);
+  st_aux(X.uy + c, uy, h);
+  st_aux(X.uz + c, uz, h);
 }
 
 // ------------------------------------------------------------------- C -----
@@ -178,7 +225,8 @@ __device__ __forceinline__ void phaseC19_cell(const Params& P, int c, const floa
   Nb nb;
   make_nb(P, x, y, z, nb);
   const long long N = P.N;
-  const float Fx = X.Fx[c], Fy = X.Fy[c], Fz = X.Fz[c];
+  const Hint h = make_hint();
+  const float Fx = ld_aux(X.Fx + c, h), Fy = ld_aux(X.Fy + c, h), Fz = ld_aux(X.Fz + c, h);
   float rho, jx, jy, jz;
   sum19(fl, rho, jx, jy, jz);
   const int m = P.any_nonperiodic ? node_faces(P, x, y, z) : 0;
@@ -192,9 +240,9 @@ __device__ __forceinline__ void phaseC19_cell(const Params& P, int c, const floa
   for (int i = 0; i < 19; ++i) {
     const int k = nb_kind(nb, c19x(i), c19y(i), c19z(i));
     if (k == 0)
-      fB[i * N + (c + nb_off(nb, c19x(i), c19y(i), c19z(i)))] = fs[i];
+      st_pop(fB + i * N + (c + nb_off(nb, c19x(i), c19y(i), c19z(i))), fs[i], h);
     else if (k & FACE_WALL)
-      fB[opp19(i) * N + c] = fs[i];  // modified bounce-back
+      st_pop(fB + opp19(i) * N + c, fs[i], h);  // modified bounce-back
     // else: leaves through an open face
   }
 }
@@ -209,7 +257,8 @@ __device__ __forceinline__ void phaseC7_cell(const Params& P, int c, const float
   Nb nb;
   make_nb(P, x, y, z, nb);
   const long long N = P.N;
-  const float rho = X.rho[c];
+  const Hint h = make_hint();
+  const float rho = ld_aux(X.rho + c, h);
   const float T = sum7(gl);
   float du = 0.f;
 #pragma unroll
@@ -218,25 +267,25 @@ __device__ __forceinline__ void phaseC7_cell(const Params& P, int c, const float
     if (k & FACE_WALL) continue;  // zero velocity beyond a wall
     const int n = c + nb_off(nb, c19x(i), c19y(i), c19z(i));
     float s = 0.f;
-    if (c19x(i)) s += c19x(i) * X.ux[n];
-    if (c19y(i)) s += c19y(i) * X.uy[n];
-    if (c19z(i)) s += c19z(i) * X.uz[n];
+    if (c19x(i)) s += c19x(i) * ld_aux(X.ux + n, h);
+    if (c19y(i)) s += c19y(i) * ld_aux(X.uy + n, h);
+    if (c19z(i)) s += c19z(i) * ld_aux(X.uz + n, h);
     du += w19(i) * s;
   }
   du *= 3.f;
   float p, dpdT;
   eos_pr(P, rho, T, p, dpdT);
   float gs[7];
-  collide7(P, gl, rho, T, X.ux[c], X.uy[c], X.uz[c], du, dpdT, gs);
+  collide7(P, gl, rho, T, ld_aux(X.ux + c, h), ld_aux(X.uy + c, h), ld_aux(X.uz + c, h), du, dpdT, gs);
   // relaxed streaming: g_i(y) += (g*_i(y - c_i) - g_i(y)) / (rho(y) c_v)
-  gB[c] = gl[0] + (gs[0] - gl[0]) * rcp(rho * P.cv);
+  st_pop(gB + c, gl[0] + (gs[0] - gl[0]) * rcp(rho * P.cv), h);
 #pragma unroll
   for (int i = 1; i < 7; ++i) {
     if (nb_kind(nb, c7x(i), c7y(i), c7z(i))) continue;
     const int yc = c + nb_off(nb, c7x(i), c7y(i), c7z(i));
-    const float gold = __ldg(gA + i * N + yc);
-    const float ry = X.rho[yc];
-    gB[i * N + yc] = gold + (gs[i] - gold) * rcp(ry * P.cv);
+    const float gold = ld_pop(gA + i * N + yc, h);
+    const float ry = ld_aux(X.rho + yc, h);
+    st_pop(gB + i * N + yc, gold + (gs[i] - gold) * rcp(ry * P.cv), h);
   }
 }
 
@@ -249,18 +298,20 @@ __device__ __forceinline__ void phaseC_cell(const Params& P, int c, const float*
 __device__ __forceinline__ void phaseC19(const Params& P, int c, const float* __restrict__ fA, float* fB,
                                          const Aux& X) {
   const long long N = P.N;
+  const Hint h = make_hint();
   float fl[19];
 #pragma unroll
-  for (int i = 0; i < 19; ++i) fl[i] = __ldg(fA + i * N + c);
+  for (int i = 0; i < 19; ++i) fl[i] = ld_pop(fA + i * N + c, h);
   phaseC19_cell(P, c, fl, fB, X);
 }
 
 __device__ __forceinline__ void phaseC7(const Params& P, int c, const float* __restrict__ gA, float* gB,
                                         const Aux& X) {
   const long long N = P.N;
+  const Hint h = make_hint();
   float gl[7];
 #pragma unroll
-  for (int i = 0; i < 7; ++i) gl[i] = __ldg(gA + i * N + c);
+  for (int i = 0; i < 7; ++i) gl[i] = ld_pop(gA + i * N + c, h);
   phaseC7_cell(P, c, gl, gA, gB, X);
 }
 

@@ -21,7 +21,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_PSI_DOMAIN, ERR_TIMEOUT, ERR_STATE = 0
 FACE_PERIODIC, FACE_WALL, FACE_OPEN = 0, 1, 2
 STORE_F32, STORE_F16_SHIFTED, STORE_BF16_SHIFTED = 0, 1, 2
 MEM_DEVICE, MEM_HOST = 0, 1
-SCHED_FUSED, SCHED_PHASES = 0, 1
+SCHED_FUSED, SCHED_PHASES, SCHED_SLABS = 0, 1, 2
 
 _D = ct.c_double
 

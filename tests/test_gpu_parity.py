@@ -92,7 +92,7 @@ def case_params(name, thermo):
                          face_theta_deg=c.get("theta", [90] * 6))
 
 
-@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_PHASES])
+@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_PHASES, lbm.SCHED_SLABS])
 @pytest.mark.parametrize("name", list(CASES))
 def test_one_step_populations_match_oracle(name, schedule, thermo):
     p = case_params(name, thermo)
@@ -191,7 +191,7 @@ def _slab_oracle(thermo):
     return _SLAB
 
 
-@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_PHASES])
+@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_PHASES, lbm.SCHED_SLABS])
 def test_slab_1000_steps_rho_T_match_oracle(schedule, thermo):
     """16x16x64 flat slab between bounce-back walls (bottom T_s + 0.02 T_c, top T_s), W = 2."""
     s = _slab_oracle(thermo)
@@ -201,34 +201,53 @@ def test_slab_1000_steps_rho_T_match_oracle(schedule, thermo):
     assert relerr(gg.sum(0), go.sum(0)) < 1e-3
 
 
-def test_open_droplet_1000_steps_rho_T_match_oracle(thermo):
+_DROP = {}
+
+
+@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_PHASES, lbm.SCHED_SLABS])
+def test_open_droplet_1000_steps_rho_T_match_oracle(schedule, thermo):
     """Evaporating droplet with constant-pressure faces on all six sides (20^3, R = 5)."""
-    p, rho0, T0 = W.droplet(thermo["Tc"], thermo["rho_v"], thermo["rho_l"], n=20, R=5.0, W=3.0, seed=2206)
-    o = Oracle(p)
-    f0, g0 = o.init_state(rho0, T0)
-    f0, g0 = f32(f0), f32(g0)
-    st, fo, go = o.run(f0.astype(np.float64), g0.astype(np.float64), 1000)
-    assert st == 0
-    _, fg, gg = gpu_step(p, f0, g0, 1000)
+    if not _DROP:
+        p, rho0, T0 = W.droplet(thermo["Tc"], thermo["rho_v"], thermo["rho_l"], n=20, R=5.0, W=3.0, seed=2206)
+        o = Oracle(p)
+        f0, g0 = o.init_state(rho0, T0)
+        f0, g0 = f32(f0), f32(g0)
+        st, fo, go = o.run(f0.astype(np.float64), g0.astype(np.float64), 1000)
+        assert st == 0
+        _DROP.update(p=p, f0=f0, g0=g0, fo=fo, go=go)
+    p, f0, g0, fo, go = (_DROP[k] for k in ("p", "f0", "g0", "fo", "go"))
+    _, fg, gg = gpu_step(p, f0, g0, 1000, schedule)
     assert relerr(fg.sum(0), fo.sum(0)) < 1e-3
     assert relerr(gg.sum(0), go.sum(0)) < 1e-3
 
 
+_FULL = {}
+
+
+def _full_size_oracle(cfg, thermo):
+    if cfg not in _FULL:
+        if cfg == "d2_128":
+            p, rho0, T0 = W.droplet(thermo["Tc"], thermo["rho_v"], thermo["rho_l"], n=128, R=15.0)
+        else:
+            p, rho0, T0 = W.sessile(thermo["Tc"], thermo["rho_v"], thermo["rho_l"])
+        o = Oracle(p)
+        f0, g0 = o.init_state(rho0, T0)
+        # a few steps of evolution first so that velocities and forces are developed
+        if cfg == "d2_128":
+            st, f0, g0 = o.run(f0, g0, 2)
+        f0, g0 = f32(f0), f32(g0)
+        st, fo, go = o.step(f0.astype(np.float64), g0.astype(np.float64))
+        assert st == 0
+        _FULL[cfg] = (p, f0, g0, fo, go)
+    return _FULL[cfg]
+
+
+@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_SLABS])
 @pytest.mark.parametrize("cfg", ["d2_128", "sessile_256"])
-def test_full_size_one_step_matches_oracle(cfg, thermo):
-    """One step at the benchmark sizes, in the fused launch the benchmark times."""
-    if cfg == "d2_128":
-        p, rho0, T0 = W.droplet(thermo["Tc"], thermo["rho_v"], thermo["rho_l"], n=128, R=15.0)
-    else:
-        p, rho0, T0 = W.sessile(thermo["Tc"], thermo["rho_v"], thermo["rho_l"])
-    o = Oracle(p)
-    f0, g0 = o.init_state(rho0, T0)
-    # a few steps of evolution first so that velocities and forces are developed
-    st, f0, g0 = o.run(f0, g0, 2) if cfg == "d2_128" else (0, f0, g0)
-    f0, g0 = f32(f0), f32(g0)
-    st, fo, go = o.step(f0.astype(np.float64), g0.astype(np.float64))
-    assert st == 0
-    _, fg, gg = gpu_step(p, f0, g0, 1)
+def test_full_size_one_step_matches_oracle(cfg, schedule, thermo):
+    """One step at the benchmark sizes, in the launch configurations the benchmark times."""
+    p, f0, g0, fo, go = _full_size_oracle(cfg, thermo)
+    _, fg, gg = gpu_step(p, f0, g0, 1, schedule)
     assert pop_err(fg, fo, thermo) < 1e-5
     assert pop_err(gg, go, thermo) < 1e-5
 
