@@ -36,6 +36,15 @@ from paper_2206_00946_gb300 import workloads as W  # noqa: E402
 METRIC = "fused D3Q19+D3Q7 MLUPS"
 UNIT = "MLUPS"
 BYTES_PER_LU = 208  # f and g (19 + 7 FP32 populations) read once and written once per lattice update
+STORAGE = {"f32": (0, 4), "f16": (1, 2), "bf16": (2, 2)}  # lbm_storage code, bytes per stored population
+
+
+def kernel_alg_bytes(kernel: str, esize: int):
+    """Algorithmic bytes per cell of one launch of `kernel` (populations it must read and write once)."""
+    return {"phaseC": 2 * 19 * esize,   # D3Q19 collide + push: f read and written
+            "phaseC7": 2 * 7 * esize,   # D3Q7 collide + relaxed push: g read and written
+            "phaseA": 26 * esize,       # macroscopic fields: f and g read
+            "fused": 2 * 26 * esize}.get(kernel)
 WORKLOAD = "d2-law droplet 128^3, R=15, W=5, open (Zou-He) faces rho_b=rho_v, T_faces=T_c, seed 2206"
 
 
@@ -128,6 +137,19 @@ def dist_env():
     return rank, world, local
 
 
+def job_throughput(dist, local_s: float, units_per_rank: int, device="cpu"):
+    """Whole-job throughput of weakly scaled replicas: every rank processed
+    units_per_rank units in local_s seconds; the job took the slowest rank's
+    time.  Returns (max seconds over ranks, total units / that time)."""
+    world = dist.get_world_size() if dist else 1
+    if dist:
+        import torch
+        t = torch.tensor([local_s], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        local_s = float(t.item())
+    return local_s, world * units_per_rank / local_s
+
+
 def thermo_product():
     """T_c and the coexistence densities from the library's host helpers (not the oracle)."""
     from paper_2206_00946_gb300 import lbm
@@ -193,6 +215,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128, help="lattice side (the workload is 128)")
     ap.add_argument("--schedule", default="slabs", choices=["fused", "phases", "slabs"])
+    ap.add_argument("--storage", default="f32", choices=list(STORAGE))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -213,6 +236,8 @@ def main():
     Tc, rv, rl = thermo_product()
     p, rho0, T0 = W.droplet(Tc, rv, rl, n=args.n, R=15.0)
     p["schedule"] = {"fused": lbm.SCHED_FUSED, "phases": lbm.SCHED_PHASES, "slabs": lbm.SCHED_SLABS}[args.schedule]
+    p["storage"], esize = STORAGE[args.storage]
+    step_bytes = 26 * 2 * esize  # algorithmic bytes per lattice update in this storage
     N = p["nx"] * p["ny"] * p["nz"]
     stream = torch.cuda.current_stream()
     rho_d = torch.tensor(rho0.reshape(-1), dtype=torch.float32, device="cuda")
@@ -244,22 +269,28 @@ def main():
     st = lat.lbm_sync()
     if st != lbm.OK:
         raise SystemExit(f"timed run failed: {lbm.lbm_status_string(st)}")
-    t_ms = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
-    ms_max = float(t_ms.item())
-    ms_step = ms_max / args.steps
-    value = world * N * args.steps / (ms_max * 1e-3) / 1e6
+    dev = "cuda" if (dist and dist.get_backend() == "nccl") else "cpu"
+    s_max, lups = job_throughput(dist, ms * 1e-3, N * args.steps, dev)
+    ms_step = s_max * 1e3 / args.steps
+    value = lups / 1e6
 
-    # per-kernel device time from the library's launch timing (CUDA events on the launch stream)
+    lat.close()
+
+    # Per-kernel device time from the library's launch timing (CUDA events on each
+    # kernel's launch stream).  The slab schedule runs every phase as many
+    # concurrent sub-range launches, so its kernels are timed here in the phase
+    # schedule: the same kernels, one launch per phase over the whole lattice.
     nl = min(args.steps, 200)
-    lat.lbm_profile(True)
-    lat.lbm_step(nl)
-    prof = lat.lbm_profile_read()
-    lat.lbm_profile(False)
+    q = dict(p, schedule=p["schedule"] if args.schedule == "fused" else lbm.SCHED_PHASES)
+    latp = lbm.Lattice(q, rho_d, T_d, stream=stream.cuda_stream)
+    latp.lbm_step(args.warmup)
+    latp.lbm_profile(True)
+    latp.lbm_step(nl)
+    prof = latp.lbm_profile_read()
+    latp.lbm_profile(False)
+    latp.close()
     dom = max(prof, key=lambda k: prof[k][1])
     per_launch_ms = prof[dom][1] / prof[dom][0]
-    lat.close()
 
     # end to end through the C ABI with host buffers: init from host fields, K steps, macros to host
     rho_h = np.ascontiguousarray(rho0.reshape(-1), dtype=np.float32)
@@ -276,10 +307,7 @@ def main():
     lat2.close()
     if st2 != lbm.OK:
         raise SystemExit(f"e2e run failed: {lbm.lbm_status_string(st2)}")
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * N * args.steps / float(e2e_t.item()) / 1e6
+    e2e_value = job_throughput(dist, e2e_s, N * args.steps, dev)[1] / 1e6
 
     if rank != 0:
         if dist:
@@ -289,10 +317,10 @@ def main():
     pk = peaks()
     peak = pk.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in pk else "fallback"
-    # the collide+stream kernel (alone, or inside the fused step) reads and writes every population once
-    achieved = BYTES_PER_LU * N / (per_launch_ms * 1e-3) / 1e9
+    alg = kernel_alg_bytes(dom, esize)
+    achieved = alg * N / (per_launch_ms * 1e-3) / 1e9 if alg else None
     digest = src_digest()
-    traffic = ncu_traffic(dom, digest, N)
+    traffic = ncu_traffic(dom + ("" if args.storage == "f32" else "_" + args.storage), digest, N)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         steps_cpu = 2
@@ -305,13 +333,18 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if args.n == 128 else WORKLOAD.replace("128^3", f"{args.n}^3"),
                    "cells": N, "schedule": args.schedule, "parallelism": f"replicas x{world}",
-                   "l2": f"inputs larger than L2: {2 * 26 * 4 * N / 1e6:.0f} MB of double-buffered populations"},
+                   "storage": {"f32": "f32", "f16": "f16 shifted by w_i rho_ref / w_i T_ref",
+                               "bf16": "bf16 shifted by w_i rho_ref / w_i T_ref"}[args.storage],
+                   "l2": f"inputs larger than L2: {2 * 26 * esize * N / 1e6:.0f} MB of double-buffered populations"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
+                     "frac": achieved / peak if achieved else None, "traffic": traffic,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)",
-                     "bytes_per_lu": BYTES_PER_LU, "kernel": dom, "per_launch_ms": per_launch_ms,
+                     "kernel": dom, "alg_bytes_per_cell": alg, "per_launch_ms": per_launch_ms,
+                     "kernel_timing": "CUDA events on the kernel's stream, phase schedule, whole-lattice launches",
                      "kernel_src_sha": digest,
-                     "step_effective_GBs": BYTES_PER_LU * N / (ms_step * 1e-3) / 1e9,
+                     "step_bytes_per_lu": step_bytes,
+                     "step_effective_GBs": step_bytes * N / (ms_step * 1e-3) / 1e9,
+                     "step_frac": step_bytes * N / (ms_step * 1e-3) / 1e9 / peak,
                      "kernels": {k: {"launches": v[0], "ms_per_launch": v[1] / v[0],
                                      "share": v[1] / sum(w[1] for w in prof.values())} for k, v in prof.items()}},
         "cpu_baseline": cpu,

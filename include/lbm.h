@@ -82,7 +82,11 @@ typedef struct lbm_params {
   double face_T[6];              /* Dirichlet temperature of every non-periodic face (Sec. 3.1) */
   double face_rho[6];            /* prescribed density of an open face (Sec. 3.3) */
   double face_theta_deg[6];      /* contact angle of a wall face, Eq. 36 */
-  int storage;                   /* lbm_storage */
+  int storage;                   /* lbm_storage: FP32 populations, or 16-bit IEEE half / bfloat16
+                                    holding f_i - w_i rho_ref and g_i - w_i T_ref (all arithmetic in FP32;
+                                    the FUSED schedule supports FP32 only) */
+  double store_rho_ref;          /* shift rho_ref of the 16-bit storage (e.g. rho_v) */
+  double store_T_ref;            /* shift T_ref of the 16-bit storage (e.g. the mean temperature) */
   int schedule;                  /* lbm_schedule: one persistent launch per step (FUSED), one launch
                                     per phase (PHASES), or per phase and z-slab on several streams,
                                     replayed from a CUDA graph (SLABS) */
@@ -99,6 +103,20 @@ int lbm_set_state(lbm_ctx* ctx, const float* f, const float* g, int mem);
 
 /* Copies the current populations out (mem); synchronises the stream. */
 int lbm_get_state(lbm_ctx* ctx, float* f, float* g, int mem);
+
+/* Checkpoint / restore of the time-stepping state (the populations in the
+ * context's storage format), e.g. for recomputation between checkpoints.
+ * The image is a 256-byte header (magic, lattice size, storage mode and
+ * shifts) followed by f and g; lbm_checkpoint_bytes gives its size.
+ * lbm_checkpoint writes the image to dst (mem), synchronises the stream and
+ * returns the error flags like lbm_get_state.  lbm_restore reads an image
+ * written by a context with the same lattice size, storage mode and shifts
+ * (else LBM_ERR_ARG) and makes it the current state; device images are
+ * copied asynchronously, host images before it returns.  The caller owns
+ * the image buffer. */
+long long lbm_checkpoint_bytes(const lbm_ctx* ctx);
+int lbm_checkpoint(lbm_ctx* ctx, void* dst, int mem);
+int lbm_restore(lbm_ctx* ctx, const void* src, int mem);
 
 /* Per-node Dirichlet temperature of non-periodic face `face` (Sec. 3.1): an
  * array over the face's two tangential coordinates, lower axis fastest

@@ -25,22 +25,43 @@ constexpr int kBulkSmem = 2 * 26 * kBulkTile * 4 + 2 * 8;           // two stage
 #define LBM_PHASEC_MINBLOCKS 4
 #endif
 
-__global__ void k_init(Params P, const float* __restrict__ rho0, const float* __restrict__ T0, float* f, float* g) {
+template <typename T>
+__global__ void k_init(Params P, const float* __restrict__ rho0, const float* __restrict__ T0, T* f, T* g) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x) {
     float fe[19];
     feq19(rho0[c], 0.f, 0.f, 0.f, fe);
 #pragma unroll
-    for (int i = 0; i < 19; ++i) f[i * P.N + c] = fe[i];
-    const float T = T0[c];
-    g[c] = (1.f - P.wbar) * T;
+    for (int i = 0; i < 19; ++i) PopStore<T>::st(f + i * P.N + c, fe[i], fbase(P, i));
+    const float Tc = T0[c];
+    PopStore<T>::st(g + c, (1.f - P.wbar) * Tc, gbase(P, 0));
 #pragma unroll
-    for (int i = 1; i < 7; ++i) g[i * P.N + c] = P.wbar * (1.f / 6.f) * T;
+    for (int i = 1; i < 7; ++i) PopStore<T>::st(g + i * P.N + c, P.wbar * (1.f / 6.f) * Tc, gbase(P, i));
+  }
+}
+
+// float populations (state exchanged with the caller) <-> storage, q directions
+template <typename T>
+__global__ void k_store(Params P, const float* __restrict__ src, T* dst, int q, int is_g) {
+  const long long n = (long long)q * P.N;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(k / P.N);
+    PopStore<T>::st(dst + k, src[k], is_g ? gbase(P, i) : fbase(P, i));
+  }
+}
+
+template <typename T>
+__global__ void k_load(Params P, const T* __restrict__ src, float* dst, int q, int is_g) {
+  const long long n = (long long)q * P.N;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(k / P.N);
+    dst[k] = PopStore<T>::ld_plain(src + k, is_g ? gbase(P, i) : fbase(P, i));
   }
 }
 
 // Phase kernels over the cell range [c0, c1) (whole planes) with grid-stride loops.
-__global__ void k_phaseA(Params P, const float* __restrict__ f, const float* __restrict__ g, Aux X, float* Tout,
-                         int* err, int c0, int c1) {
+template <typename T>
+__global__ void k_phaseA(Params P, const T* __restrict__ f, const T* __restrict__ g, Aux X, float* Tout, int* err,
+                         int c0, int c1) {
   int e = 0;
   for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x)
     phaseA(P, c, f, g, X, Tout, e);
@@ -51,20 +72,22 @@ __global__ void k_phaseB(Params P, Aux X, int c0, int c1) {
   for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x) phaseB(P, c, X);
 }
 
-__global__ void __launch_bounds__(256, LBM_PHASEC_MINBLOCKS) k_phaseC19(Params P, const float* __restrict__ fA,
-                                                                        float* fB, Aux X, int c0, int c1) {
+template <typename T>
+__global__ void __launch_bounds__(256, LBM_PHASEC_MINBLOCKS) k_phaseC19(Params P, const T* __restrict__ fA, T* fB,
+                                                                        Aux X, int c0, int c1) {
   for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x)
     phaseC19(P, c, fA, fB, X);
 }
 
-__global__ void __launch_bounds__(256) k_phaseC7(Params P, const float* __restrict__ gA, float* gB, Aux X, int c0,
-                                                 int c1) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_phaseC7(Params P, const T* __restrict__ gA, T* gB, Aux X, int c0, int c1) {
   for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x)
     phaseC7(P, c, gA, gB, X);
 }
 
 // one thread per boundary candidate (boundary_candidate enumerates them)
-__global__ void k_phaseD(Params P, float* fB, float* gB, Aux X) {
+template <typename T>
+__global__ void k_phaseD(Params P, T* fB, T* gB, Aux X) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < (int)P.bd_total; k += gridDim.x * blockDim.x) {
     int x, y, z;
     boundary_candidate(P, k, x, y, z);
@@ -74,7 +97,8 @@ __global__ void k_phaseD(Params P, float* fB, float* gB, Aux X) {
 }
 
 // boundary nodes of planes z0 + blockIdx.y
-__global__ void k_phaseD_planes(Params P, float* fB, float* gB, Aux X, int z0) {
+template <typename T>
+__global__ void k_phaseD_planes(Params P, T* fB, T* gB, Aux X, int z0) {
   const int z = z0 + blockIdx.y;
   const int cnt = boundary_count(P, z);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
@@ -86,14 +110,15 @@ __global__ void k_phaseD_planes(Params P, float* fB, float* gB, Aux X, int z0) {
 }
 
 // FP64 block reduction: mass, sum rho cv T, droplet volume, non-finite count.
-__global__ void k_reduce(Params P, const float* __restrict__ f, const float* __restrict__ g, double* partial) {
+template <typename S>
+__global__ void k_reduce(Params P, const S* __restrict__ f, const S* __restrict__ g, double* partial) {
   double a[4] = {0, 0, 0, 0};
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x) {
     float fl[19], gl[7];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) fl[i] = __ldg(f + i * P.N + c);
+    for (int i = 0; i < 19; ++i) fl[i] = PopStore<S>::ld_plain(f + i * P.N + c, fbase(P, i));
 #pragma unroll
-    for (int i = 0; i < 7; ++i) gl[i] = __ldg(g + i * P.N + c);
+    for (int i = 0; i < 7; ++i) gl[i] = PopStore<S>::ld_plain(g + i * P.N + c, gbase(P, i));
     float rho, jx, jy, jz;
     sum19(fl, rho, jx, jy, jz);
     const float T = sum7(gl);
@@ -156,11 +181,12 @@ __global__ void k_fill(float* p, long long n, float v) {
     p[k] = v;
 }
 
-__global__ void k_sumT(Params P, const float* __restrict__ g, float* T) {
+template <typename S>
+__global__ void k_sumT(Params P, const S* __restrict__ g, float* T) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x) {
     float gl[7];
 #pragma unroll
-    for (int i = 0; i < 7; ++i) gl[i] = g[i * P.N + c];
+    for (int i = 0; i < 7; ++i) gl[i] = PopStore<S>::ld_plain(g + i * P.N + c, gbase(P, i));
     T[c] = sum7(gl);
   }
 }
@@ -200,8 +226,9 @@ struct lbm_ctx {
   cudaStream_t stream;
   int device;
   long long N;
-  float* f[2];
-  float* g[2];
+  void* f[2];  // populations, element type per storage mode
+  void* g[2];
+  size_t esize;
   int cur;
   float* aux;
   Aux X;
@@ -249,7 +276,9 @@ int check_params(const lbm_params* p) {
   const long long N = (long long)p->nx * p->ny * p->nz;
   if (N > (1LL << 31) - 1) return LBM_ERR_ARG;
   if (p->vartheta != 0) return LBM_ERR_ARG;
-  if (p->storage != LBM_STORE_F32) return LBM_ERR_ARG;
+  if (p->storage != LBM_STORE_F32 && p->storage != LBM_STORE_F16_SHIFTED && p->storage != LBM_STORE_BF16_SHIFTED)
+    return LBM_ERR_ARG;
+  if (p->storage != LBM_STORE_F32 && p->schedule == LBM_SCHED_FUSED) return LBM_ERR_ARG;  // FP32 only
   if (p->schedule != LBM_SCHED_FUSED && p->schedule != LBM_SCHED_PHASES && p->schedule != LBM_SCHED_SLABS)
     return LBM_ERR_ARG;
   if (p->eos_kind != 0 && p->eos_kind != 1) return LBM_ERR_ARG;
@@ -316,6 +345,21 @@ Params make_device_params(const lbm_params& p) {
   P.rho_v = (float)p.rho_v;
   P.inv_drho = (p.rho_l > p.rho_v) ? (float)(1.0 / (p.rho_l - p.rho_v)) : 0.f;
   P.lam_uniform = p.lambda_l == p.lambda_v;
+  // shifts of the 16-bit storage; defaults: rho_v, and the mean Dirichlet face temperature
+  // (else 0.9 T_c for the Peng-Robinson fluid, else 1)
+  double tref = p.store_T_ref;
+  if (!(tref > 0)) {
+    double s = 0;
+    int n = 0;
+    for (int f = 0; f < 6; ++f)
+      if (p.face_kind[f] != LBM_FACE_PERIODIC) {
+        s += p.face_T[f];
+        ++n;
+      }
+    tref = n ? s / n : (p.eos_kind == 0 ? 0.9 * lbm_Tc(&p) : 1.0);
+  }
+  P.rho_ref = (float)(p.store_rho_ref > 0 ? p.store_rho_ref : (p.rho_v > 0 ? p.rho_v : 0.0));
+  P.T_ref = (float)tref;
   P.any_nonperiodic = 0;
   for (int f = 0; f < 6; ++f) {
     P.face_kind[f] = p.face_kind[f];
@@ -406,58 +450,78 @@ void prof_end(lbm_ctx* c, int kind, cudaEvent_t a) {
   c->evs->push_back({kind, a, b});
 }
 
+template <typename T>
+T* fbuf(lbm_ctx* c, int k) {
+  return static_cast<T*>(c->f[k]);
+}
+template <typename T>
+T* gbuf(lbm_ctx* c, int k) {
+  return static_cast<T*>(c->g[k]);
+}
+
+// calls FN<T>(args...) with T the population storage type of the context
+#define LBM_WITH_STORAGE(c, FN, ...)                                                             \
+  ((c)->hp.storage == LBM_STORE_F16_SHIFTED    ? FN<__half>(__VA_ARGS__)                          \
+   : (c)->hp.storage == LBM_STORE_BF16_SHIFTED ? FN<__nv_bfloat16>(__VA_ARGS__)                   \
+                                               : FN<float>(__VA_ARGS__))
+
 // Phases A and B on the current state (macros of time t); returns launch status.
-int run_macros(lbm_ctx* c, float* Tout) {
-  const float* f = c->f[c->cur];
-  const float* g = c->g[c->cur];
-  k_phaseA<<<c->grid, kThreads, 0, c->stream>>>(c->P, f, g, c->X, Tout, c->err_d, 0, (int)c->N);
+template <typename T>
+int run_macros_t(lbm_ctx* c, float* Tout) {
+  k_phaseA<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, c->cur), gbuf<T>(c, c->cur), c->X, Tout,
+                                                   c->err_d, 0, (int)c->N);
   k_phaseB<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->X, 0, (int)c->N);
   return cuda_status(cudaGetLastError());
 }
 
-int step_phases(lbm_ctx* c) {
+int run_macros(lbm_ctx* c, float* Tout) { return LBM_WITH_STORAGE(c, run_macros_t, c, Tout); }
+
+template <typename T>
+int step_phases_t(lbm_ctx* c) {
   const int a = c->cur, b = 1 - c->cur;
   cudaEvent_t e = prof_begin(c);
-  k_phaseA<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->f[a], c->g[a], c->X, nullptr, c->err_d, 0, (int)c->N);
+  k_phaseA<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, a), gbuf<T>(c, a), c->X, nullptr, c->err_d, 0,
+                                                   (int)c->N);
   prof_end(c, 0, e);
   e = prof_begin(c);
   k_phaseB<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->X, 0, (int)c->N);
   prof_end(c, 1, e);
-  if (c->bulk_grid > 0) {
+  if (c->bulk_grid > 0) {  // FP32 storage only
     e = prof_begin(c);
-    k_phaseC_bulk<kBulkTile><<<c->bulk_grid, kBulkTile, kBulkSmem, c->stream>>>(c->P, c->f[a], c->g[a], c->f[b],
-                                                                               c->g[b], c->X, c->err_d);
+    k_phaseC_bulk<kBulkTile><<<c->bulk_grid, kBulkTile, kBulkSmem, c->stream>>>(
+        c->P, fbuf<float>(c, a), gbuf<float>(c, a), fbuf<float>(c, b), gbuf<float>(c, b), c->X, c->err_d);
     prof_end(c, 2, e);
   } else {
     // the D3Q19 and D3Q7 collisions are independent: the D3Q7 kernel (gather-bound)
-    // runs on a side stream next to the D3Q19 kernel (arithmetic- and bandwidth-bound)
-    cudaEventRecord(c->ev_fork, c->stream);
-    cudaStreamWaitEvent(c->side, c->ev_fork, 0);
-    cudaEvent_t e7 = nullptr;
-    if (c->profiling) {
-      e7 = ev_get(c);
-      cudaEventRecord(e7, c->side);
-    }
-    k_phaseC7<<<c->grid, kThreads, 0, c->side>>>(c->P, c->g[a], c->g[b], c->X, 0, (int)c->N);
-    if (e7) {
-      cudaEvent_t e7b = ev_get(c);
-      cudaEventRecord(e7b, c->side);
-      c->evs->push_back({5, e7, e7b});
+    // runs on a side stream next to the D3Q19 kernel (arithmetic- and bandwidth-bound).
+    // While profiling, both run on the context stream one after the other, so that
+    // each event pair brackets one kernel running alone.
+    cudaStream_t s7 = c->profiling ? c->stream : c->side;
+    if (!c->profiling) {
+      cudaEventRecord(c->ev_fork, c->stream);
+      cudaStreamWaitEvent(c->side, c->ev_fork, 0);
     }
     e = prof_begin(c);
-    k_phaseC19<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->f[a], c->f[b], c->X, 0, (int)c->N);
+    k_phaseC19<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, a), fbuf<T>(c, b), c->X, 0, (int)c->N);
     prof_end(c, 2, e);
-    cudaEventRecord(c->ev_join, c->side);
-    cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    e = prof_begin(c);
+    k_phaseC7<T><<<c->grid, kThreads, 0, s7>>>(c->P, gbuf<T>(c, a), gbuf<T>(c, b), c->X, 0, (int)c->N);
+    prof_end(c, 5, e);
+    if (!c->profiling) {
+      cudaEventRecord(c->ev_join, c->side);
+      cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    }
   }
   if (c->P.bd_total > 0) {
     e = prof_begin(c);
-    k_phaseD<<<grid_for(c->P.bd_total), kThreads, 0, c->stream>>>(c->P, c->f[b], c->g[b], c->X);
+    k_phaseD<T><<<grid_for(c->P.bd_total), kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, b), gbuf<T>(c, b), c->X);
     prof_end(c, 3, e);
   }
   c->cur = b;
   return cuda_status(cudaGetLastError());
 }
+
+int step_phases(lbm_ctx* c) { return LBM_WITH_STORAGE(c, step_phases_t, c); }
 
 
 // ----------------------------------------------------------- slab pipeline --
@@ -596,7 +660,8 @@ int slab_plan_create(lbm_ctx* c) {
 // Enqueues one time step (buffers cur -> 1-cur) on the slab streams.  `first`:
 // the previous step's per-slab events are not waited for (the caller forked
 // all slab streams from the main stream after that step).
-int slab_enqueue_step(lbm_ctx* c, bool first) {
+template <typename T>
+int slab_enqueue_step_t(lbm_ctx* c, bool first) {
   SlabPlan& S = *c->slabs;
   const int a = c->cur, b = 1 - c->cur;
   const bool zper = c->P.face_kind[4] == FACE_PERIODIC;
@@ -617,16 +682,16 @@ int slab_enqueue_step(lbm_ctx* c, bool first) {
     const int blocks = std::min(grid_for((long long)(c1 - c0)), 152 * 8);
     switch (ph) {
       case SPH_A:
-        k_phaseA<<<blocks, kThreads, 0, st>>>(c->P, c->f[a], c->g[a], c->X, nullptr, c->err_d, c0, c1);
+        k_phaseA<T><<<blocks, kThreads, 0, st>>>(c->P, fbuf<T>(c, a), gbuf<T>(c, a), c->X, nullptr, c->err_d, c0, c1);
         break;
       case SPH_B:
         k_phaseB<<<blocks, kThreads, 0, st>>>(c->P, c->X, c0, c1);
         break;
       case SPH_C19:
-        k_phaseC19<<<blocks, kThreads, 0, st>>>(c->P, c->f[a], c->f[b], c->X, c0, c1);
+        k_phaseC19<T><<<blocks, kThreads, 0, st>>>(c->P, fbuf<T>(c, a), fbuf<T>(c, b), c->X, c0, c1);
         break;
       case SPH_C7:
-        k_phaseC7<<<blocks, kThreads, 0, st>>>(c->P, c->g[a], c->g[b], c->X, c0, c1);
+        k_phaseC7<T><<<blocks, kThreads, 0, st>>>(c->P, gbuf<T>(c, a), gbuf<T>(c, b), c->X, c0, c1);
         break;
       default: {
         int maxcnt = 0;
@@ -635,7 +700,7 @@ int slab_enqueue_step(lbm_ctx* c, bool first) {
           maxcnt = std::max(maxcnt, zb ? plane : c->P.bd_perim);
         }
         dim3 gd((unsigned)std::max(1, (maxcnt + kThreads - 1) / kThreads), (unsigned)(z1 - z0));
-        k_phaseD_planes<<<gd, kThreads, 0, st>>>(c->P, c->f[b], c->g[b], c->X, z0);
+        k_phaseD_planes<T><<<gd, kThreads, 0, st>>>(c->P, fbuf<T>(c, b), gbuf<T>(c, b), c->X, z0);
       }
     }
     cudaEventRecord(S.ev[code], st);
@@ -643,6 +708,8 @@ int slab_enqueue_step(lbm_ctx* c, bool first) {
   c->cur = b;
   return cuda_status(cudaGetLastError());
 }
+
+int slab_enqueue_step(lbm_ctx* c, bool first) { return LBM_WITH_STORAGE(c, slab_enqueue_step_t, c, first); }
 
 // every slab stream waits for `main`
 void slab_fork(lbm_ctx* c, cudaStream_t main) {
@@ -709,6 +776,41 @@ int step_slabs(lbm_ctx* c, int n) {
   prof_end(c, 4, e);
   return st;
 }
+}  // namespace
+
+namespace {
+
+// Moves f/g (float, caller memory) into or out of 16-bit shifted storage through a
+// temporary device buffer (not on the time-stepping path).
+template <typename T>
+int convert_state_t(lbm_ctx* c, float* f, float* g, int mem, bool in) {
+  const long long N = c->N;
+  float* tmp = nullptr;
+  if (cudaMalloc(&tmp, sizeof(float) * 19 * N) != cudaSuccess) return LBM_ERR_CUDA;
+  int st = LBM_OK;
+  const int blocks = grid_for(19 * N);
+  float* user[2] = {f, g};
+  const int q[2] = {19, 7};
+  void* buf[2] = {c->f[c->cur], c->g[c->cur]};
+  for (int k = 0; k < 2 && st == LBM_OK; ++k) {
+    if (!user[k]) continue;
+    if (in) {
+      st = copy_in(tmp, user[k], q[k] * N, mem, c->stream);
+      if (!st) k_store<T><<<blocks, kThreads, 0, c->stream>>>(c->P, tmp, static_cast<T*>(buf[k]), q[k], k);
+    } else {
+      k_load<T><<<blocks, kThreads, 0, c->stream>>>(c->P, static_cast<const T*>(buf[k]), tmp, q[k], k);
+      st = copy_out(user[k], tmp, q[k] * N, mem, c->stream);
+    }
+    if (!st) st = cuda_status(cudaStreamSynchronize(c->stream));
+  }
+  cudaFree(tmp);
+  return st;
+}
+
+int convert_state(lbm_ctx* c, float* f, float* g, int mem, bool in) {
+  return LBM_WITH_STORAGE(c, convert_state_t, c, f, g, mem, in);
+}
+
 }  // namespace
 
 extern "C" {
@@ -811,12 +913,13 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
   c->stream = (cudaStream_t)stream;
   c->N = c->P.N;
   c->grid = grid_for(c->N);
+  c->esize = p->storage == LBM_STORE_F32 ? sizeof(float) : 2;
   cudaGetDevice(&c->device);
   const long long N = c->N;
   bool ok = true;
   for (int k = 0; k < 2; ++k) {
-    ok = ok && cudaMalloc(&c->f[k], sizeof(float) * 19 * N) == cudaSuccess;
-    ok = ok && cudaMalloc(&c->g[k], sizeof(float) * 7 * N) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->f[k], c->esize * 19 * N) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->g[k], c->esize * 7 * N) == cudaSuccess;
   }
   ok = ok && cudaMalloc(&c->aux, sizeof(float) * 11 * N) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
@@ -849,7 +952,7 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
   }
   // bulk-staged phase C: opt-in (LBM_BULK=1); measured slower than the unstaged kernel on
   // GB300 because phase C is bound by its neighbour gathers, not by the population loads
-  if (N % 4 == 0 && std::getenv("LBM_BULK") != nullptr) {
+  if (N % 4 == 0 && p->storage == LBM_STORE_F32 && std::getenv("LBM_BULK") != nullptr) {
     int per_sm = 0, sms = 0;
     cudaFuncSetAttribute(k_phaseC_bulk<kBulkTile>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBulkSmem);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -885,7 +988,13 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
       r = (float*)rho0;
       t = (float*)T0;
     }
-    k_init<<<c->grid, kThreads, 0, c->stream>>>(c->P, r, t, c->f[0], c->g[0]);
+    if (p->storage == LBM_STORE_F16_SHIFTED)
+      k_init<__half><<<c->grid, kThreads, 0, c->stream>>>(c->P, r, t, fbuf<__half>(c, 0), gbuf<__half>(c, 0));
+    else if (p->storage == LBM_STORE_BF16_SHIFTED)
+      k_init<__nv_bfloat16><<<c->grid, kThreads, 0, c->stream>>>(c->P, r, t, fbuf<__nv_bfloat16>(c, 0),
+                                                                 gbuf<__nv_bfloat16>(c, 0));
+    else
+      k_init<float><<<c->grid, kThreads, 0, c->stream>>>(c->P, r, t, fbuf<float>(c, 0), gbuf<float>(c, 0));
     if (cudaGetLastError() != cudaSuccess) {
       lbm_destroy(c);
       return LBM_ERR_CUDA;
@@ -898,8 +1007,13 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
 
 int lbm_set_state(lbm_ctx* c, const float* f, const float* g, int mem) {
   if (!c || !f || !g) return LBM_ERR_ARG;
-  int st = copy_in(c->f[c->cur], f, 19 * c->N, mem, c->stream);
-  if (!st) st = copy_in(c->g[c->cur], g, 7 * c->N, mem, c->stream);
+  int st = LBM_OK;
+  if (c->hp.storage == LBM_STORE_F32) {
+    st = copy_in(fbuf<float>(c, c->cur), f, 19 * c->N, mem, c->stream);
+    if (!st) st = copy_in(gbuf<float>(c, c->cur), g, 7 * c->N, mem, c->stream);
+  } else {
+    st = convert_state(c, const_cast<float*>(f), const_cast<float*>(g), mem, true);
+  }
   if (!st && mem == LBM_MEM_HOST) st = cuda_status(cudaStreamSynchronize(c->stream));
   if (!st && fused_reset(&c->plan, c->P, c->stream)) st = LBM_ERR_CUDA;
   if (!st) st = cuda_status(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream));
@@ -911,10 +1025,89 @@ int lbm_get_state(lbm_ctx* c, float* f, float* g, int mem) {
   if (!c) return LBM_ERR_ARG;
   if (!c->has_state) return LBM_ERR_STATE;
   int st = LBM_OK;
-  if (f) st = copy_out(f, c->f[c->cur], 19 * c->N, mem, c->stream);
-  if (!st && g) st = copy_out(g, c->g[c->cur], 7 * c->N, mem, c->stream);
+  if (c->hp.storage == LBM_STORE_F32) {
+    if (f) st = copy_out(f, fbuf<float>(c, c->cur), 19 * c->N, mem, c->stream);
+    if (!st && g) st = copy_out(g, gbuf<float>(c, c->cur), 7 * c->N, mem, c->stream);
+  } else {
+    st = convert_state(c, f, g, mem, false);
+  }
   if (st) return st;
   return read_flags(c);
+}
+
+namespace {
+
+// Checkpoint image: this header, then f (19 N) and g (7 N) in the storage format.
+struct CkptHeader {
+  char magic[8];
+  int32_t version, nx, ny, nz, storage, esize;
+  float rho_ref, T_ref;
+  int32_t pad[64 - 10];
+};
+static_assert(sizeof(CkptHeader) == 256, "checkpoint header is 256 bytes");
+constexpr char kCkptMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '1'};
+
+CkptHeader ckpt_header(const lbm_ctx* c) {
+  CkptHeader h{};
+  for (int i = 0; i < 8; ++i) h.magic[i] = kCkptMagic[i];
+  h.version = 1;
+  h.nx = c->hp.nx;
+  h.ny = c->hp.ny;
+  h.nz = c->hp.nz;
+  h.storage = c->hp.storage;
+  h.esize = (int32_t)c->esize;
+  h.rho_ref = c->P.rho_ref;
+  h.T_ref = c->P.T_ref;
+  return h;
+}
+
+}  // namespace
+
+long long lbm_checkpoint_bytes(const lbm_ctx* c) {
+  if (!c) return 0;
+  return (long long)sizeof(CkptHeader) + 26LL * c->N * (long long)c->esize;
+}
+
+int lbm_checkpoint(lbm_ctx* c, void* dst, int mem) {
+  if (!c || !dst) return LBM_ERR_ARG;
+  if (!c->has_state) return LBM_ERR_STATE;
+  const CkptHeader h = ckpt_header(c);
+  const cudaMemcpyKind kd = mem == LBM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  char* d = static_cast<char*>(dst);
+  const size_t fb = 19ull * c->N * c->esize, gb = 7ull * c->N * c->esize;
+  LBM_TRY(cudaMemcpyAsync(d + sizeof(h), c->f[c->cur], fb, kd, c->stream));
+  LBM_TRY(cudaMemcpyAsync(d + sizeof(h) + fb, c->g[c->cur], gb, kd, c->stream));
+  if (mem == LBM_MEM_HOST) {
+    std::memcpy(d, &h, sizeof(h));
+  } else {
+    LBM_TRY(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+  }
+  return read_flags(c);  // synchronises: the header source is on this stack frame
+}
+
+int lbm_restore(lbm_ctx* c, const void* src, int mem) {
+  if (!c || !src) return LBM_ERR_ARG;
+  CkptHeader h{};
+  const char* s = static_cast<const char*>(src);
+  if (mem == LBM_MEM_HOST) {
+    std::memcpy(&h, s, sizeof(h));
+  } else {
+    LBM_TRY(cudaMemcpyAsync(&h, s, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    LBM_TRY(cudaStreamSynchronize(c->stream));
+  }
+  const CkptHeader e = ckpt_header(c);
+  if (std::memcmp(h.magic, e.magic, 8) != 0 || h.version != e.version || h.nx != e.nx || h.ny != e.ny ||
+      h.nz != e.nz || h.storage != e.storage || h.esize != e.esize || h.rho_ref != e.rho_ref || h.T_ref != e.T_ref)
+    return LBM_ERR_ARG;
+  const cudaMemcpyKind kd = mem == LBM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const size_t fb = 19ull * c->N * c->esize, gb = 7ull * c->N * c->esize;
+  LBM_TRY(cudaMemcpyAsync(c->f[c->cur], s + sizeof(h), fb, kd, c->stream));
+  LBM_TRY(cudaMemcpyAsync(c->g[c->cur], s + sizeof(h) + fb, gb, kd, c->stream));
+  if (mem == LBM_MEM_HOST) LBM_TRY(cudaStreamSynchronize(c->stream));
+  if (fused_reset(&c->plan, c->P, c->stream)) return LBM_ERR_CUDA;
+  LBM_TRY(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream));
+  c->has_state = true;
+  return LBM_OK;
 }
 
 int lbm_set_face_T(lbm_ctx* c, int face, const float* T_face, int mem) {
@@ -933,8 +1126,8 @@ int lbm_step(lbm_ctx* c, int n) {
     int st;
     if (c->hp.schedule == LBM_SCHED_FUSED) {
       cudaEvent_t e = prof_begin(c);
-      st = fused_step(&c->plan, c->P, c->f[c->cur], c->g[c->cur], c->f[1 - c->cur], c->g[1 - c->cur], c->X,
-                      c->err_d, c->stream);
+      st = fused_step(&c->plan, c->P, fbuf<float>(c, c->cur), gbuf<float>(c, c->cur), fbuf<float>(c, 1 - c->cur),
+                      gbuf<float>(c, 1 - c->cur), c->X, c->err_d, c->stream);
       prof_end(c, 4, e);
       c->cur = 1 - c->cur;
     } else {
@@ -979,7 +1172,12 @@ int lbm_macros(lbm_ctx* c, float* rho, float* ux, float* uy, float* uz, float* T
   // T is summed into the ux slot of the scratch first when requested, then copied
   float* Tscratch = c->aux + 5 * c->N;  // Fx slot, rewritten by phase B below
   if (T) {
-    k_sumT<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->g[c->cur], Tscratch);
+    if (c->hp.storage == LBM_STORE_F16_SHIFTED)
+      k_sumT<__half><<<c->grid, kThreads, 0, c->stream>>>(c->P, gbuf<__half>(c, c->cur), Tscratch);
+    else if (c->hp.storage == LBM_STORE_BF16_SHIFTED)
+      k_sumT<__nv_bfloat16><<<c->grid, kThreads, 0, c->stream>>>(c->P, gbuf<__nv_bfloat16>(c, c->cur), Tscratch);
+    else
+      k_sumT<float><<<c->grid, kThreads, 0, c->stream>>>(c->P, gbuf<float>(c, c->cur), Tscratch);
     int st = copy_out(T, Tscratch, c->N, mem, c->stream);
     if (st) return st;
   }
@@ -996,7 +1194,15 @@ int lbm_macros(lbm_ctx* c, float* rho, float* ux, float* uy, float* uz, float* T
 int lbm_reduce(lbm_ctx* c, double out[4]) {
   if (!c || !out) return LBM_ERR_ARG;
   if (!c->has_state) return LBM_ERR_STATE;
-  k_reduce<<<c->red_blocks, kThreads, 0, c->stream>>>(c->P, c->f[c->cur], c->g[c->cur], c->partial);
+  if (c->hp.storage == LBM_STORE_F16_SHIFTED)
+    k_reduce<__half><<<c->red_blocks, kThreads, 0, c->stream>>>(c->P, fbuf<__half>(c, c->cur), gbuf<__half>(c, c->cur),
+                                                                c->partial);
+  else if (c->hp.storage == LBM_STORE_BF16_SHIFTED)
+    k_reduce<__nv_bfloat16><<<c->red_blocks, kThreads, 0, c->stream>>>(
+        c->P, fbuf<__nv_bfloat16>(c, c->cur), gbuf<__nv_bfloat16>(c, c->cur), c->partial);
+  else
+    k_reduce<float><<<c->red_blocks, kThreads, 0, c->stream>>>(c->P, fbuf<float>(c, c->cur), gbuf<float>(c, c->cur),
+                                                               c->partial);
   k_reduce_final<<<1, 32, 0, c->stream>>>(c->partial, c->red_blocks, c->red_out);
   LBM_TRY(cudaGetLastError());
   LBM_TRY(cudaMemcpyAsync(c->red_h, c->red_out, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream));

@@ -87,6 +87,7 @@ struct Params {
   float s_e, s_v, s_q, s_pi;
   float cv, inv_cv, wbar, inv_cs2t;  // c_s^2 of D3Q7 = wbar/3
   float lambda_l, lambda_v, rho_l, rho_v, inv_drho;
+  float rho_ref, T_ref;  // shifts of the 16-bit population storage
   int lam_uniform;
   int face_kind[6];
   float face_rho[6];

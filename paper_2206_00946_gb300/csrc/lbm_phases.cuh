@@ -9,6 +9,9 @@
 //      extrapolation of g at Dirichlet nodes (Sec. 3.1), on the new state
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "lbm_lattice.cuh"
 
 namespace lbm {
@@ -60,6 +63,53 @@ __device__ __forceinline__ void st_aux(float* a, float v, const Hint& h) {
   asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(h.keep));
 }
 #endif
+
+// Population storage.  FP32 stores f_i itself; the shifted 16-bit forms store
+// f_i - w_i rho_ref and g_i - w_i T_ref in IEEE half or bfloat16, and every
+// arithmetic operation stays in FP32: decode = base + (float)stored.
+template <typename ST>
+struct PopStore;
+
+template <>
+struct PopStore<float> {
+  __device__ __forceinline__ static float ld(const float* a, float, const Hint& h) { return ld_pop(a, h); }
+  __device__ __forceinline__ static float ld_plain(const float* a, float) { return *a; }
+  __device__ __forceinline__ static void st(float* a, float v, float) { *a = v; }
+};
+
+__device__ __forceinline__ unsigned short ld_u16_stream(const void* a, const Hint& h) {
+  unsigned short v;
+  asm volatile("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(a), "l"(h.stream));
+  return v;
+}
+
+template <>
+struct PopStore<__half> {
+  __device__ __forceinline__ static float ld(const __half* a, float base, const Hint& h) {
+    return base + __half2float(__ushort_as_half(ld_u16_stream(a, h)));
+  }
+  __device__ __forceinline__ static float ld_plain(const __half* a, float base) { return base + __half2float(*a); }
+  __device__ __forceinline__ static void st(__half* a, float v, float base) { *a = __float2half_rn(v - base); }
+};
+
+template <>
+struct PopStore<__nv_bfloat16> {
+  __device__ __forceinline__ static float ld(const __nv_bfloat16* a, float base, const Hint& h) {
+    return base + __bfloat162float(__ushort_as_bfloat16(ld_u16_stream(a, h)));
+  }
+  __device__ __forceinline__ static float ld_plain(const __nv_bfloat16* a, float base) {
+    return base + __bfloat162float(*a);
+  }
+  __device__ __forceinline__ static void st(__nv_bfloat16* a, float v, float base) {
+    *a = __float2bfloat16_rn(v - base);
+  }
+};
+
+// shift bases of direction i
+__device__ __forceinline__ float fbase(const Params& P, int i) { return w19(i) * P.rho_ref; }
+__device__ __forceinline__ float gbase(const Params& P, int i) {
+  return (i == 0 ? 1.f - P.wbar : P.wbar * (1.f / 6.f)) * P.T_ref;
+}
 
 __device__ __forceinline__ void sum19(const float* f, float& rho, float& jx, float& jy, float& jz) {
   rho = ((f[0] + (f[1] + f[2])) + ((f[3] + f[4]) + (f[5] + f[6]))) +
@@ -139,15 +189,16 @@ __device__ __forceinline__ bool interior1(const Params& P, int x, int y, int z) 
 }
 
 // ------------------------------------------------------------------- A -----
-__device__ __forceinline__ void phaseA(const Params& P, int c, const float* __restrict__ f,
-                                       const float* __restrict__ g, const Aux& X, float* __restrict__ Tout,
+template <typename ST>
+__device__ __forceinline__ void phaseA(const Params& P, int c, const ST* __restrict__ f,
+                                       const ST* __restrict__ g, const Aux& X, float* __restrict__ Tout,
                                        int& err) {
   const Hint h = make_hint();
   float fl[19], gl[7];
 #pragma unroll
-  for (int i = 0; i < 19; ++i) fl[i] = ld_pop(f + i * P.N + c, h);
+  for (int i = 0; i < 19; ++i) fl[i] = PopStore<ST>::ld(f + i * P.N + c, fbase(P, i), h);
 #pragma unroll
-  for (int i = 0; i < 7; ++i) gl[i] = ld_pop(g + i * P.N + c, h);
+  for (int i = 0; i < 7; ++i) gl[i] = PopStore<ST>::ld(g + i * P.N + c, gbase(P, i), h);
   float rho, jx, jy, jz;
   sum19(fl, rho, jx, jy, jz);
   const float T = sum7(gl);
@@ -219,7 +270,8 @@ __device__ __forceinline__ void phaseB(const Params& P, int c, const Aux& X) {
 // ------------------------------------------------------------------- C -----
 // Phase C, D3Q19 part, for one cell whose pre-collision populations are in fl:
 // collision with the exact-difference forcing, push streaming, bounce-back.
-__device__ __forceinline__ void phaseC19_cell(const Params& P, int c, const float* fl, float* fB, const Aux& X) {
+template <typename ST>
+__device__ __forceinline__ void phaseC19_cell(const Params& P, int c, const float* fl, ST* fB, const Aux& X) {
   int x, y, z;
   cell_xyz(P, c, x, y, z);
   Nb nb;
@@ -240,9 +292,9 @@ __device__ __forceinline__ void phaseC19_cell(const Params& P, int c, const floa
   for (int i = 0; i < 19; ++i) {
     const int k = nb_kind(nb, c19x(i), c19y(i), c19z(i));
     if (k == 0)
-      st_pop(fB + i * N + (c + nb_off(nb, c19x(i), c19y(i), c19z(i))), fs[i], h);
+      PopStore<ST>::st(fB + i * N + (c + nb_off(nb, c19x(i), c19y(i), c19z(i))), fs[i], fbase(P, i));
     else if (k & FACE_WALL)
-      st_pop(fB + opp19(i) * N + c, fs[i], h);  // modified bounce-back
+      PopStore<ST>::st(fB + opp19(i) * N + c, fs[i], fbase(P, opp19(i)));  // modified bounce-back
     // else: leaves through an open face
   }
 }
@@ -250,8 +302,9 @@ __device__ __forceinline__ void phaseC19_cell(const Params& P, int c, const floa
 // Phase C, D3Q7 part: div u by the isotropic D3Q19 difference, grad T from the
 // local moments, collision with the source, relaxed push streaming.  rho and the
 // real velocity of the cell come from phases A and B.
-__device__ __forceinline__ void phaseC7_cell(const Params& P, int c, const float* gl, const float* __restrict__ gA,
-                                             float* gB, const Aux& X) {
+template <typename ST>
+__device__ __forceinline__ void phaseC7_cell(const Params& P, int c, const float* gl, const ST* __restrict__ gA, ST* gB,
+                                             const Aux& X) {
   int x, y, z;
   cell_xyz(P, c, x, y, z);
   Nb nb;
@@ -278,47 +331,49 @@ __device__ __forceinline__ void phaseC7_cell(const Params& P, int c, const float
   float gs[7];
   collide7(P, gl, rho, T, ld_aux(X.ux + c, h), ld_aux(X.uy + c, h), ld_aux(X.uz + c, h), du, dpdT, gs);
   // relaxed streaming: g_i(y) += (g*_i(y - c_i) - g_i(y)) / (rho(y) c_v)
-  st_pop(gB + c, gl[0] + (gs[0] - gl[0]) * rcp(rho * P.cv), h);
+  PopStore<ST>::st(gB + c, gl[0] + (gs[0] - gl[0]) * rcp(rho * P.cv), gbase(P, 0));
 #pragma unroll
   for (int i = 1; i < 7; ++i) {
     if (nb_kind(nb, c7x(i), c7y(i), c7z(i))) continue;
     const int yc = c + nb_off(nb, c7x(i), c7y(i), c7z(i));
-    const float gold = ld_pop(gA + i * N + yc, h);
+    const float gold = PopStore<ST>::ld(gA + i * N + yc, gbase(P, i), h);
     const float ry = ld_aux(X.rho + yc, h);
-    st_pop(gB + i * N + yc, gold + (gs[i] - gold) * rcp(ry * P.cv), h);
+    PopStore<ST>::st(gB + i * N + yc, gold + (gs[i] - gold) * rcp(ry * P.cv), gbase(P, i));
   }
 }
 
+template <typename ST>
 __device__ __forceinline__ void phaseC_cell(const Params& P, int c, const float* fl, const float* gl,
-                                            const float* __restrict__ gA, float* fB, float* gB, const Aux& X) {
-  phaseC19_cell(P, c, fl, fB, X);
-  phaseC7_cell(P, c, gl, gA, gB, X);
+                                            const ST* __restrict__ gA, ST* fB, ST* gB, const Aux& X) {
+  phaseC19_cell<ST>(P, c, fl, fB, X);
+  phaseC7_cell<ST>(P, c, gl, gA, gB, X);
 }
 
-__device__ __forceinline__ void phaseC19(const Params& P, int c, const float* __restrict__ fA, float* fB,
-                                         const Aux& X) {
+template <typename ST>
+__device__ __forceinline__ void phaseC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB, const Aux& X) {
   const long long N = P.N;
   const Hint h = make_hint();
   float fl[19];
 #pragma unroll
-  for (int i = 0; i < 19; ++i) fl[i] = ld_pop(fA + i * N + c, h);
-  phaseC19_cell(P, c, fl, fB, X);
+  for (int i = 0; i < 19; ++i) fl[i] = PopStore<ST>::ld(fA + i * N + c, fbase(P, i), h);
+  phaseC19_cell<ST>(P, c, fl, fB, X);
 }
 
-__device__ __forceinline__ void phaseC7(const Params& P, int c, const float* __restrict__ gA, float* gB,
-                                        const Aux& X) {
+template <typename ST>
+__device__ __forceinline__ void phaseC7(const Params& P, int c, const ST* __restrict__ gA, ST* gB, const Aux& X) {
   const long long N = P.N;
   const Hint h = make_hint();
   float gl[7];
 #pragma unroll
-  for (int i = 0; i < 7; ++i) gl[i] = ld_pop(gA + i * N + c, h);
-  phaseC7_cell(P, c, gl, gA, gB, X);
+  for (int i = 0; i < 7; ++i) gl[i] = PopStore<ST>::ld(gA + i * N + c, gbase(P, i), h);
+  phaseC7_cell<ST>(P, c, gl, gA, gB, X);
 }
 
-__device__ __forceinline__ void phaseC(const Params& P, int c, const float* __restrict__ fA,
-                                       const float* __restrict__ gA, float* fB, float* gB, const Aux& X) {
-  phaseC19(P, c, fA, fB, X);
-  phaseC7(P, c, gA, gB, X);
+template <typename ST>
+__device__ __forceinline__ void phaseC(const Params& P, int c, const ST* __restrict__ fA, const ST* __restrict__ gA,
+                                       ST* fB, ST* gB, const Aux& X) {
+  phaseC19<ST>(P, c, fA, fB, X);
+  phaseC7<ST>(P, c, gA, gB, X);
 }
 
 // ------------------------------------------------------------------- D -----
@@ -330,7 +385,8 @@ __device__ __forceinline__ float face_T_at(const Params& P, int face, int x, int
   return t[x + P.nx * y];
 }
 
-__device__ __forceinline__ void phaseD(const Params& P, int c, int x, int y, int z, int m, float* fB, float* gB,
+template <typename ST>
+__device__ __forceinline__ void phaseD(const Params& P, int c, int x, int y, int z, int m, ST* fB, ST* gB,
                                        const Aux& X) {
   const long long N = P.N;
   int nnp = 0, nopen = 0, oface = -1;
@@ -362,25 +418,25 @@ __device__ __forceinline__ void phaseD(const Params& P, int c, int x, int y, int
     float fl[19];
     if (nnp == 1) {
 #pragma unroll
-      for (int i = 0; i < 19; ++i) fl[i] = ((unk >> i) & 1u) ? 0.f : fB[i * N + c];
+      for (int i = 0; i < 19; ++i) fl[i] = ((unk >> i) & 1u) ? 0.f : PopStore<ST>::ld_plain(fB + i * N + c, fbase(P, i));
       zouhe(oface, P.face_rho[oface], X.Fx[c], X.Fy[c], X.Fz[c], fl);
     } else {
       feq19(rb / (float)nopen, 0.f, 0.f, 0.f, fl);
     }
 #pragma unroll
     for (int i = 1; i < 19; ++i)
-      if ((unk >> i) & 1u) fB[i * N + c] = fl[i];
+      if ((unk >> i) & 1u) PopStore<ST>::st(fB + i * N + c, fl[i], fbase(P, i));
   }
   Tb /= (float)nnp;
   const int cf = cell_of(P, q[0], q[1], q[2]);
   float gf[7];
 #pragma unroll
-  for (int i = 0; i < 7; ++i) gf[i] = gB[i * N + cf];
+  for (int i = 0; i < 7; ++i) gf[i] = PopStore<ST>::ld_plain(gB + i * N + cf, gbase(P, i));
   const float Tf = sum7(gf);
   const float w0 = 1.f - P.wbar, w1 = P.wbar * (1.f / 6.f);
-  gB[c] = w0 * Tb + gf[0] - w0 * Tf;
+  PopStore<ST>::st(gB + c, w0 * Tb + gf[0] - w0 * Tf, gbase(P, 0));
 #pragma unroll
-  for (int i = 1; i < 7; ++i) gB[i * N + c] = w1 * Tb + gf[i] - w1 * Tf;
+  for (int i = 1; i < 7; ++i) PopStore<ST>::st(gB + i * N + c, w1 * Tb + gf[i] - w1 * Tf, gbase(P, i));
 }
 
 }  // namespace lbm

@@ -36,14 +36,15 @@ class lbm_params(ct.Structure):
         ("vartheta", ct.c_int), ("meq_printed", ct.c_int), ("wall_ueq_zero", ct.c_int),
         ("eos_kind", ct.c_int), ("eos_c0", _D),
         ("face_kind", ct.c_int * 6), ("face_T", _D * 6), ("face_rho", _D * 6), ("face_theta_deg", _D * 6),
-        ("storage", ct.c_int), ("schedule", ct.c_int),
+        ("storage", ct.c_int), ("store_rho_ref", _D), ("store_T_ref", _D), ("schedule", ct.c_int),
     ]
 
 
 # every symbol declared in include/lbm.h
 EXPORTS = ["lbm_init", "lbm_set_state", "lbm_get_state", "lbm_set_face_T", "lbm_step", "lbm_macros",
            "lbm_reduce", "lbm_sync", "lbm_stream_map", "lbm_destroy", "lbm_status_string", "lbm_Tc",
-           "lbm_maxwell", "lbm_launches_per_step", "lbm_profile", "lbm_profile_read", "lbm_reduce_static"]
+           "lbm_maxwell", "lbm_launches_per_step", "lbm_profile", "lbm_profile_read", "lbm_reduce_static",
+           "lbm_checkpoint_bytes", "lbm_checkpoint", "lbm_restore"]
 PROFILE_KINDS = ["phaseA", "phaseB", "phaseC", "phaseD", "fused", "phaseC7"]
 
 _lib = None
@@ -84,6 +85,10 @@ def load(path: str = LIB_PATH):
     L.lbm_profile.argtypes = [vp, ct.c_int]
     L.lbm_profile_read.argtypes = [vp, vp, vp, ct.c_int]
     L.lbm_reduce_static.argtypes = [vp, vp, ct.c_longlong, _D, _D, _D, vp, vp]
+    L.lbm_checkpoint_bytes.argtypes = [vp]
+    L.lbm_checkpoint_bytes.restype = ct.c_longlong
+    L.lbm_checkpoint.argtypes = [vp, vp, ct.c_int]
+    L.lbm_restore.argtypes = [vp, vp, ct.c_int]
     _lib = L
     return L
 
@@ -187,6 +192,16 @@ class Lattice:
     def lbm_get_state(self, f, g):
         st = load().lbm_get_state(self._ctx, _ptr(f), _ptr(g), _mem_of(f, g))
         return st
+
+    def lbm_checkpoint_bytes(self):
+        return int(load().lbm_checkpoint_bytes(self._ctx))
+
+    def lbm_checkpoint(self, dst):
+        """Writes the state image into dst (uint8 numpy array or torch tensor of lbm_checkpoint_bytes())."""
+        return load().lbm_checkpoint(self._ctx, _ptr(dst), _mem_of(dst))
+
+    def lbm_restore(self, src):
+        _check(load().lbm_restore(self._ctx, _ptr(src), _mem_of(src)), "lbm_restore")
 
     def lbm_set_face_T(self, face, T_face):
         _check(load().lbm_set_face_T(self._ctx, int(face), _ptr(T_face), _mem_of(T_face)), "lbm_set_face_T")

@@ -22,7 +22,8 @@ DEFAULTS = dict(
     s_e=1.25, s_v=0.8, s_q=1.0, s_pi=1.0,
     cv=5.0, wbar=0.75, lambda_l=1.0 / 3.0, lambda_v=1.0 / 3.0,
     rho_l=1.0, rho_v=1.0,
-    vartheta=0, meq_printed=0, wall_ueq_zero=1, eos_kind=0, eos_c0=0.0,
+    vartheta=0, meq_printed=0, wall_ueq_zero=1, eos_kind=0, eos_c0=0.0, storage=0,
+    store_rho_ref=0.0, store_T_ref=0.0,
     face_kind=[PERIODIC] * 6, face_T=[0.0] * 6, face_rho=[0.0] * 6, face_theta_deg=[90.0] * 6,
 )
 
