@@ -59,12 +59,13 @@ __global__ void k_load(Params P, const T* __restrict__ src, float* dst, int q, i
 }
 
 // Phase kernels over the cell range [c0, c1) (whole planes) with grid-stride loops.
+// write_j: store j for phase B (only lbm_macros runs phase B on its own).
 template <typename T>
 __global__ void k_phaseA(Params P, const T* __restrict__ f, const T* __restrict__ g, Aux X, float* Tout, int* err,
-                         int c0, int c1) {
+                         int c0, int c1, int write_j) {
   int e = 0;
   for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x)
-    phaseA(P, c, f, g, X, Tout, e);
+    phaseA(P, c, f, g, X, Tout, e, write_j != 0);
   if (e) atomicOr(err, e);
 }
 
@@ -79,6 +80,14 @@ __global__ void __launch_bounds__(256, LBM_PHASEC_MINBLOCKS) k_phaseC19(Params P
     phaseC19(P, c, fA, fB, X);
 }
 
+// force, velocity and the D3Q19 collision + push in one pass (phases B and C19)
+template <typename T>
+__global__ void __launch_bounds__(256, LBM_PHASEC_MINBLOCKS) k_phaseBC19(Params P, const T* __restrict__ fA, T* fB,
+                                                                         Aux X, int c0, int c1) {
+  for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x)
+    phaseBC19(P, c, fA, fB, X);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_phaseC7(Params P, const T* __restrict__ gA, T* gB, Aux X, int c0, int c1) {
   for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x)
@@ -87,7 +96,7 @@ __global__ void __launch_bounds__(256) k_phaseC7(Params P, const T* __restrict__
 
 // one thread per boundary candidate (boundary_candidate enumerates them)
 template <typename T>
-__global__ void k_phaseD(Params P, T* fB, T* gB, Aux X) {
+__global__ void __launch_bounds__(256, 3) k_phaseD(Params P, T* fB, T* gB, Aux X) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < (int)P.bd_total; k += gridDim.x * blockDim.x) {
     int x, y, z;
     boundary_candidate(P, k, x, y, z);
@@ -98,7 +107,7 @@ __global__ void k_phaseD(Params P, T* fB, T* gB, Aux X) {
 
 // boundary nodes of planes z0 + blockIdx.y
 template <typename T>
-__global__ void k_phaseD_planes(Params P, T* fB, T* gB, Aux X, int z0) {
+__global__ void __launch_bounds__(256, 3) k_phaseD_planes(Params P, T* fB, T* gB, Aux X, int z0) {
   const int z = z0 + blockIdx.y;
   const int cnt = boundary_count(P, z);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
@@ -200,11 +209,13 @@ __global__ void k_sumT(Params P, const S* __restrict__ g, float* T) {
 // stages of neighbouring slabs it reads, through events on a few streams, so
 // the phases of different slabs overlap on the GPU and a slab's populations are
 // read again (phase C) shortly after phase A read them, from L2.  Dependencies
-// (s = slab): B(s) <- A(s-1..s+1); C19(s) <- B(s); C7(s) <- B(s-1..s+1);
-// D(s) <- C19, C7 (s-2..s+2); and across steps A(s) <- D(s-2..s+2) of the
-// previous step (C19, C7 (s-1..s+1) when no slab has boundary nodes).  A run
-// of steps is captured once into a CUDA graph per buffer parity and replayed.
-enum { SPH_A = 0, SPH_B = 1, SPH_C19 = 2, SPH_C7 = 3, SPH_D = 4, SPH_N = 5 };
+// (s = slab, t = step): BC19(s) <- A(s-1..s+1) (force + D3Q19 pass);
+// C7(s) <- BC19(s-1..s+1); D(s) <- BC19, C7 (s-1..s+1); and across steps
+// A_t(s) <- BC19_{t-1}, C7_{t-1} (s-1..s+1), D_{t-1}(s).  Slabs hold at least
+// three planes, so the inward neighbour of a face node lies in its own slab.
+// A run of steps is captured once into a CUDA graph per buffer parity and
+// replayed.
+enum { SPH_A = 0, SPH_C19 = 1, SPH_C7 = 2, SPH_D = 3, SPH_N = 4 };
 constexpr int kMaxSlabStreams = 8;
 
 struct SlabPlan {
@@ -469,48 +480,38 @@ T* gbuf(lbm_ctx* c, int k) {
 template <typename T>
 int run_macros_t(lbm_ctx* c, float* Tout) {
   k_phaseA<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, c->cur), gbuf<T>(c, c->cur), c->X, Tout,
-                                                   c->err_d, 0, (int)c->N);
+                                                   c->err_d, 0, (int)c->N, 1);
   k_phaseB<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->X, 0, (int)c->N);
   return cuda_status(cudaGetLastError());
 }
 
 int run_macros(lbm_ctx* c, float* Tout) { return LBM_WITH_STORAGE(c, run_macros_t, c, Tout); }
 
+// One step, one launch per phase: A, force + D3Q19 collision/push (B and C19
+// in one pass), D3Q7 collision/push, D on the face nodes of the new state.
 template <typename T>
 int step_phases_t(lbm_ctx* c) {
   const int a = c->cur, b = 1 - c->cur;
   cudaEvent_t e = prof_begin(c);
   k_phaseA<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, a), gbuf<T>(c, a), c->X, nullptr, c->err_d, 0,
-                                                   (int)c->N);
+                                                   (int)c->N, 0);
   prof_end(c, 0, e);
-  e = prof_begin(c);
-  k_phaseB<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->X, 0, (int)c->N);
-  prof_end(c, 1, e);
-  if (c->bulk_grid > 0) {  // FP32 storage only
+  if (c->bulk_grid > 0) {  // FP32 storage only: staged C19 + C7 after a separate phase B
+    e = prof_begin(c);
+    k_phaseB<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->X, 0, (int)c->N);
+    prof_end(c, 1, e);
     e = prof_begin(c);
     k_phaseC_bulk<kBulkTile><<<c->bulk_grid, kBulkTile, kBulkSmem, c->stream>>>(
         c->P, fbuf<float>(c, a), gbuf<float>(c, a), fbuf<float>(c, b), gbuf<float>(c, b), c->X, c->err_d);
     prof_end(c, 2, e);
   } else {
-    // the D3Q19 and D3Q7 collisions are independent: the D3Q7 kernel (gather-bound)
-    // runs on a side stream next to the D3Q19 kernel (arithmetic- and bandwidth-bound).
-    // While profiling, both run on the context stream one after the other, so that
-    // each event pair brackets one kernel running alone.
-    cudaStream_t s7 = c->profiling ? c->stream : c->side;
-    if (!c->profiling) {
-      cudaEventRecord(c->ev_fork, c->stream);
-      cudaStreamWaitEvent(c->side, c->ev_fork, 0);
-    }
     e = prof_begin(c);
-    k_phaseC19<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, a), fbuf<T>(c, b), c->X, 0, (int)c->N);
+    k_phaseBC19<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, a), fbuf<T>(c, b), c->X, 0, (int)c->N);
     prof_end(c, 2, e);
+    // the D3Q7 phase needs the velocity of the neighbours: after the whole D3Q19 pass
     e = prof_begin(c);
-    k_phaseC7<T><<<c->grid, kThreads, 0, s7>>>(c->P, gbuf<T>(c, a), gbuf<T>(c, b), c->X, 0, (int)c->N);
+    k_phaseC7<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, gbuf<T>(c, a), gbuf<T>(c, b), c->X, 0, (int)c->N);
     prof_end(c, 5, e);
-    if (!c->profiling) {
-      cudaEventRecord(c->ev_join, c->side);
-      cudaStreamWaitEvent(c->stream, c->ev_join, 0);
-    }
   }
   if (c->P.bd_total > 0) {
     e = prof_begin(c);
@@ -543,36 +544,32 @@ void slab_deps_within(const SlabPlan& S, bool zper, int ph, int s, std::vector<i
   auto add = [&](int p, int q) {
     bool ok;
     const int w = slab_of_wrap(S, zper, q, ok);
-    if (!ok) return;
-    if (p == SPH_D && !S.has_d[w]) return;
-    d.push_back(p * S.nslab + w);
+    if (ok) d.push_back(p * S.nslab + w);
   };
-  if (ph == SPH_B)
+  if (ph == SPH_C19)
     for (int k = -1; k <= 1; ++k) add(SPH_A, s + k);
-  if (ph == SPH_C19) add(SPH_B, s);
   if (ph == SPH_C7)
-    for (int k = -1; k <= 1; ++k) add(SPH_B, s + k);
+    for (int k = -1; k <= 1; ++k) add(SPH_C19, s + k);
   if (ph == SPH_D)
-    for (int k = -2; k <= 2; ++k) {
+    for (int k = -1; k <= 1; ++k) {
       add(SPH_C19, s + k);
       add(SPH_C7, s + k);
     }
 }
 
-// stages of the previous step that phase A of slab s waits for
+// stages of the previous step that phase A of slab s waits for: the pushes and
+// boundary rules that write slab s, and the reads of the scratch of slab s
+// that phase A overwrites
 void slab_deps_prev(const SlabPlan& S, bool zper, int s, std::vector<int>& d) {
   d.clear();
-  for (int k = -2; k <= 2; ++k) {
+  for (int k = -1; k <= 1; ++k) {
     bool ok;
     const int w = slab_of_wrap(S, zper, s + k, ok);
     if (!ok) continue;
-    if (S.has_d[w]) {
-      d.push_back(SPH_D * S.nslab + w);
-    } else {
-      d.push_back(SPH_C19 * S.nslab + w);
-      d.push_back(SPH_C7 * S.nslab + w);
-    }
+    d.push_back(SPH_C19 * S.nslab + w);
+    d.push_back(SPH_C7 * S.nslab + w);
   }
+  if (S.has_d[s]) d.push_back(SPH_D * S.nslab + s);
 }
 
 int env_int(const char* name, int dflt) {
@@ -612,7 +609,7 @@ int slab_plan_create(lbm_ctx* c) {
       if (plane_has_boundary(c->P, z)) S->has_d[s] = 1;
   const bool zper = c->P.face_kind[4] == FACE_PERIODIC;
   // topological order along the diagonal wavefront slab + lag(phase)
-  const int lag[SPH_N] = {0, 1, 2, 2, 4};
+  const int lag[SPH_N] = {0, 1, 2, 3};
   const int n = S->nslab;
   std::vector<char> placed(SPH_N * n, 0), exists(SPH_N * n, 1);
   for (int s = 0; s < n; ++s) exists[SPH_D * n + s] = S->has_d[s];
@@ -682,13 +679,11 @@ int slab_enqueue_step_t(lbm_ctx* c, bool first) {
     const int blocks = std::min(grid_for((long long)(c1 - c0)), 152 * 8);
     switch (ph) {
       case SPH_A:
-        k_phaseA<T><<<blocks, kThreads, 0, st>>>(c->P, fbuf<T>(c, a), gbuf<T>(c, a), c->X, nullptr, c->err_d, c0, c1);
-        break;
-      case SPH_B:
-        k_phaseB<<<blocks, kThreads, 0, st>>>(c->P, c->X, c0, c1);
+        k_phaseA<T><<<blocks, kThreads, 0, st>>>(c->P, fbuf<T>(c, a), gbuf<T>(c, a), c->X, nullptr, c->err_d, c0, c1,
+                                                 0);
         break;
       case SPH_C19:
-        k_phaseC19<T><<<blocks, kThreads, 0, st>>>(c->P, fbuf<T>(c, a), fbuf<T>(c, b), c->X, c0, c1);
+        k_phaseBC19<T><<<blocks, kThreads, 0, st>>>(c->P, fbuf<T>(c, a), fbuf<T>(c, b), c->X, c0, c1);
         break;
       case SPH_C7:
         k_phaseC7<T><<<blocks, kThreads, 0, st>>>(c->P, gbuf<T>(c, a), gbuf<T>(c, b), c->X, c0, c1);

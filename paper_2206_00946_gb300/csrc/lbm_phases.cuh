@@ -75,6 +75,7 @@ struct PopStore<float> {
   __device__ __forceinline__ static float ld(const float* a, float, const Hint& h) { return ld_pop(a, h); }
   __device__ __forceinline__ static float ld_plain(const float* a, float) { return *a; }
   __device__ __forceinline__ static void st(float* a, float v, float) { *a = v; }
+  __device__ __forceinline__ static float round(float v, float) { return v; }
 };
 
 __device__ __forceinline__ unsigned short ld_u16_stream(const void* a, const Hint& h) {
@@ -90,6 +91,10 @@ struct PopStore<__half> {
   }
   __device__ __forceinline__ static float ld_plain(const __half* a, float base) { return base + __half2float(*a); }
   __device__ __forceinline__ static void st(__half* a, float v, float base) { *a = __float2half_rn(v - base); }
+  // the value a later load of st(v) returns
+  __device__ __forceinline__ static float round(float v, float base) {
+    return base + __half2float(__float2half_rn(v - base));
+  }
 };
 
 template <>
@@ -102,6 +107,9 @@ struct PopStore<__nv_bfloat16> {
   }
   __device__ __forceinline__ static void st(__nv_bfloat16* a, float v, float base) {
     *a = __float2bfloat16_rn(v - base);
+  }
+  __device__ __forceinline__ static float round(float v, float base) {
+    return base + __bfloat162float(__float2bfloat16_rn(v - base));
   }
 };
 
@@ -189,10 +197,87 @@ __device__ __forceinline__ bool interior1(const Params& P, int x, int y, int z) 
 }
 
 // ------------------------------------------------------------------- A -----
+__device__ __forceinline__ float face_T_at(const Params& P, int face, int x, int y, int z) {
+  const int a = face >> 1;
+  const float* t = P.Tface[face];
+  if (a == 0) return t[y + P.ny * z];
+  if (a == 1) return t[x + P.nx * z];
+  return t[x + P.nx * y];
+}
+
+// Unknown D3Q19 directions of a node: those arriving from beyond a non-periodic face.
+__device__ __forceinline__ unsigned unknown19(const Params& P, int x, int y, int z) {
+  unsigned unk = 0;
+#pragma unroll
+  for (int i = 1; i < 19; ++i) {
+    const int sx = x - c19x(i), sy = y - c19y(i), sz = z - c19z(i);
+    const bool u = ((sx < 0 || sx >= P.nx) && P.face_kind[0] != FACE_PERIODIC) ||
+                   ((sy < 0 || sy >= P.ny) && P.face_kind[2] != FACE_PERIODIC) ||
+                   ((sz < 0 || sz >= P.nz) && P.face_kind[4] != FACE_PERIODIC);
+    unk |= (u ? 1u : 0u) << i;
+  }
+  return unk;
+}
+
+// The rules of phase D (constant-pressure open faces, Sec. 3.3; the
+// non-equilibrium extrapolation of g, Sec. 3.1) at a face node whose streamed
+// populations are in fl: the rewritten populations are stored (and replaced in
+// fl / gl by the values a later load returns).  Every load is issued before the
+// first store, so that the node's memory round trips overlap.
 template <typename ST>
-__device__ __forceinline__ void phaseA(const Params& P, int c, const ST* __restrict__ f,
-                                       const ST* __restrict__ g, const Aux& X, float* __restrict__ Tout,
-                                       int& err) {
+__device__ __forceinline__ void boundary_rules(const Params& P, int c, int x, int y, int z, int m, float* fl,
+                                                  float* gl, ST* f, ST* g, const Aux& X) {
+  const long long N = P.N;
+  int nnp = 0, nopen = 0, oface = -1;
+  float rb = 0.f, Tb = 0.f;
+  int q[3] = {x, y, z};
+#pragma unroll
+  for (int fc = 0; fc < 6; ++fc) {
+    if (!((m >> fc) & 1)) continue;
+    ++nnp;
+    if (P.face_kind[fc] == FACE_OPEN) {
+      ++nopen;
+      oface = fc;
+      rb += P.face_rho[fc];
+    }
+    Tb += face_T_at(P, fc, x, y, z);
+    q[fc >> 1] += (fc & 1) ? -1 : 1;
+  }
+  const int cf = cell_of(P, q[0], q[1], q[2]);
+  float gf[7];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) gf[i] = PopStore<ST>::ld_plain(g + i * N + cf, gbase(P, i));
+  const float Fx = X.Fx[c], Fy = X.Fy[c], Fz = X.Fz[c];
+  if (nopen) {
+    // one open face: Zou-He (writes only the unknowns); edges and corners of open
+    // faces: every unknown = f^eq(rho_b, 0) = w_i rho_b, rho_b the faces' mean
+    const unsigned unk = unknown19(P, x, y, z);
+    if (nnp == 1) zouhe(oface, P.face_rho[oface], Fx, Fy, Fz, fl);
+    const float rbm = rb / (float)nopen;
+#pragma unroll
+    for (int i = 1; i < 19; ++i)
+      if ((unk >> i) & 1u) {
+        const float v = nnp == 1 ? fl[i] : w19(i) * rbm;
+        PopStore<ST>::st(f + i * N + c, v, fbase(P, i));
+        fl[i] = PopStore<ST>::round(v, fbase(P, i));
+      }
+  }
+  Tb /= (float)nnp;
+  const float Tf = sum7(gf);
+  const float w0 = 1.f - P.wbar, w1 = P.wbar * (1.f / 6.f);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    const float w = i == 0 ? w0 : w1;
+    const float v = w * Tb + gf[i] - w * Tf;
+    PopStore<ST>::st(g + i * N + c, v, gbase(P, i));
+    gl[i] = PopStore<ST>::round(v, gbase(P, i));
+  }
+}
+
+// write_j: store j for phase B (the fused force + D3Q19 pass recomputes it).
+template <typename ST>
+__device__ __forceinline__ void phaseA(const Params& P, int c, const ST* __restrict__ f, const ST* __restrict__ g,
+                                       const Aux& X, float* __restrict__ Tout, int& err, bool write_j = true) {
   const Hint h = make_hint();
   float fl[19], gl[7];
 #pragma unroll
@@ -207,9 +292,11 @@ __device__ __forceinline__ void phaseA(const Params& P, int c, const ST* __restr
   eos_pr(P, rho, T, p, dpdT);
   if (!psi_of(P, rho, p, psi)) err |= ERRF_PSI;
   st_aux(X.rho + c, rho, h);
-  st_aux(X.jx + c, jx, h);
-  st_aux(X.jy + c, jy, h);
-  st_aux(X.jz + c, jz, h);
+  if (write_j) {
+    st_aux(X.jx + c, jx, h);
+    st_aux(X.jy + c, jy, h);
+    st_aux(X.jz + c, jz, h);
+  }
   st_aux(X.psi + c, psi, h);
   if (Tout) Tout[c] = T;
 }
@@ -225,13 +312,10 @@ __device__ __forceinline__ bool needs_wetting(const Params& P, const Nb& nb) {
   return w;
 }
 
-__device__ __forceinline__ void phaseB(const Params& P, int c, const Aux& X) {
-  int x, y, z;
-  cell_xyz(P, c, x, y, z);
-  Nb nb;
-  make_nb(P, x, y, z, nb);
+// F = -G psi(x) sum_i varpi_i psi(x + c_i) c_i (Eq. 6), ghost psi beyond the faces
+__device__ __forceinline__ void force_at(const Params& P, int c, int x, int y, int z, const Nb& nb, const Aux& X,
+                                         const Hint& h, float& Fx, float& Fy, float& Fz) {
   const float* psi = X.psi;
-  const Hint h = make_hint();
   float sx = 0.f, sy = 0.f, sz = 0.f;
   if (!needs_wetting(P, nb)) {
 #pragma unroll
@@ -250,7 +334,19 @@ __device__ __forceinline__ void phaseB(const Params& P, int c, const Aux& X) {
     }
   }
   const float k = -P.G * ld_aux(psi + c, h);
-  const float Fx = k * sx, Fy = k * sy, Fz = k * sz;
+  Fx = k * sx;
+  Fy = k * sy;
+  Fz = k * sz;
+}
+
+__device__ __forceinline__ void phaseB(const Params& P, int c, const Aux& X) {
+  int x, y, z;
+  cell_xyz(P, c, x, y, z);
+  Nb nb;
+  make_nb(P, x, y, z, nb);
+  const Hint h = make_hint();
+  float Fx, Fy, Fz;
+  force_at(P, c, x, y, z, nb, X, h, Fx, Fy, Fz);
   st_aux(X.Fx + c, Fx, h);
   st_aux(X.Fy + c, Fy, h);
   st_aux(X.Fz + c, Fz, h);
@@ -296,6 +392,53 @@ __device__ __forceinline__ void phaseC19_cell(const Params& P, int c, const floa
     else if (k & FACE_WALL)
       PopStore<ST>::st(fB + opp19(i) * N + c, fs[i], fbase(P, opp19(i)));  // modified bounce-back
     // else: leaves through an open face
+  }
+}
+
+// Phases B and C19 of one cell in one pass: the force from the psi stencil, the
+// real velocity (both stored for the D3Q7 phase and the next step's open faces),
+// then the D3Q19 collision and push of phaseC19_cell.
+template <typename ST>
+__device__ __forceinline__ void phaseBC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB, const Aux& X) {
+  int x, y, z;
+  cell_xyz(P, c, x, y, z);
+  Nb nb;
+  make_nb(P, x, y, z, nb);
+  const long long N = P.N;
+  const Hint h = make_hint();
+  float Fx, Fy, Fz;
+  force_at(P, c, x, y, z, nb, X, h, Fx, Fy, Fz);
+  st_aux(X.Fx + c, Fx, h);
+  st_aux(X.Fy + c, Fy, h);
+  st_aux(X.Fz + c, Fz, h);
+  float fl[19];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) fl[i] = PopStore<ST>::ld(fA + i * N + c, fbase(P, i), h);
+  float rho, jx, jy, jz;
+  sum19(fl, rho, jx, jy, jz);
+  const int m = P.any_nonperiodic ? node_faces(P, x, y, z) : 0;
+  const bool wall = m && on_wall(P, m);
+  const float ir = rcp(rho);
+  float vx = 0.f, vy = 0.f, vz = 0.f;
+  if (!wall) {
+    vx = (jx + 0.5f * Fx) * ir;
+    vy = (jy + 0.5f * Fy) * ir;
+    vz = (jz + 0.5f * Fz) * ir;
+  }
+  st_aux(X.ux + c, vx, h);
+  st_aux(X.uy + c, vy, h);
+  st_aux(X.uz + c, vz, h);
+  float ux = jx * ir, uy = jy * ir, uz = jz * ir;
+  if (wall && P.wall_ueq_zero) ux = uy = uz = 0.f;
+  float fs[19];
+  collide19(P, fl, rho, ux, uy, uz, Fx, Fy, Fz, fs);
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    const int k = nb_kind(nb, c19x(i), c19y(i), c19z(i));
+    if (k == 0)
+      PopStore<ST>::st(fB + i * N + (c + nb_off(nb, c19x(i), c19y(i), c19z(i))), fs[i], fbase(P, i));
+    else if (k & FACE_WALL)
+      PopStore<ST>::st(fB + opp19(i) * N + c, fs[i], fbase(P, opp19(i)));  // modified bounce-back
   }
 }
 
@@ -377,66 +520,14 @@ __device__ __forceinline__ void phaseC(const Params& P, int c, const ST* __restr
 }
 
 // ------------------------------------------------------------------- D -----
-__device__ __forceinline__ float face_T_at(const Params& P, int face, int x, int y, int z) {
-  const int a = face >> 1;
-  const float* t = P.Tface[face];
-  if (a == 0) return t[y + P.ny * z];
-  if (a == 1) return t[x + P.nx * z];
-  return t[x + P.nx * y];
-}
-
 template <typename ST>
 __device__ __forceinline__ void phaseD(const Params& P, int c, int x, int y, int z, int m, ST* fB, ST* gB,
                                        const Aux& X) {
   const long long N = P.N;
-  int nnp = 0, nopen = 0, oface = -1;
-  float rb = 0.f, Tb = 0.f;
-  int q[3] = {x, y, z};
+  float fl[19], gl[7];
 #pragma unroll
-  for (int f = 0; f < 6; ++f) {
-    if (!((m >> f) & 1)) continue;
-    ++nnp;
-    if (P.face_kind[f] == FACE_OPEN) {
-      ++nopen;
-      oface = f;
-      rb += P.face_rho[f];
-    }
-    Tb += face_T_at(P, f, x, y, z);
-    q[f >> 1] += (f & 1) ? -1 : 1;
-  }
-  if (nopen) {
-    // unknown populations: those arriving from beyond a non-periodic face
-    unsigned unk = 0;
-#pragma unroll
-    for (int i = 1; i < 19; ++i) {
-      const int sx = x - c19x(i), sy = y - c19y(i), sz = z - c19z(i);
-      const bool u = ((sx < 0 || sx >= P.nx) && P.face_kind[0] != FACE_PERIODIC) ||
-                     ((sy < 0 || sy >= P.ny) && P.face_kind[2] != FACE_PERIODIC) ||
-                     ((sz < 0 || sz >= P.nz) && P.face_kind[4] != FACE_PERIODIC);
-      unk |= (u ? 1u : 0u) << i;
-    }
-    float fl[19];
-    if (nnp == 1) {
-#pragma unroll
-      for (int i = 0; i < 19; ++i) fl[i] = ((unk >> i) & 1u) ? 0.f : PopStore<ST>::ld_plain(fB + i * N + c, fbase(P, i));
-      zouhe(oface, P.face_rho[oface], X.Fx[c], X.Fy[c], X.Fz[c], fl);
-    } else {
-      feq19(rb / (float)nopen, 0.f, 0.f, 0.f, fl);
-    }
-#pragma unroll
-    for (int i = 1; i < 19; ++i)
-      if ((unk >> i) & 1u) PopStore<ST>::st(fB + i * N + c, fl[i], fbase(P, i));
-  }
-  Tb /= (float)nnp;
-  const int cf = cell_of(P, q[0], q[1], q[2]);
-  float gf[7];
-#pragma unroll
-  for (int i = 0; i < 7; ++i) gf[i] = PopStore<ST>::ld_plain(gB + i * N + cf, gbase(P, i));
-  const float Tf = sum7(gf);
-  const float w0 = 1.f - P.wbar, w1 = P.wbar * (1.f / 6.f);
-  PopStore<ST>::st(gB + c, w0 * Tb + gf[0] - w0 * Tf, gbase(P, 0));
-#pragma unroll
-  for (int i = 1; i < 7; ++i) PopStore<ST>::st(gB + i * N + c, w1 * Tb + gf[i] - w1 * Tf, gbase(P, i));
+  for (int i = 0; i < 19; ++i) fl[i] = PopStore<ST>::ld_plain(fB + i * N + c, fbase(P, i));
+  boundary_rules<ST>(P, c, x, y, z, m, fl, gl, fB, gB, X);
 }
 
 }  // namespace lbm
