@@ -51,6 +51,8 @@ LBM_HD float rcp(float x) {
 #endif
 }
 
+LBM_HD double rcp(double x) { return 1.0 / x; }
+
 // Division of a non-negative 32-bit value (< 2^31) by a runtime divisor d with a
 // precomputed multiplier: q = umulhi(n, mul) >> shr (mul = 0 means d = 1).
 LBM_HD unsigned fdiv(unsigned n, unsigned mul, unsigned shr) {
@@ -99,33 +101,35 @@ struct Params {
 // --------------------------------------------------------------- thermo ----
 // Peng-Robinson EOS (Eq. 37) with xi(T) = [1 + kappa (1 - sqrt(T/Tc))]^2, its
 // T-derivative at constant rho, and psi of Eq. 7 (dx = dt = 1, c_s-hat^2 = 1/3).
-LBM_HD void eos_pr(const Params& P, float rho, float T, float& p, float& dpdT) {
+template <typename R>
+LBM_HD void eos_pr(const Params& P, R rho, R T, R& p, R& dpdT) {
   if (P.eos_kind == 1) {
     p = P.eos_c0 * rho;
-    dpdT = 0.f;
+    dpdT = R(0);
     return;
   }
-  const float sr = sqrtf(T * P.inv_Tc);
-  const float s = 1.f + P.kappa * (1.f - sr);
-  const float xi = s * s;
+  const R sr = sqrt(T * P.inv_Tc);
+  const R s = R(1) + P.kappa * (R(1) - sr);
+  const R xi = s * s;
   // d xi / dT = -kappa s / sqrt(T Tc) = -kappa s sr / T
-  const float dxi = -P.kappa * s * sr * rcp(T);
-  const float br = P.b * rho;
-  const float inv1 = rcp(1.f - br);
-  const float den = 1.f + br * (2.f - br);
-  const float att = P.a * rho * rho * rcp(den);
+  const R dxi = -P.kappa * s * sr * rcp(T);
+  const R br = P.b * rho;
+  const R inv1 = rcp(R(1) - br);
+  const R den = R(1) + br * (R(2) - br);
+  const R att = P.a * rho * rho * rcp(den);
   p = rho * P.R * T * inv1 - xi * att;
   dpdT = rho * P.R * inv1 - dxi * att;
 }
 
 // psi^2 = 2 (p - rho/3) / G.  Returns false when the argument is negative.
-LBM_HD bool psi_of(const Params& P, float rho, float p, float& psi) {
-  const float arg = 2.f * (p - rho * (1.f / 3.f)) * P.inv_G;
-  if (!(arg >= 0.f)) {
-    psi = 0.f;
+template <typename R>
+LBM_HD bool psi_of(const Params& P, R rho, R p, R& psi) {
+  const R arg = R(2) * (p - rho * (R(1) / R(3))) * P.inv_G;
+  if (!(arg >= R(0))) {
+    psi = R(0);
     return false;
   }
-  psi = sqrtf(arg);
+  psi = sqrt(arg);
   return true;
 }
 
@@ -133,45 +137,46 @@ LBM_HD bool psi_of(const Params& P, float rho, float p, float& psi) {
 // Collision of Eq. 8 for one cell: m = M-hat f; m* = m - Lambda (m - m^eq(u)) +
 // [m^eq(u + F/rho) - m^eq(u)]; f* = M-hat^-1 m*.  m^eq is M-hat f^eq in closed form
 // (rows 16-18 optionally as printed in Eq. 9).  u is u^eq (zero at wall nodes).
-LBM_HD void collide19(const Params& P, const float* f, float rho, float ux, float uy, float uz, float Fx,
-                      float Fy, float Fz, float* fs) {
+template <typename R>
+LBM_HD void collide19(const Params& P, const R* f, R rho, R ux, R uy, R uz, R Fx,
+                      R Fy, R Fz, R* fs) {
   // raw moments, rows 4..18 of M-hat
-  const float s7_10 = f[7] + f[8] + f[9] + f[10];
-  const float s11_14 = f[11] + f[12] + f[13] + f[14];
-  const float s15_18 = f[15] + f[16] + f[17] + f[18];
-  const float a12 = f[1] + f[2], a34 = f[3] + f[4], a56 = f[5] + f[6];
-  const float m4 = a12 + a34 + a56 + 2.f * (s7_10 + s11_14 + s15_18);
-  const float m5 = 2.f * a12 - a34 - a56 + s7_10 + s11_14 - 2.f * s15_18;
-  const float m6 = a34 - a56 + s7_10 - s11_14;
-  const float m7 = f[7] + f[8] - f[9] - f[10];
-  const float m8 = f[11] + f[12] - f[13] - f[14];
-  const float m9 = f[15] + f[16] - f[17] - f[18];
-  const float m10 = f[7] - f[8] - f[9] + f[10];
-  const float m11 = f[7] - f[8] + f[9] - f[10];
-  const float m12 = f[11] - f[12] - f[13] + f[14];
-  const float m13 = f[11] - f[12] + f[13] - f[14];
-  const float m14 = f[15] - f[16] - f[17] + f[18];
-  const float m15 = f[15] - f[16] + f[17] - f[18];
-  const float m16 = s7_10, m17 = s11_14, m18 = s15_18;
+  const R s7_10 = f[7] + f[8] + f[9] + f[10];
+  const R s11_14 = f[11] + f[12] + f[13] + f[14];
+  const R s15_18 = f[15] + f[16] + f[17] + f[18];
+  const R a12 = f[1] + f[2], a34 = f[3] + f[4], a56 = f[5] + f[6];
+  const R m4 = a12 + a34 + a56 + R(2) * (s7_10 + s11_14 + s15_18);
+  const R m5 = R(2) * a12 - a34 - a56 + s7_10 + s11_14 - R(2) * s15_18;
+  const R m6 = a34 - a56 + s7_10 - s11_14;
+  const R m7 = f[7] + f[8] - f[9] - f[10];
+  const R m8 = f[11] + f[12] - f[13] - f[14];
+  const R m9 = f[15] + f[16] - f[17] - f[18];
+  const R m10 = f[7] - f[8] - f[9] + f[10];
+  const R m11 = f[7] - f[8] + f[9] - f[10];
+  const R m12 = f[11] - f[12] - f[13] + f[14];
+  const R m13 = f[11] - f[12] + f[13] - f[14];
+  const R m14 = f[15] - f[16] - f[17] + f[18];
+  const R m15 = f[15] - f[16] + f[17] - f[18];
+  const R m16 = s7_10, m17 = s11_14, m18 = s15_18;
 
-  const float ir = rcp(rho);
-  const float uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
+  const R ir = rcp(rho);
+  const R uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
   // rho (u'_a^2 - u_a^2) with u' = u + F/rho
-  const float qx = 2.f * ux * Fx + Fx * Fx * ir;
-  const float qy = 2.f * uy * Fy + Fy * Fy * ir;
-  const float qz = 2.f * uz * Fz + Fz * Fz * ir;
-  const float third = 1.f / 3.f, ninth = 1.f / 9.f, sixth = 1.f / 6.f;
+  const R qx = R(2) * ux * Fx + Fx * Fx * ir;
+  const R qy = R(2) * uy * Fy + Fy * Fy * ir;
+  const R qz = R(2) * uz * Fz + Fz * Fz * ir;
+  const R third = R(1) / R(3), ninth = R(1) / R(9), sixth = R(1) / R(6);
 
-  const float e4 = rho * (1.f + uxx + uyy + uzz), d4 = qx + qy + qz;
-  const float e5 = rho * (2.f * uxx - uyy - uzz), d5 = 2.f * qx - qy - qz;
-  const float e6 = rho * (uyy - uzz), d6 = qy - qz;
-  const float e7 = rho * ux * uy, d7 = ux * Fy + Fx * uy + Fx * Fy * ir;
-  const float e8 = rho * ux * uz, d8 = ux * Fz + Fx * uz + Fx * Fz * ir;
-  const float e9 = rho * uy * uz, d9 = uy * Fz + Fy * uz + Fy * Fz * ir;
-  const float e10 = third * rho * uy, e11 = third * rho * ux, e12 = third * rho * uz;
-  float e16, e17, e18, d16, d17, d18;
+  const R e4 = rho * (R(1) + uxx + uyy + uzz), d4 = qx + qy + qz;
+  const R e5 = rho * (R(2) * uxx - uyy - uzz), d5 = R(2) * qx - qy - qz;
+  const R e6 = rho * (uyy - uzz), d6 = qy - qz;
+  const R e7 = rho * ux * uy, d7 = ux * Fy + Fx * uy + Fx * Fy * ir;
+  const R e8 = rho * ux * uz, d8 = ux * Fz + Fx * uz + Fx * Fz * ir;
+  const R e9 = rho * uy * uz, d9 = uy * Fz + Fy * uz + Fy * Fz * ir;
+  const R e10 = third * rho * uy, e11 = third * rho * ux, e12 = third * rho * uz;
+  R e16, e17, e18, d16, d17, d18;
   if (P.meq_printed) {
-    const float base = ninth * rho - sixth * rho * (uxx + uyy + uzz), db = -sixth * d4;
+    const R base = ninth * rho - sixth * rho * (uxx + uyy + uzz), db = -sixth * d4;
     e16 = base + third * rho * (uxx + uyy);
     e17 = base + third * rho * (uxx + uzz);
     e18 = base + third * rho * (uyy + uzz);
@@ -186,84 +191,87 @@ LBM_HD void collide19(const Params& P, const float* f, float rho, float ux, floa
     d17 = -sixth * qy + third * (qx + qz);
     d18 = -sixth * qx + third * (qy + qz);
   }
-  const float se = P.s_e, sv = P.s_v, sq = P.s_q, sp = P.s_pi;
+  const R se = P.s_e, sv = P.s_v, sq = P.s_q, sp = P.s_pi;
   // post-collision moments
-  const float n0 = rho;
-  const float n1 = rho * ux + Fx, n2 = rho * uy + Fy, n3 = rho * uz + Fz;
-  const float n4 = m4 - se * (m4 - e4) + d4;
-  const float n5 = m5 - sv * (m5 - e5) + d5;
-  const float n6 = m6 - sv * (m6 - e6) + d6;
-  const float n7 = m7 - sv * (m7 - e7) + d7;
-  const float n8 = m8 - sv * (m8 - e8) + d8;
-  const float n9 = m9 - sv * (m9 - e9) + d9;
-  const float n10 = m10 - sq * (m10 - e10) + third * Fy;
-  const float n11 = m11 - sq * (m11 - e11) + third * Fx;
-  const float n12 = m12 - sq * (m12 - e12) + third * Fz;
-  const float n13 = m13 - sq * (m13 - e11) + third * Fx;
-  const float n14 = m14 - sq * (m14 - e12) + third * Fz;
-  const float n15 = m15 - sq * (m15 - e10) + third * Fy;
-  const float n16 = m16 - sp * (m16 - e16) + d16;
-  const float n17 = m17 - sp * (m17 - e17) + d17;
-  const float n18 = m18 - sp * (m18 - e18) + d18;
+  const R n0 = rho;
+  const R n1 = rho * ux + Fx, n2 = rho * uy + Fy, n3 = rho * uz + Fz;
+  const R n4 = m4 - se * (m4 - e4) + d4;
+  const R n5 = m5 - sv * (m5 - e5) + d5;
+  const R n6 = m6 - sv * (m6 - e6) + d6;
+  const R n7 = m7 - sv * (m7 - e7) + d7;
+  const R n8 = m8 - sv * (m8 - e8) + d8;
+  const R n9 = m9 - sv * (m9 - e9) + d9;
+  const R n10 = m10 - sq * (m10 - e10) + third * Fy;
+  const R n11 = m11 - sq * (m11 - e11) + third * Fx;
+  const R n12 = m12 - sq * (m12 - e12) + third * Fz;
+  const R n13 = m13 - sq * (m13 - e11) + third * Fx;
+  const R n14 = m14 - sq * (m14 - e12) + third * Fz;
+  const R n15 = m15 - sq * (m15 - e10) + third * Fy;
+  const R n16 = m16 - sp * (m16 - e16) + d16;
+  const R n17 = m17 - sp * (m17 - e17) + d17;
+  const R n18 = m18 - sp * (m18 - e18) + d18;
 
   // f* = M-hat^-1 m*, solved by hand from the block structure of M-hat
-  const float D = n16 + n17 + n18;
-  const float S = n4 - 2.f * D;            // (f1+f2) + (f3+f4) + (f5+f6)
-  const float A = (n5 - n16 - n17 + 2.f * n18 + S) * third;  // f1 + f2
-  const float P6 = n6 - n16 + n17;          // (f3+f4) - (f5+f6)
-  const float B = 0.5f * (S - A + P6);      // f3 + f4
-  const float C = 0.5f * (S - A - P6);      // f5 + f6
-  const float dx = n1 - n11 - n13, dy = n2 - n10 - n15, dz = n3 - n12 - n14;
+  const R D = n16 + n17 + n18;
+  const R S = n4 - R(2) * D;            // (f1+f2) + (f3+f4) + (f5+f6)
+  const R A = (n5 - n16 - n17 + R(2) * n18 + S) * third;  // f1 + f2
+  const R P6 = n6 - n16 + n17;          // (f3+f4) - (f5+f6)
+  const R B = R(0.5) * (S - A + P6);      // f3 + f4
+  const R C = R(0.5) * (S - A - P6);      // f5 + f6
+  const R dx = n1 - n11 - n13, dy = n2 - n10 - n15, dz = n3 - n12 - n14;
   fs[0] = n0 - n4 + D;
-  fs[1] = 0.5f * (A + dx);
-  fs[2] = 0.5f * (A - dx);
-  fs[3] = 0.5f * (B + dy);
-  fs[4] = 0.5f * (B - dy);
-  fs[5] = 0.5f * (C + dz);
-  fs[6] = 0.5f * (C - dz);
-  fs[7] = 0.25f * (n16 + n7 + n10 + n11);
-  fs[8] = 0.25f * (n16 + n7 - n10 - n11);
-  fs[9] = 0.25f * (n16 - n7 - n10 + n11);
-  fs[10] = 0.25f * (n16 - n7 + n10 - n11);
-  fs[11] = 0.25f * (n17 + n8 + n12 + n13);
-  fs[12] = 0.25f * (n17 + n8 - n12 - n13);
-  fs[13] = 0.25f * (n17 - n8 - n12 + n13);
-  fs[14] = 0.25f * (n17 - n8 + n12 - n13);
-  fs[15] = 0.25f * (n18 + n9 + n14 + n15);
-  fs[16] = 0.25f * (n18 + n9 - n14 - n15);
-  fs[17] = 0.25f * (n18 - n9 - n14 + n15);
-  fs[18] = 0.25f * (n18 - n9 + n14 - n15);
+  fs[1] = R(0.5) * (A + dx);
+  fs[2] = R(0.5) * (A - dx);
+  fs[3] = R(0.5) * (B + dy);
+  fs[4] = R(0.5) * (B - dy);
+  fs[5] = R(0.5) * (C + dz);
+  fs[6] = R(0.5) * (C - dz);
+  fs[7] = R(0.25) * (n16 + n7 + n10 + n11);
+  fs[8] = R(0.25) * (n16 + n7 - n10 - n11);
+  fs[9] = R(0.25) * (n16 - n7 - n10 + n11);
+  fs[10] = R(0.25) * (n16 - n7 + n10 - n11);
+  fs[11] = R(0.25) * (n17 + n8 + n12 + n13);
+  fs[12] = R(0.25) * (n17 + n8 - n12 - n13);
+  fs[13] = R(0.25) * (n17 - n8 - n12 + n13);
+  fs[14] = R(0.25) * (n17 - n8 + n12 - n13);
+  fs[15] = R(0.25) * (n18 + n9 + n14 + n15);
+  fs[16] = R(0.25) * (n18 + n9 - n14 - n15);
+  fs[17] = R(0.25) * (n18 - n9 - n14 + n15);
+  fs[18] = R(0.25) * (n18 - n9 + n14 - n15);
 }
 
-LBM_HD void feq19(float rho, float ux, float uy, float uz, float* fe) {
-  const float uu = ux * ux + uy * uy + uz * uz;
+template <typename R>
+LBM_HD void feq19(R rho, R ux, R uy, R uz, R* fe) {
+  const R uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
-    const float cu = c19x(i) * ux + c19y(i) * uy + c19z(i) * uz;
-    fe[i] = w19(i) * rho * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
+    const R cu = c19x(i) * ux + c19y(i) * uy + c19z(i) * uz;
+    fe[i] = w19(i) * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
   }
 }
 
 // ------------------------------------------------------------ D3Q7 MRT ------
-LBM_HD float lambda_of(const Params& P, float rho) {
+template <typename R>
+LBM_HD R lambda_of(const Params& P, R rho) {
   if (P.lam_uniform) return P.lambda_v;
-  float phi = (rho - P.rho_v) * P.inv_drho;
-  phi = fminf(fmaxf(phi, 0.f), 1.f);
+  R phi = (rho - P.rho_v) * P.inv_drho;
+  phi = fmin(fmax(phi, R(0)), R(1));
   return P.lambda_v + (P.lambda_l - P.lambda_v) * phi;
 }
 
 // Eq. 13 collision with the source of Eq. 15: g* = g - M^-1 Lambda M (g - w T) - w Fbar,
 // Lambda = diag(1, vs, vs, vs, 1, 1, 1), vs from lambda, grad T = -vs m_alpha / c_s^2.
-LBM_HD void collide7(const Params& P, const float* g, float rho, float T, float ux, float uy, float uz, float divu,
-                     float dpdT, float* gs) {
-  const float m1 = g[1] - g[2], m2 = g[3] - g[4], m3 = g[5] - g[6];
-  const float vs = rcp(lambda_of(P, rho) * P.inv_cs2t + 0.5f);
-  const float k = -vs * P.inv_cs2t;
-  const float ugT = k * (ux * m1 + uy * m2 + uz * m3);
-  const float Fbar = rho * P.cv * ugT + T * dpdT * divu;
-  const float h = T - Fbar;
-  const float w0 = 1.f - P.wbar, w1 = P.wbar * (1.f / 6.f);
-  const float r = 0.5f * (1.f - vs);
+template <typename R>
+LBM_HD void collide7(const Params& P, const R* g, R rho, R T, R ux, R uy, R uz, R divu,
+                     R dpdT, R* gs) {
+  const R m1 = g[1] - g[2], m2 = g[3] - g[4], m3 = g[5] - g[6];
+  const R vs = rcp(lambda_of(P, rho) * P.inv_cs2t + R(0.5));
+  const R k = -vs * P.inv_cs2t;
+  const R ugT = k * (ux * m1 + uy * m2 + uz * m3);
+  const R Fbar = rho * P.cv * ugT + T * dpdT * divu;
+  const R h = T - Fbar;
+  const R w0 = R(1) - P.wbar, w1 = P.wbar * (R(1) / R(6));
+  const R r = R(0.5) * (R(1) - vs);
   gs[0] = w0 * h;
   gs[1] = w1 * h + r * m1;
   gs[2] = w1 * h - r * m1;
@@ -277,10 +285,11 @@ LBM_HD void collide7(const Params& P, const float* g, float rho, float T, float 
 // Constant-pressure boundary of Sec. 3.3 on face `face` (outward normal n):
 // u_n = [sum_{c.n=0} f + 2 sum_{c.n=1} f + F.n/2]/rho_b - 1; f_{-n} = f_n - rho_b u_n / 3;
 // diagonal unknowns c = -n + sig e_a: f = f_opp - rho_b u_n/6 - sig/2 (sum_{c.n=0} c_a f + F_a/2) + F.n/8.
-LBM_HD void zouhe(int face, float rho_b, float Fx, float Fy, float Fz, float* f) {
+template <typename R>
+LBM_HD void zouhe(int face, R rho_b, R Fx, R Fy, R Fz, R* f) {
   const int ax = face >> 1;
   const int sg = (face & 1) ? 1 : -1;
-  float SZ = 0.f, SP = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
+  R SZ = R(0), SP = R(0), tx = R(0), ty = R(0), tz = R(0);
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     const int cn = sg * (ax == 0 ? c19x(i) : (ax == 1 ? c19y(i) : c19z(i)));
@@ -293,10 +302,10 @@ LBM_HD void zouhe(int face, float rho_b, float Fx, float Fy, float Fz, float* f)
       SP += f[i];
     }
   }
-  const float Fn = sg * (ax == 0 ? Fx : (ax == 1 ? Fy : Fz));
-  const float un = (SZ + 2.f * SP + 0.5f * Fn) * rcp(rho_b) - 1.f;
-  const float base6 = -rho_b * un * (1.f / 6.f) + 0.125f * Fn;
-  const float hx = 0.5f * (tx + 0.5f * Fx), hy = 0.5f * (ty + 0.5f * Fy), hz = 0.5f * (tz + 0.5f * Fz);
+  const R Fn = sg * (ax == 0 ? Fx : (ax == 1 ? Fy : Fz));
+  const R un = (SZ + R(2) * SP + R(0.5) * Fn) * rcp(rho_b) - R(1);
+  const R base6 = -rho_b * un * (R(1) / R(6)) + R(0.125) * Fn;
+  const R hx = R(0.5) * (tx + R(0.5) * Fx), hy = R(0.5) * (ty + R(0.5) * Fy), hz = R(0.5) * (tz + R(0.5) * Fz);
 #pragma unroll
   for (int i = 1; i < 19; ++i) {
     const int cx = c19x(i), cy = c19y(i), cz = c19z(i);
@@ -304,9 +313,9 @@ LBM_HD void zouhe(int face, float rho_b, float Fx, float Fy, float Fz, float* f)
     if (cn != -1) continue;
     const int tx_ = ax == 0 ? 0 : cx, ty_ = ax == 1 ? 0 : cy, tz_ = ax == 2 ? 0 : cz;
     if (tx_ == 0 && ty_ == 0 && tz_ == 0) {
-      f[i] = f[opp19(i)] - rho_b * un * (1.f / 3.f);
+      f[i] = f[opp19(i)] - rho_b * un * (R(1) / R(3));
     } else {
-      const float t = tx_ * hx + ty_ * hy + tz_ * hz;  // sig/2 (S_a + F_a/2)
+      const R t = tx_ * hx + ty_ * hy + tz_ * hz;  // sig/2 (S_a + F_a/2)
       f[i] = f[opp19(i)] + base6 - t;
     }
   }
