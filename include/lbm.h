@@ -118,6 +118,34 @@ long long lbm_checkpoint_bytes(const lbm_ctx* ctx);
 int lbm_checkpoint(lbm_ctx* ctx, void* dst, int mem);
 int lbm_restore(lbm_ctx* ctx, const void* src, int mem);
 
+/* Discrete adjoint of the time step (no counterpart in the paper, which solves
+ * forward problems only).  The gradients are those of the FP32 step exactly
+ * as the library computes it, accumulated in FP64 over the steps.
+ *
+ * lbm_record advances n steps from the current state like lbm_step and keeps
+ * a checkpoint of the populations every K steps (device memory: n/K + 1
+ * states plus K states of recompute buffer, 104 bytes per cell each).
+ * Requirements: FP32 storage, vartheta = 0, wall faces at 90 degrees
+ * (LBM_ERR_ARG otherwise); a state must be set (LBM_ERR_STATE).
+ *
+ * lbm_adjoint_step runs the adjoint backwards through the n recorded steps (n
+ * must equal the recorded count, else LBM_ERR_STATE), recomputing each
+ * K-step segment from its checkpoint.  Inputs (device, N floats, NULL = 0):
+ * dL_drho and dL_dT, the gradient of the loss with respect to the final
+ * rho = sum f and T = sum g.  Outputs (device, NULL to skip): dL_dTface, the
+ * gradient with respect to the per-node face temperatures of lbm_set_face_T,
+ * the arrays of the non-periodic faces concatenated in face order (periodic
+ * faces contribute none), FP64; dL_dT0, N doubles, the gradient with respect
+ * to an initial temperature field T0 entering as g_i = w_i T0 (Sec. 4.2).
+ * On return the current state is the recorded final state.
+ *
+ * lbm_adjoint_state copies the adjoint of the recorded initial populations
+ * (d L / d f, 19 N floats; d L / d g, 7 N floats; mem) after lbm_adjoint_step. */
+int lbm_record(lbm_ctx* ctx, int n, int K);
+int lbm_adjoint_step(lbm_ctx* ctx, int n, const float* dL_drho, const float* dL_dT, double* dL_dTface,
+                     double* dL_dT0);
+int lbm_adjoint_state(lbm_ctx* ctx, float* f_bar, float* g_bar, int mem);
+
 /* Per-node Dirichlet temperature of non-periodic face `face` (Sec. 3.1): an
  * array over the face's two tangential coordinates, lower axis fastest
  * (z faces: nx*ny, x faces: ny*nz, y faces: nx*nz floats) (mem).  Edge and

@@ -16,29 +16,10 @@
 #include <cstdlib>
 #include <vector>
 
+#include "lbm_fused_plan.cuh"
 #include "lbm_phases.cuh"
 
 namespace lbm {
-
-enum { PH_A = 0, PH_B = 1, PH_C = 2, PH_D = 3 };
-
-struct FusedPlan {
-  int threads;           // threads per CTA
-  int tile;              // cells per work item (multiple of threads)
-  int tiles_per_plane;
-  int nstages;
-  int grid;              // persistent CTAs
-  long long total_items;
-  unsigned epoch;        // launches since the counters were cleared
-  int* stages_d;         // [nstages] phase << 24 | z
-  int* stage_first_d;    // [nstages] first item of each stage
-  int* item_stage_d;     // [total_items] stage of each item
-  std::vector<int> stage_first_h, item_stage_h;
-  unsigned* done_d;      // [4 * nz] tiles finished per (phase, plane), cumulative over launches
-  unsigned* ctr_d;       // dispatch counter, cumulative over launches
-  int* abort_d;
-  std::vector<int> stages_h;
-};
 
 struct FusedArgs {
   const float* fA;

@@ -442,6 +442,24 @@ __device__ __forceinline__ void phaseBC19(const Params& P, int c, const ST* __re
   }
 }
 
+// div u = 3 sum_i w_i c_i . u(x + c_i): the isotropic D3Q19 difference of the
+// real velocity (zero beyond a wall, the boundary node's value beyond an open face).
+__device__ __forceinline__ float divu_at(const Params& P, int c, const Nb& nb, const Aux& X, const Hint& h) {
+  float du = 0.f;
+#pragma unroll
+  for (int i = 1; i < 19; ++i) {
+    const int k = nb_kind(nb, c19x(i), c19y(i), c19z(i));
+    if (k & FACE_WALL) continue;  // zero velocity beyond a wall
+    const int n = c + nb_off(nb, c19x(i), c19y(i), c19z(i));
+    float s = 0.f;
+    if (c19x(i)) s += c19x(i) * ld_aux(X.ux + n, h);
+    if (c19y(i)) s += c19y(i) * ld_aux(X.uy + n, h);
+    if (c19z(i)) s += c19z(i) * ld_aux(X.uz + n, h);
+    du += w19(i) * s;
+  }
+  return du * 3.f;
+}
+
 // Phase C, D3Q7 part: div u by the isotropic D3Q19 difference, grad T from the
 // local moments, collision with the source, relaxed push streaming.  rho and the
 // real velocity of the cell come from phases A and B.
@@ -456,19 +474,7 @@ __device__ __forceinline__ void phaseC7_cell(const Params& P, int c, const float
   const Hint h = make_hint();
   const float rho = ld_aux(X.rho + c, h);
   const float T = sum7(gl);
-  float du = 0.f;
-#pragma unroll
-  for (int i = 1; i < 19; ++i) {
-    const int k = nb_kind(nb, c19x(i), c19y(i), c19z(i));
-    if (k & FACE_WALL) continue;  // zero velocity beyond a wall
-    const int n = c + nb_off(nb, c19x(i), c19y(i), c19z(i));
-    float s = 0.f;
-    if (c19x(i)) s += c19x(i) * ld_aux(X.ux + n, h);
-    if (c19y(i)) s += c19y(i) * ld_aux(X.uy + n, h);
-    if (c19z(i)) s += c19z(i) * ld_aux(X.uz + n, h);
-    du += w19(i) * s;
-  }
-  du *= 3.f;
+  const float du = divu_at(P, c, nb, X, h);
   float p, dpdT;
   eos_pr(P, rho, T, p, dpdT);
   float gs[7];

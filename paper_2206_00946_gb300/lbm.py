@@ -44,7 +44,8 @@ class lbm_params(ct.Structure):
 EXPORTS = ["lbm_init", "lbm_set_state", "lbm_get_state", "lbm_set_face_T", "lbm_step", "lbm_macros",
            "lbm_reduce", "lbm_sync", "lbm_stream_map", "lbm_destroy", "lbm_status_string", "lbm_Tc",
            "lbm_maxwell", "lbm_launches_per_step", "lbm_profile", "lbm_profile_read", "lbm_reduce_static",
-           "lbm_checkpoint_bytes", "lbm_checkpoint", "lbm_restore"]
+           "lbm_checkpoint_bytes", "lbm_checkpoint", "lbm_restore", "lbm_record", "lbm_adjoint_step",
+           "lbm_adjoint_state"]
 PROFILE_KINDS = ["phaseA", "phaseB", "phaseC", "phaseD", "fused", "phaseC7"]
 
 _lib = None
@@ -89,6 +90,9 @@ def load(path: str = LIB_PATH):
     L.lbm_checkpoint_bytes.restype = ct.c_longlong
     L.lbm_checkpoint.argtypes = [vp, vp, ct.c_int]
     L.lbm_restore.argtypes = [vp, vp, ct.c_int]
+    L.lbm_record.argtypes = [vp, ct.c_int, ct.c_int]
+    L.lbm_adjoint_step.argtypes = [vp, ct.c_int, vp, vp, vp, vp]
+    L.lbm_adjoint_state.argtypes = [vp, vp, vp, ct.c_int]
     _lib = L
     return L
 
@@ -202,6 +206,19 @@ class Lattice:
 
     def lbm_restore(self, src):
         _check(load().lbm_restore(self._ctx, _ptr(src), _mem_of(src)), "lbm_restore")
+
+    def lbm_record(self, n, K):
+        """Advances n steps keeping a checkpoint every K steps for lbm_adjoint_step."""
+        _check(load().lbm_record(self._ctx, int(n), int(K)), "lbm_record")
+
+    def lbm_adjoint_step(self, n, dL_drho=None, dL_dT=None, dL_dTface=None, dL_dT0=None):
+        """Adjoint of the n recorded steps; device tensors (float32 seeds, float64 outputs)."""
+        _check(load().lbm_adjoint_step(self._ctx, int(n), _ptr(dL_drho), _ptr(dL_dT), _ptr(dL_dTface),
+                                       _ptr(dL_dT0)), "lbm_adjoint_step")
+
+    def lbm_adjoint_state(self, f_bar, g_bar):
+        _check(load().lbm_adjoint_state(self._ctx, _ptr(f_bar), _ptr(g_bar), _mem_of(f_bar, g_bar)),
+               "lbm_adjoint_state")
 
     def lbm_set_face_T(self, face, T_face):
         _check(load().lbm_set_face_T(self._ctx, int(face), _ptr(T_face), _mem_of(T_face)), "lbm_set_face_T")
