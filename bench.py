@@ -150,6 +150,48 @@ def job_throughput(dist, local_s: float, units_per_rank: int, device="cpu"):
     return local_s, world * units_per_rank / local_s
 
 
+def adjoint_cost(lbm, Tc, rv, rl, schedule, stream, n=200, K=100):
+    """Adjoint / forward cost on a 64^3 droplet of radius 10 with open faces: the
+    time of lbm_adjoint_step over n recorded steps (segment recompute included)
+    over the time of n forward steps, both CUDA events on the context stream."""
+    import torch
+    p, rho0, T0 = W.droplet(Tc, rv, rl, n=64, R=10.0)
+    p["schedule"] = schedule
+    rho_d = torch.tensor(rho0.reshape(-1), dtype=torch.float32, device="cuda")
+    T_d = torch.tensor(T0.reshape(-1), dtype=torch.float32, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    lat = lbm.Lattice(p, rho_d, T_d, stream=stream.cuda_stream)
+    lat.lbm_step(20)
+    e = [ev() for _ in range(6)]
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    lat.lbm_step(n)
+    e[1].record(stream)
+    lat.close()
+    lat = lbm.Lattice(p, rho_d, T_d, stream=stream.cuda_stream)
+    e[2].record(stream)
+    lat.lbm_record(n, K)
+    e[3].record(stream)
+    rho = torch.empty_like(rho_d)
+    lat.lbm_macros(rho=rho)
+    mid, w = 0.5 * (rl + rv), 0.1 * (rl - rv)
+    th = torch.tanh((rho - mid) / w)
+    seed = (0.5 * (1 + th) + rho * 0.5 * (1 - th * th) / w).contiguous()  # d(liquid mass)/d rho
+    dT0 = torch.empty(lat.N, dtype=torch.float64, device="cuda")
+    dTf = torch.empty(6 * 64 * 64, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    e[4].record(stream)
+    lat.lbm_adjoint_step(n, seed, None, dTf, dT0)
+    e[5].record(stream)
+    torch.cuda.synchronize()
+    lat.close()
+    fwd, rec, adj = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3]), e[4].elapsed_time(e[5])
+    return {"workload": f"d2-law droplet 64^3, R=10, open faces, loss = smooth liquid mass after {n} steps, "
+                        f"checkpoint every {K} steps; gradients w.r.t. T0 and the six face-temperature fields",
+            "forward_ms_per_step": fwd / n, "record_ms_per_step": rec / n, "adjoint_ms_per_step": adj / n,
+            "ratio": adj / fwd, "ratio_with_record": (adj + rec) / fwd}
+
+
 def thermo_product():
     """T_c and the coexistence densities from the library's host helpers (not the oracle)."""
     from paper_2206_00946_gb300 import lbm
@@ -217,6 +259,7 @@ def main():
     ap.add_argument("--schedule", default="slabs", choices=["fused", "phases", "slabs"])
     ap.add_argument("--storage", default="f32", choices=list(STORAGE))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward cost measurement")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = dist_env()
@@ -309,6 +352,10 @@ def main():
         raise SystemExit(f"e2e run failed: {lbm.lbm_status_string(st2)}")
     e2e_value = job_throughput(dist, e2e_s, N * args.steps, dev)[1] / 1e6
 
+    adj = None
+    if args.storage == "f32" and not args.no_adjoint:
+        adj = adjoint_cost(lbm, Tc, rv, rl, p["schedule"], stream)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -348,6 +395,7 @@ def main():
                      "kernels": {k: {"launches": v[0], "ms_per_launch": v[1] / v[0],
                                      "share": v[1] / sum(w[1] for w in prof.values())} for k, v in prof.items()}},
         "cpu_baseline": cpu,
+        "adjoint": adj,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * N / args.steps,
                 "d2h_bytes_per_step": 5 * 4 * N / args.steps},
         "gpu_launches": launches * args.steps,

@@ -35,44 +35,35 @@ struct AdjAux {
   float *Ub;     // 3N: d L / d u from the D3Q7 collision at the cell itself
   float *Divb;   // d L / d (div u)
   float *Dpb;    // d L / d (dp/dT)
-  float *gstar;  // 7N: post-collision D3Q7 populations of the recomputed step
 };
 
+// Segment slot: the state of one step and the scratch the forward step
+// computed from it: f (19N), g (7N), rho, psi, F (3N), u (3N), div u and the
+// post-collision D3Q7 populations g* (7N) = 42 N floats.
+constexpr int kSlot = 42;
+
+Aux slot_aux(float* s, long long N, const Aux& ctxX) {
+  Aux X = ctxX;  // j is not needed by the adjoint (the step does not store it)
+  X.rho = s + 26 * N;
+  X.psi = s + 27 * N;
+  X.Fx = s + 28 * N;
+  X.Fy = s + 29 * N;
+  X.Fz = s + 30 * N;
+  X.ux = s + 31 * N;
+  X.uy = s + 32 * N;
+  X.uz = s + 33 * N;
+  X.divu = s + 34 * N;
+  X.gstar = s + 35 * N;
+  return X;
+}
+
 // ---------------------------------------------------------------- forward --
-__global__ void k_adj_A(Params P, const float* f, const float* g, Aux X, int* err) {
-  int e = 0;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x)
-    phaseA<float>(P, c, f, g, X, nullptr, e, true);
-  if (e) atomicOr(err, e);
-}
-
-__global__ void k_adj_B(Params P, Aux X) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x) phaseB(P, c, X);
-}
-
-// g* of every cell (the D3Q7 collision of phaseC7_cell without the streaming)
-__global__ void k_adj_gstar(Params P, const float* g, Aux X, float* gstar) {
-  const Hint h = make_hint();
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x) {
-    int x, y, z;
-    cell_xyz(P, c, x, y, z);
-    Nb nb;
-    make_nb(P, x, y, z, nb);
-    float gl[7];
-    for (int i = 0; i < 7; ++i) gl[i] = g[i * P.N + c];
-    const float rho = X.rho[c], T = sum7(gl);
-    const float du = divu_at(P, c, nb, X, h);
-    float p, dpdT, gs[7];
-    eos_pr(P, rho, T, p, dpdT);
-    collide7(P, gl, rho, T, X.ux[c], X.uy[c], X.uz[c], du, dpdT, gs);
-    for (int i = 0; i < 7; ++i) gstar[i * P.N + c] = gs[i];
-  }
-}
-
 __global__ void k_adj_seed(Params P, const float* rhob, const float* Tb, float* fb, float* gb) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x) {
     const float r = rhob ? rhob[c] : 0.f, t = Tb ? Tb[c] : 0.f;
+#pragma unroll
     for (int i = 0; i < 19; ++i) fb[i * P.N + c] = r;
+#pragma unroll
     for (int i = 0; i < 7; ++i) gb[i * P.N + c] = t;
   }
 }
@@ -97,6 +88,7 @@ __global__ void k_adj_faces(Params P, float* fb, float* gb, Aux X, float* Fb, DT
     if (!m) continue;
     const int c = cell_of(P, x, y, z);
     int nnp = 0, nopen = 0, oface = -1, q[3] = {x, y, z};
+#pragma unroll
     for (int fc = 0; fc < 6; ++fc) {
       if (!((m >> fc) & 1)) continue;
       ++nnp;
@@ -108,13 +100,18 @@ __global__ void k_adj_faces(Params P, float* fb, float* gb, Aux X, float* Fb, DT
     }
     // extrapolation: g_k(x_b) = w_k T_b + g_k(x_f) - w_k sum_j g_j(x_f)
     float a[7], Tb = 0.f;
+#pragma unroll
     for (int i = 0; i < 7; ++i) {
       a[i] = gb[i * N + c];
-      gb[i * N + c] = 0.f;
       Tb += (i == 0 ? w0 : w1) * a[i];
     }
     const int cf = cell_of(P, q[0], q[1], q[2]);
-    for (int i = 0; i < 7; ++i) atomicAdd(gb + i * N + cf, a[i] - Tb);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+      gb[i * N + c] = 0.f;
+      atomicAdd(gb + i * N + cf, a[i] - Tb);
+    }
+#pragma unroll
     for (int fc = 0; fc < 6; ++fc) {
       if (!((m >> fc) & 1)) continue;
       const int ax = fc >> 1;
@@ -122,8 +119,8 @@ __global__ void k_adj_faces(Params P, float* fb, float* gb, Aux X, float* Fb, DT
       dTf.p[fc][idx] += (double)Tb / nnp;  // one (face, node) entry per thread
     }
     if (nopen) {
-      const unsigned unk = unknown19(P, x, y, z);
       float fl[19];
+#pragma unroll
       for (int i = 0; i < 19; ++i) fl[i] = fb[i * N + c];
       if (nnp == 1) {
         float F3[3] = {0.f, 0.f, 0.f};
@@ -132,9 +129,12 @@ __global__ void k_adj_faces(Params P, float* fb, float* gb, Aux X, float* Fb, DT
         Fb[N + c] += F3[1];
         Fb[2 * N + c] += F3[2];
       } else {
+        const unsigned unk = unknown19(P, x, y, z);
+#pragma unroll
         for (int i = 1; i < 19; ++i)
           if ((unk >> i) & 1u) fl[i] = 0.f;  // f^eq(rho_b, 0): constant
       }
+#pragma unroll
       for (int i = 0; i < 19; ++i) fb[i * N + c] = fl[i];
     }
   }
@@ -143,20 +143,26 @@ __global__ void k_adj_faces(Params P, float* fb, float* gb, Aux X, float* Fb, DT
 // ------------------------------------------------------- D3Q19 transpose ----
 // d L / d f*(x) gathered from the slots the push wrote (bounce-back included),
 // then the collision's vector-Jacobian product.
-__global__ void k_adj_c19(Params P, const float* f, const float* fb1, float* fb0, Aux X, float* Fb) {
+__global__ void __launch_bounds__(256, 2) k_adj_c19(Params P, const float* f, const float* fb1, float* fb0, Aux X,
+                                                     float* Fb) {
   const long long N = P.N;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)N; c += gridDim.x * blockDim.x) {
     int x, y, z;
     cell_xyz(P, c, x, y, z);
+    Nb nb;
+    make_nb(P, x, y, z, nb);
     float fl[19], fsb[19], fbo[19], F3[3] = {X.Fx[c], X.Fy[c], X.Fz[c]}, Fo[3];
+#pragma unroll
     for (int i = 0; i < 19; ++i) {
       fl[i] = f[i * N + c];
-      const long long d = dest19(P, x, y, z, i);
-      fsb[i] = d < 0 ? 0.f : fb1[d];
+      const int k = nb_kind(nb, c19x(i), c19y(i), c19z(i));
+      fsb[i] = k == 0 ? fb1[i * N + c + nb_off(nb, c19x(i), c19y(i), c19z(i))]
+                      : ((k & FACE_WALL) ? fb1[opp19(i) * N + c] : 0.f);
     }
     const int m = P.any_nonperiodic ? node_faces(P, x, y, z) : 0;
     const bool wall = m && on_wall(P, m);
     collide19_vjp(P, fl, !(wall && P.wall_ueq_zero), F3, fsb, fbo, Fo);
+#pragma unroll
     for (int i = 0; i < 19; ++i) fb0[i * N + c] = fbo[i];
     Fb[c] += Fo[0];
     Fb[N + c] += Fo[1];
@@ -170,37 +176,48 @@ __global__ void k_adj_c19(Params P, const float* f, const float* fb1, float* fb0
 // retained g_i(x) and rho(x) c_v), then the D3Q7 collision's product.
 __global__ void k_adj_c7(Params P, const float* g, const float* gb1, float* gb0, Aux X, AdjAux A) {
   const long long N = P.N;
-  const Hint h = make_hint();
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)N; c += gridDim.x * blockDim.x) {
     int x, y, z;
     cell_xyz(P, c, x, y, z);
     Nb nb;
     make_nb(P, x, y, z, nb);
     float gl[7], gsb[7], gout[7];
+#pragma unroll
     for (int i = 0; i < 7; ++i) gl[i] = g[i * N + c];
     const float rho = X.rho[c], T = sum7(gl);
     const float beta = 1.f / (rho * P.cv);
-    float rhob = 0.f;
-    for (int i = 0; i < 7; ++i) {
-      const float a = gb1[i * N + c];
+    // rest population: source and destination are the cell itself
+    float a = gb1[c];
+    gsb[0] = a * beta;
+    gout[0] = (1.f - beta) * a;
+    float rhob = -a * (X.gstar[c] - gl[0]) * beta / rho;
+#pragma unroll
+    for (int i = 1; i < 7; ++i) {
+      const int ax = (i - 1) >> 1, s = (i & 1) ? 1 : 0;  // s: 1 for +c, 0 for -c
+      a = gb1[i * N + c];
       // as a source: population i goes to y = x + c_i
-      const int yd = dest7_cell(P, x, y, z, i);
-      gsb[i] = yd < 0 ? 0.f : gb1[i * N + yd] / (X.rho[yd] * P.cv);
-      // as a destination: the source x - c_i
-      const int s = dest7_cell(P, x, y, z, i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1));
-      if (s < 0) {
-        gout[i] = a;
+      if (nb.kind[ax][s] == 0) {
+        const int yd = c + nb.off[ax][s];
+        gsb[i] = gb1[i * N + yd] / (X.rho[yd] * P.cv);
       } else {
+        gsb[i] = 0.f;
+      }
+      // as a destination: the source x - c_i
+      if (nb.kind[ax][1 - s] == 0) {
+        const int sc = c + nb.off[ax][1 - s];
         gout[i] = (1.f - beta) * a;
-        rhob -= a * (A.gstar[i * N + s] - gl[i]) * beta / rho;
+        rhob -= a * (X.gstar[i * N + sc] - gl[i]) * beta / rho;
+      } else {
+        gout[i] = a;
       }
     }
-    const float du = divu_at(P, c, nb, X, h);
+    const float du = X.divu[c];
     float p, dpdT;
     eos_pr(P, rho, T, p, dpdT);
     const float u3[3] = {X.ux[c], X.uy[c], X.uz[c]};
     float gbv[7], rb7, Tb, ub[3], divb, dpb;
     collide7_vjp(P, gl, rho, T, u3, du, dpdT, gsb, gbv, rb7, Tb, ub, divb, dpb);
+#pragma unroll
     for (int i = 0; i < 7; ++i) gb0[i * N + c] = gout[i] + gbv[i] + Tb;
     A.Rb[c] = rhob + rb7;
     A.Ub[c] = ub[0];
@@ -211,31 +228,80 @@ __global__ void k_adj_c7(Params P, const float* g, const float* gb1, float* gb0,
   }
 }
 
-// Per-axis preimages under the ghost rule of a stencil: the coordinates x_a
-// whose move by c lands on ya.  mode 0 (psi): open faces copy the boundary
-// node, walls mirror through the wall layer; mode 1 (velocity): open faces
-// copy, moves across a wall contribute nothing.  Periodic faces wrap.
-__device__ __forceinline__ int preimage_axis(const Params& P, int a, int ya, int c, int mode, int* xs) {
-  if (c == 0) {
-    xs[0] = ya;
-    return 1;
-  }
+// ------------------------------------------------- stencil transposes -------
+// A stencil read of the forward step at x in direction c (the psi force, the
+// div u difference) lands on the cell y = x + c, or, beyond a non-periodic
+// face, on the ghost rule's image (open face: the boundary node itself; wall,
+// psi only: the mirror node; wall, velocity: nothing).  Its transpose at y
+// gathers from every such x.  The main source x = y - c exists exactly when
+// the move from y by -c crosses no non-periodic face; the other sources (an
+// "extra" coordinate on some axis) exist only for y on or next to a face.
+// Extra source coordinate of ya on axis a for a move of sign sg (-1: none).
+__device__ __forceinline__ int extra_coord(const Params& P, int a, int ya, int sg, int mode) {
+  if (P.face_kind[2 * a] == FACE_PERIODIC) return -1;
   const int n = dim_of(P, a);
-  const bool per = P.face_kind[2 * a] == FACE_PERIODIC;
-  int cnt = 0;
-  const int s = ya - c;
-  if (s >= 0 && s < n) xs[cnt++] = s;
-  else if (per) xs[cnt++] = wrapi(s, n);
-  if (!per) {
-    const int b = c > 0 ? n - 1 : 0;  // the boundary coordinate a move by c leaves from
-    const int kind = P.face_kind[2 * a + (c > 0 ? 1 : 0)];
-    if (kind == FACE_OPEN && ya == b) xs[cnt++] = b;
-    if (kind == FACE_WALL && mode == 0 && ya == b - c) xs[cnt++] = b;
-  }
-  return cnt;
+  const int b = sg > 0 ? n - 1 : 0;
+  const int kind = P.face_kind[2 * a + (sg > 0 ? 1 : 0)];
+  if (kind == FACE_OPEN && ya == b) return b;
+  if (kind == FACE_WALL && mode == 0 && ya == b - sg) return b;
+  return -1;
 }
 
-// --------------------------------------- velocity, force and EOS transposes --
+// Extra coordinates of a cell for the six (axis, sign) pairs; bit 2a+(sg>0) of
+// the returned mask is set where one exists.
+__device__ __forceinline__ unsigned extra_table(const Params& P, const int* q, int mode, int (*ec)[2]) {
+  unsigned m = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      ec[a][s] = extra_coord(P, a, q[a], s ? 1 : -1, mode);
+      m |= (ec[a][s] >= 0 ? 1u : 0u) << (2 * a + s);
+    }
+  return m;
+}
+
+// main source coordinate of ya for a move by c (-1: none)
+__device__ __forceinline__ int main_coord(const Params& P, int a, int ya, int c) {
+  if (c == 0) return ya;
+  const int n = dim_of(P, a), s = ya - c;
+  if (s >= 0 && s < n) return s;
+  return P.face_kind[2 * a] == FACE_PERIODIC ? wrapi(s, n) : -1;
+}
+
+// sum of val(x) over the sources of a move (cx, cy, cz) with at least one
+// extra coordinate
+template <typename V>
+__device__ __forceinline__ float extra_sources(const Params& P, const int* q, int cx, int cy, int cz,
+                                               const int (*ec)[2], V val) {
+  const int c3[3] = {cx, cy, cz};
+  int mc[3], e3[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    mc[a] = main_coord(P, a, q[a], c3[a]);
+    e3[a] = c3[a] ? ec[a][c3[a] > 0] : -1;
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int msk = 1; msk < 8; ++msk) {
+    int r[3];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      r[a] = ((msk >> a) & 1) ? e3[a] : mc[a];
+      ok = ok && r[a] >= 0;
+    }
+    if (ok) s += val(cell_of(P, r[0], r[1], r[2]));
+  }
+  return s;
+}
+
+// does the move (cx, cy, cz) have an extra source at a cell with mask m
+__device__ __forceinline__ bool has_extra(unsigned m, int cx, int cy, int cz) {
+  return (cx && ((m >> (0 + (cx > 0))) & 1)) || (cy && ((m >> (2 + (cy > 0))) & 1)) ||
+         (cz && ((m >> (4 + (cz > 0))) & 1));
+}
+
 // d L / d u(y) = the D3Q7 collision's own term + the div u stencil transposed,
 // then u = (j + F/2) / rho (zero at walls): d L / d j, d L / d F, d L / d rho.
 __global__ void k_adj_u(Params P, Aux X, AdjAux A, float* Jb) {
@@ -243,24 +309,26 @@ __global__ void k_adj_u(Params P, Aux X, AdjAux A, float* Jb) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)N; c += gridDim.x * blockDim.x) {
     int q[3];
     cell_xyz(P, c, q[0], q[1], q[2]);
+    Nb nb;
+    make_nb(P, q[0], q[1], q[2], nb);
     float ub[3] = {A.Ub[c], A.Ub[N + c], A.Ub[2 * N + c]};
+    int ec[3][2];
+    const unsigned em = P.any_nonperiodic ? extra_table(P, q, 1, ec) : 0u;
+#pragma unroll
     for (int i = 1; i < 19; ++i) {
-      const int ci[3] = {c19x(i), c19y(i), c19z(i)};
-      int xs[3][2], cn[3];
-      for (int a = 0; a < 3; ++a) cn[a] = preimage_axis(P, a, q[a], ci[a], 1, xs[a]);
-      float s = 0.f;
-      for (int i0 = 0; i0 < cn[0]; ++i0)
-        for (int i1 = 0; i1 < cn[1]; ++i1)
-          for (int i2 = 0; i2 < cn[2]; ++i2) s += A.Divb[cell_of(P, xs[0][i0], xs[1][i1], xs[2][i2])];
+      const int cx = c19x(i), cy = c19y(i), cz = c19z(i);
+      float s = nb_kind(nb, -cx, -cy, -cz) == 0 ? A.Divb[c + nb_off(nb, -cx, -cy, -cz)] : 0.f;
+      if (has_extra(em, cx, cy, cz)) s += extra_sources(P, q, cx, cy, cz, ec, [&](int x) { return A.Divb[x]; });
       const float k = 3.f * w19(i) * s;
-      ub[0] += ci[0] * k;
-      ub[1] += ci[1] * k;
-      ub[2] += ci[2] * k;
+      ub[0] += cx * k;
+      ub[1] += cy * k;
+      ub[2] += cz * k;
     }
     const int m = P.any_nonperiodic ? node_faces(P, q[0], q[1], q[2]) : 0;
     float j3[3] = {0.f, 0.f, 0.f};
     if (!(m && on_wall(P, m))) {
-      const float rho = X.rho[c], ir = 1.f / rho;
+      const float ir = 1.f / X.rho[c];
+#pragma unroll
       for (int a = 0; a < 3; ++a) {
         j3[a] = ub[a] * ir;
         A.Fb[a * N + c] += 0.5f * ub[a] * ir;
@@ -273,12 +341,9 @@ __global__ void k_adj_u(Params P, Aux X, AdjAux A, float* Jb) {
   }
 }
 
-// d L / d psi(y) from F(x) = -G psi(x) sum_i varpi_i psi(x + c_i) c_i (own and
-// transposed stencil terms), the EOS chain rule to rho and T, and the
-// macroscopic fields rho = sum f, j = sum c f, T = sum g folded into the
-// adjoint of the populations at time t.
-__global__ void k_adj_psi(Params P, const float* f, const float* g, Aux X, AdjAux A, const float* Jb, float* fb0,
-                          float* gb0) {
+// d L / d psi(y) from F(x) = -G psi(x) sum_i varpi_i psi(x + c_i) c_i: the
+// cell's own factor and the transposed stencil.
+__global__ void k_adj_psi(Params P, Aux X, AdjAux A, float* Psib) {
   const long long N = P.N;
   const Hint h = make_hint();
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)N; c += gridDim.x * blockDim.x) {
@@ -286,33 +351,42 @@ __global__ void k_adj_psi(Params P, const float* f, const float* g, Aux X, AdjAu
     cell_xyz(P, c, q[0], q[1], q[2]);
     Nb nb;
     make_nb(P, q[0], q[1], q[2], nb);
-    const float psi = X.psi[c];
+    int ec[3][2];
+    const unsigned em = P.any_nonperiodic ? extra_table(P, q, 0, ec) : 0u;
     float S[3] = {0.f, 0.f, 0.f};
     float psib = 0.f;
+#pragma unroll
     for (int i = 1; i < 19; ++i) {
-      const int ci[3] = {c19x(i), c19y(i), c19z(i)};
-      const float v = varpi19(i) * ld_aux(X.psi + c + nb_off_psi(nb, ci[0], ci[1], ci[2]), h);
-      S[0] += ci[0] * v;
-      S[1] += ci[1] * v;
-      S[2] += ci[2] * v;
-      int xs[3][2], cn[3];
-      for (int a = 0; a < 3; ++a) cn[a] = preimage_axis(P, a, q[a], ci[a], 0, xs[a]);
-      for (int i0 = 0; i0 < cn[0]; ++i0)
-        for (int i1 = 0; i1 < cn[1]; ++i1)
-          for (int i2 = 0; i2 < cn[2]; ++i2) {
-            const int x = cell_of(P, xs[0][i0], xs[1][i1], xs[2][i2]);
-            psib += -P.G * X.psi[x] * varpi19(i) *
-                    (ci[0] * A.Fb[x] + ci[1] * A.Fb[N + x] + ci[2] * A.Fb[2 * N + x]);
-          }
+      const int cx = c19x(i), cy = c19y(i), cz = c19z(i);
+      const float v = varpi19(i) * ld_aux(X.psi + c + nb_off_psi(nb, cx, cy, cz), h);
+      S[0] += cx * v;
+      S[1] += cy * v;
+      S[2] += cz * v;
+      auto term = [&](int x) { return X.psi[x] * (cx * A.Fb[x] + cy * A.Fb[N + x] + cz * A.Fb[2 * N + x]); };
+      float t = nb_kind(nb, -cx, -cy, -cz) == 0 ? term(c + nb_off(nb, -cx, -cy, -cz)) : 0.f;
+      if (has_extra(em, cx, cy, cz)) t += extra_sources(P, q, cx, cy, cz, ec, term);
+      psib += varpi19(i) * t;
     }
-    psib += -P.G * (A.Fb[c] * S[0] + A.Fb[N + c] * S[1] + A.Fb[2 * N + c] * S[2]);
-    float gl[7];
-    for (int i = 0; i < 7; ++i) gl[i] = g[i * N + c];
-    const float rho = X.rho[c], T = sum7(gl);
+    Psib[c] = -P.G * (psib + A.Fb[c] * S[0] + A.Fb[N + c] * S[1] + A.Fb[2 * N + c] * S[2]);
+  }
+}
+
+// The EOS chain rule of psi and dp/dT to rho and T, and the macroscopic fields
+// rho = sum f, j = sum c f, T = sum g folded into the adjoint of the
+// populations at time t.
+__global__ void k_adj_fold(Params P, const float* g, Aux X, AdjAux A, const float* Jb, const float* Psib, float* fb0,
+                           float* gb0) {
+  const long long N = P.N;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)N; c += gridDim.x * blockDim.x) {
+    float T = 0.f;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) T += g[i * N + c];
     float rhob = A.Rb[c], Tb = 0.f;
-    psi_dpdT_vjp(P, rho, T, psi, psib, A.Dpb[c], rhob, Tb);
+    psi_dpdT_vjp(P, X.rho[c], T, X.psi[c], Psib[c], A.Dpb[c], rhob, Tb);
     const float jx = Jb[c], jy = Jb[N + c], jz = Jb[2 * N + c];
+#pragma unroll
     for (int i = 0; i < 19; ++i) fb0[i * N + c] += rhob + c19x(i) * jx + c19y(i) * jy + c19z(i) * jz;
+#pragma unroll
     for (int i = 0; i < 7; ++i) gb0[i * N + c] += Tb;
   }
 }
@@ -332,12 +406,19 @@ __global__ void k_adj_T0(Params P, const float* gb, double* out) {
 // ------------------------------------------------------------------- host --
 struct AdjRec {
   int K = 0, nrec = 0, cur = 0;
+  bool last_kept = false;    // seg holds the last segment, computed by lbm_record
   long long N = 0;
   std::vector<float*> ckpt;  // f (19N) + g (7N) at steps 0, K, 2K, ...
-  float* seg = nullptr;      // the K states of the segment being reversed
+  float* fin = nullptr;      // the recorded final state (f, g)
+  float* seg[2] = {nullptr, nullptr};  // K + 1 slots of kSlot * N floats each: the segment being
+                                       // reversed and (when memory allows) the next one, recomputed
+                                       // meanwhile on the side stream
+  cudaStream_t side = nullptr, side2 = nullptr;
+  cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_adj[2] = {nullptr, nullptr}, ev_fork = nullptr,
+              ev_c19 = nullptr;
   float* fb[2] = {nullptr, nullptr};
   float* gb[2] = {nullptr, nullptr};
-  float* scr = nullptr;      // AdjAux fields + Jb
+  float* scr = nullptr;      // AdjAux fields + d L / d j
   double* dTf = nullptr;     // per-face accumulators, faces concatenated
   long long face_off[7] = {0, 0, 0, 0, 0, 0, 0};
 };
@@ -346,7 +427,22 @@ void adj_free(lbm_ctx* c) {
   if (!c || !c->adj) return;
   AdjRec* r = c->adj;
   for (float* p : r->ckpt) cudaFree(p);
-  cudaFree(r->seg);
+  cudaFree(r->fin);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(r->seg[k]);
+    if (r->ev_rec[k]) cudaEventDestroy(r->ev_rec[k]);
+    if (r->ev_adj[k]) cudaEventDestroy(r->ev_adj[k]);
+  }
+  if (r->ev_fork) cudaEventDestroy(r->ev_fork);
+  if (r->ev_c19) cudaEventDestroy(r->ev_c19);
+  if (r->side) {
+    cudaStreamSynchronize(r->side);
+    cudaStreamDestroy(r->side);
+  }
+  if (r->side2) {
+    cudaStreamSynchronize(r->side2);
+    cudaStreamDestroy(r->side2);
+  }
   for (int k = 0; k < 2; ++k) {
     cudaFree(r->fb[k]);
     cudaFree(r->gb[k]);
@@ -396,13 +492,48 @@ int flags(lbm_ctx* c) {
   return LBM_OK;
 }
 
-// One adjoint step through the step from state s (f = s, g = s + 19N):
+// Recomputes len steps from the checkpoint ck: slot t receives state t and the
+// scratch (rho, psi, F, u) the step computed from it.  The phase kernels write
+// straight into the slots (the context's buffers are pointed at them).
+// The launches go to `stream` (the context's stream is swapped for it meanwhile).
+int recompute(lbm_ctx* c, float* seg, const float* ck, int len, cudaStream_t stream) {
+  const long long N = c->N;
+  int st = cst(cudaMemcpyAsync(seg, ck, 26ull * N * sizeof(float), cudaMemcpyDeviceToDevice, stream));
+  if (st) return st;
+  void* f0[2] = {c->f[0], c->f[1]};
+  void* g0[2] = {c->g[0], c->g[1]};
+  const Aux X0 = c->X;
+  const int cur0 = c->cur;
+  cudaStream_t s0 = c->stream;
+  c->stream = stream;
+  for (int t = 0; t < len && !st; ++t) {
+    float* s = seg + (size_t)kSlot * N * t;
+    float* s1 = s + (size_t)kSlot * N;
+    c->f[c->cur] = s;
+    c->g[c->cur] = s + 19 * N;
+    c->f[1 - c->cur] = s1;
+    c->g[1 - c->cur] = s1 + 19 * N;
+    c->X = slot_aux(s, N, X0);
+    st = lbm_step_phases_internal(c);
+  }
+  c->f[0] = f0[0];
+  c->f[1] = f0[1];
+  c->g[0] = g0[0];
+  c->g[1] = g0[1];
+  c->X = X0;
+  c->cur = cur0;
+  c->stream = s0;
+  return st;
+}
+
+// One adjoint step through the step from slot s:
 // (fb1, gb1) = d L / d state(t+1) -> (fb0, gb0) = d L / d state(t).
-int adjoint_one(lbm_ctx* c, AdjRec* r, const float* s, float* fb1, float* gb1, float* fb0, float* gb0) {
+int adjoint_one(lbm_ctx* c, AdjRec* r, float* s, float* fb1, float* gb1, float* fb0, float* gb0) {
   const Params& P = c->P;
   const long long N = c->N;
   const float* f = s;
   const float* g = s + 19 * N;
+  const Aux X = slot_aux(s, N, c->X);
   cudaStream_t st = c->stream;
   const int B = blocks_for(N);
   float* q = r->scr;
@@ -412,23 +543,25 @@ int adjoint_one(lbm_ctx* c, AdjRec* r, const float* s, float* fb1, float* gb1, f
   A.Ub = q + 4 * N;
   A.Divb = q + 7 * N;
   A.Dpb = q + 8 * N;
-  A.gstar = q + 9 * N;
-  float* Jb = q + 16 * N;
-  // forward quantities of step t
-  k_adj_A<<<B, kT, 0, st>>>(P, f, g, c->X, c->err_d);
-  k_adj_B<<<B, kT, 0, st>>>(P, c->X);
-  k_adj_gstar<<<B, kT, 0, st>>>(P, g, c->X, A.gstar);
+  float* Jb = q + 9 * N;
+  float* Psib = q + 12 * N;
   if (cudaMemsetAsync(A.Fb, 0, 3 * N * sizeof(float), st) != cudaSuccess) return LBM_ERR_CUDA;
   // transposes, last forward operation first
   if (P.bd_total > 0) {
     DT6 d;
     for (int k = 0; k < 6; ++k) d.p[k] = r->face_off[k + 1] > r->face_off[k] ? r->dTf + r->face_off[k] : nullptr;
-    k_adj_faces<<<blocks_for(P.bd_total), kT, 0, st>>>(P, fb1, gb1, c->X, A.Fb, d);
+    k_adj_faces<<<(int)((P.bd_total + 63) / 64), 64, 0, st>>>(P, fb1, gb1, X, A.Fb, d);
   }
-  k_adj_c19<<<B, kT, 0, st>>>(P, f, fb1, fb0, c->X, A.Fb);
-  k_adj_c7<<<B, kT, 0, st>>>(P, g, gb1, gb0, c->X, A);
-  k_adj_u<<<B, kT, 0, st>>>(P, c->X, A, Jb);
-  k_adj_psi<<<B, kT, 0, st>>>(P, f, g, c->X, A, Jb, fb0, gb0);
+  // the two lattices' transposes are independent: D3Q19 on a second stream
+  cudaEventRecord(r->ev_fork, st);
+  cudaStreamWaitEvent(r->side2, r->ev_fork, 0);
+  k_adj_c19<<<B, kT, 0, r->side2>>>(P, f, fb1, fb0, X, A.Fb);
+  cudaEventRecord(r->ev_c19, r->side2);
+  k_adj_c7<<<B, kT, 0, st>>>(P, g, gb1, gb0, X, A);
+  cudaStreamWaitEvent(st, r->ev_c19, 0);
+  k_adj_u<<<B, kT, 0, st>>>(P, X, A, Jb);
+  k_adj_psi<<<B, kT, 0, st>>>(P, X, A, Psib);
+  k_adj_fold<<<B, kT, 0, st>>>(P, g, X, A, Jb, Psib, fb0, gb0);
   return cst(cudaGetLastError());
 }
 
@@ -455,22 +588,49 @@ extern "C" int lbm_record(lbm_ctx* c, int n, int K) {
     if (!st) r->ckpt.push_back(p);
   }
   for (int k = 0; k < 6; ++k) r->face_off[k + 1] = r->face_off[k] + face_nodes(c->hp, k);
-  if (!st) st = cst(cudaMalloc(&r->seg, 26ull * N * sizeof(float) * (size_t)std::min(K, std::max(n, 1))));
+  const size_t slots = (size_t)std::min(K, std::max(n, 1)) + 1;
+  if (!st) st = cst(cudaMalloc(&r->seg[0], (size_t)kSlot * N * sizeof(float) * slots));
+  if (!st && n > K) {  // second segment buffer for the overlapped recompute, if it fits
+    if (cudaMalloc(&r->seg[1], (size_t)kSlot * N * sizeof(float) * slots) != cudaSuccess) {
+      r->seg[1] = nullptr;
+      cudaGetLastError();
+    }
+  }
+  if (!st) st = cst(cudaStreamCreateWithFlags(&r->side, cudaStreamNonBlocking));
+  if (!st) st = cst(cudaStreamCreateWithFlags(&r->side2, cudaStreamNonBlocking));
+  for (int k = 0; k < 2 && !st; ++k) {
+    st = cst(cudaEventCreateWithFlags(&r->ev_rec[k], cudaEventDisableTiming));
+    if (!st) st = cst(cudaEventCreateWithFlags(&r->ev_adj[k], cudaEventDisableTiming));
+  }
+  if (!st) st = cst(cudaEventCreateWithFlags(&r->ev_fork, cudaEventDisableTiming));
+  if (!st) st = cst(cudaEventCreateWithFlags(&r->ev_c19, cudaEventDisableTiming));
   for (int k = 0; k < 2 && !st; ++k) {
     st = cst(cudaMalloc(&r->fb[k], 19ull * N * sizeof(float)));
     if (!st) st = cst(cudaMalloc(&r->gb[k], 7ull * N * sizeof(float)));
   }
-  if (!st) st = cst(cudaMalloc(&r->scr, 19ull * N * sizeof(float)));
+  if (!st) st = cst(cudaMalloc(&r->scr, 13ull * N * sizeof(float)));
+  if (!st) st = cst(cudaMalloc(&r->fin, 26ull * N * sizeof(float)));
   if (!st) st = cst(cudaMalloc(&r->dTf, sizeof(double) * std::max(1LL, r->face_off[6])));
-  // forward run, a checkpoint every K steps
+  // forward run, a checkpoint every K steps; the last segment's steps are
+  // computed into the recompute slots, where the adjoint starts
+  const int nseg = (n + K - 1) / K;
+  const int tlast = nseg > 0 ? (nseg - 1) * K : 0;
   int done = 0;
   if (!st) st = save_state(c, r->ckpt[0]);
-  while (!st && done < n) {
-    const int len = std::min(K, n - done);
-    st = lbm_step(c, len);
-    done += len;
-    if (!st && done % K == 0 && done / K < nck) st = save_state(c, r->ckpt[done / K]);
+  while (!st && done < tlast) {
+    st = lbm_step(c, K);
+    done += K;
+    if (!st && done / K < nck) st = save_state(c, r->ckpt[done / K]);
   }
+  if (!st && n > tlast) {
+    const int len = n - tlast;
+    st = recompute(c, r->seg[0], r->ckpt[tlast / K], len, c->stream);
+    // the state after the last step is slot len: make it current
+    if (!st) st = load_state(c, r->seg[0] + (size_t)kSlot * N * len);
+    if (!st && n % K == 0 && n / K < nck) st = save_state(c, r->ckpt[n / K]);
+    r->last_kept = !st;
+  }
+  if (!st) st = save_state(c, r->fin);
   if (!st) st = flags(c);
   if (st) {
     adj_free(c);
@@ -492,22 +652,39 @@ extern "C" int lbm_adjoint_step(lbm_ctx* c, int n, const float* dL_drho, const f
   k_adj_seed<<<blocks_for(N), kT, 0, st>>>(c->P, dL_drho, dL_dT, r->fb[0], r->gb[0]);
   const int K = r->K;
   const int nseg = (n + K - 1) / K;
+  // Segment k is reversed from buffer set[k]; while it is, segment k-1 is
+  // recomputed into the other buffer on the side stream (when there is one).
+  const bool two = r->seg[1] != nullptr;
+  auto set_of = [&](int k) { return two ? (nseg - 1 - k) & 1 : 0; };
+  auto launch_recompute = [&](int k) {
+    const int b = set_of(k);
+    if (two) cudaStreamWaitEvent(r->side, r->ev_adj[b], 0);  // its previous user is done
+    else cudaStreamWaitEvent(r->side, r->ev_adj[0], 0);
+    int e = recompute(c, r->seg[b], r->ckpt[k], std::min(K, n - k * K), r->side);
+    if (!e) e = cst(cudaEventRecord(r->ev_rec[b], r->side));
+    return e;
+  };
+  for (int b = 0; b < 2 && !s; ++b) s = cst(cudaEventRecord(r->ev_adj[b], st));
+  if (nseg > 0 && !s && !r->last_kept) s = launch_recompute(nseg - 1);
+  const bool last_was_kept = r->last_kept;
   for (int k = nseg - 1; k >= 0 && !s; --k) {
-    const int t0 = k * K, len = std::min(K, n - t0);
-    // recompute the segment's states from its checkpoint
-    s = load_state(c, r->ckpt[k]);
-    for (int t = 0; t < len && !s; ++t) {
-      s = save_state(c, r->seg + 26 * N * t);
-      if (!s && t + 1 < len) s = lbm_step(c, 1);
-    }
+    const int t0 = k * K, len = std::min(K, n - t0), b = set_of(k);
+    if (!(k == nseg - 1 && last_was_kept)) s = cst(cudaStreamWaitEvent(st, r->ev_rec[b], 0));
+    if (!s && k > 0 && two) s = launch_recompute(k - 1);  // overlapped with this segment
     for (int t = len - 1; t >= 0 && !s; --t) {
-      s = adjoint_one(c, r, r->seg + 26 * N * t, r->fb[cur], r->gb[cur], r->fb[1 - cur], r->gb[1 - cur]);
+      s = adjoint_one(c, r, r->seg[b] + (size_t)kSlot * N * t, r->fb[cur], r->gb[cur], r->fb[1 - cur],
+                      r->gb[1 - cur]);
       cur = 1 - cur;
     }
+    if (!s) s = cst(cudaEventRecord(r->ev_adj[b], st));
+    if (!s && k > 0 && !two) s = launch_recompute(k - 1);  // serial: after this segment
   }
+  if (nseg > 1) r->last_kept = false;
+  // the side streams' work is done before the stream continues
+  if (!s) s = cst(cudaEventRecord(r->ev_rec[0], r->side));
+  if (!s) s = cst(cudaStreamWaitEvent(st, r->ev_rec[0], 0));
   // leave the recorded final state current
-  if (!s) s = load_state(c, r->ckpt.back());
-  if (!s && n % K != 0) s = lbm_step(c, n % K);
+  if (!s) s = load_state(c, r->fin);
   if (!s && dL_dT0) k_adj_T0<<<blocks_for(N), kT, 0, st>>>(c->P, r->gb[cur], dL_dT0);
   if (!s && dL_dTface && r->face_off[6] > 0)
     s = cst(cudaMemcpyAsync(dL_dTface, r->dTf, sizeof(double) * r->face_off[6], cudaMemcpyDeviceToDevice, st));

@@ -46,6 +46,7 @@ LBM_HD R meq_contract(const Params& P, const R* v, R ux, R uy, R uz, R* g) {
 // Transpose of the hand-solved f* = M-hat^-1 n of collide19: nb = M-hat^-T b.
 template <typename R>
 LBM_HD void minv19_T(const R* b, R* nb) {
+#pragma unroll
   for (int k = 0; k < 19; ++k) nb[k] = R(0);
   const R q = R(1) / R(4);
   nb[0] = b[0];
@@ -133,11 +134,15 @@ LBM_HD void collide19_vjp(const Params& P, const R* f, bool ueq_from_f, const R*
   R s[19];
   s[0] = s[1] = s[2] = s[3] = R(1);
   s[4] = R(P.s_e);
+#pragma unroll
   for (int k = 5; k <= 9; ++k) s[k] = R(P.s_v);
+#pragma unroll
   for (int k = 10; k <= 15; ++k) s[k] = R(P.s_q);
+#pragma unroll
   for (int k = 16; k <= 18; ++k) s[k] = R(P.s_pi);
   // n_k = (1 - s_k) m_k + (s_k - 1) rho e_k(u) + rho e_k(u')
   R v0[19], mb[19];
+#pragma unroll
   for (int k = 0; k < 19; ++k) {
     v0[k] = (s[k] - R(1)) * nb[k];
     mb[k] = (R(1) - s[k]) * nb[k];
@@ -205,6 +210,7 @@ LBM_HD void collide7_vjp(const Params& P, const R* g, R rho, R T, const R* u, R 
     const R phi = (rho - R(P.rho_v)) * R(P.inv_drho);
     if (phi > R(0) && phi < R(1)) rhob += lamb * (R(P.lambda_l) - R(P.lambda_v)) * R(P.inv_drho);
   }
+#pragma unroll
   for (int i = 0; i < 7; ++i) gb[i] = R(0);
   gb[1] = mb1;
   gb[2] = -mb1;
@@ -223,6 +229,7 @@ LBM_HD void zouhe_vjp(int face, R rho_b, R* fb, R* Fb) {
   const int ax = face >> 1;
   const int sg = (face & 1) ? 1 : -1;
   R unb = R(0), Fnb = R(0), Sb[3] = {R(0), R(0), R(0)};
+#pragma unroll
   for (int i = 1; i < 19; ++i) {
     const int cx = c19x(i), cy = c19y(i), cz = c19z(i);
     const int cn = sg * (ax == 0 ? cx : (ax == 1 ? cy : cz));
@@ -236,6 +243,7 @@ LBM_HD void zouhe_vjp(int face, R rho_b, R* fb, R* Fb) {
     } else {
       unb -= rho_b * b / R(6);
       Fnb += b / R(8);
+#pragma unroll
       for (int a = 0; a < 3; ++a)
         if (t[a]) {  // - (sig/2) (S_a + F_a / 2)
           Sb[a] -= R(0.5) * R(t[a]) * b;
@@ -245,6 +253,7 @@ LBM_HD void zouhe_vjp(int face, R rho_b, R* fb, R* Fb) {
   }
   // u_n = (sum_Z f + 2 sum_P f + F_n/2) / rho_b - 1; S_a = sum_Z c_a f
   const R ir = R(1) / rho_b;
+#pragma unroll
   for (int i = 0; i < 19; ++i) {
     const int c[3] = {c19x(i), c19y(i), c19z(i)};
     const int cn = sg * c[ax];

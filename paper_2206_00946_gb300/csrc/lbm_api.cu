@@ -426,8 +426,9 @@ template <typename T>
 int step_phases_t(lbm_ctx* c) {
   const int a = c->cur, b = 1 - c->cur;
   cudaEvent_t e = prof_begin(c);
+  // j is stored only for the staged path, whose separate phase B reads it
   k_phaseA<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, a), gbuf<T>(c, a), c->X, nullptr, c->err_d, 0,
-                                                   (int)c->N, 0);
+                                                   (int)c->N, c->bulk_grid > 0 ? 1 : 0);
   prof_end(c, 0, e);
   if (c->bulk_grid > 0) {  // FP32 storage only: staged C19 + C7 after a separate phase B
     e = prof_begin(c);
@@ -456,6 +457,12 @@ int step_phases_t(lbm_ctx* c) {
 }
 
 int step_phases(lbm_ctx* c) { return LBM_WITH_STORAGE(c, step_phases_t, c); }
+}  // namespace
+
+// one step of the phase schedule on the context's current buffers and scratch
+int lbm_step_phases_internal(lbm_ctx* c) { return step_phases(c); }
+
+namespace {
 
 
 // ----------------------------------------------------------- slab pipeline --

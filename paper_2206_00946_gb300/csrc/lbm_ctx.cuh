@@ -14,6 +14,7 @@ using namespace lbm;
 
 struct AdjRec;  // recorded forward run of the discrete adjoint (lbm_adjoint.cu)
 void adj_free(lbm_ctx* c);
+int lbm_step_phases_internal(lbm_ctx* c);  // one step, one launch per phase
 
 #define LBM_PROF_KINDS 6
 

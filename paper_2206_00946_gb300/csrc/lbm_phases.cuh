@@ -19,6 +19,7 @@ namespace lbm {
 struct Aux {
   float *rho, *jx, *jy, *jz, *psi;  // phase A
   float *Fx, *Fy, *Fz, *ux, *uy, *uz;  // phase B
+  float *gstar, *divu;  // optional (NULL): the D3Q7 phase also stores g* (7N) and div u
 };
 
 // L2 residency: population loads stream through once per kernel (evict-first),
@@ -479,6 +480,11 @@ __device__ __forceinline__ void phaseC7_cell(const Params& P, int c, const float
   eos_pr(P, rho, T, p, dpdT);
   float gs[7];
   collide7(P, gl, rho, T, ld_aux(X.ux + c, h), ld_aux(X.uy + c, h), ld_aux(X.uz + c, h), du, dpdT, gs);
+  if (X.gstar) {  // kept for the adjoint's recomputed steps
+    X.divu[c] = du;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) X.gstar[i * N + c] = gs[i];
+  }
   // relaxed streaming: g_i(y) += (g*_i(y - c_i) - g_i(y)) / (rho(y) c_v)
   PopStore<ST>::st(gB + c, gl[0] + (gs[0] - gl[0]) * rcp(rho * P.cv), gbase(P, 0));
 #pragma unroll

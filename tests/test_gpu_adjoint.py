@@ -127,8 +127,12 @@ def test_adjoint_matches_oracle_differences(thermo):
         assert abs(dTb_g[k] - fd) <= 2e-3 * scaleb, (k, dTb_g[k], fd)
 
 
-def test_record_leaves_the_same_state_as_stepping(thermo):
+@pytest.mark.parametrize("schedule", [lbm.SCHED_PHASES, lbm.SCHED_SLABS, lbm.SCHED_FUSED])
+def test_record_leaves_the_same_state_as_stepping(schedule, thermo):
+    """lbm_record steps like lbm_step (its last segment runs the phase kernels, so
+    the persistent schedule agrees to rounding only: it contracts other FMAs)."""
     p, rho0, T0, face, Tb, wT = _case("open", thermo)
+    p = dict(p, schedule=schedule)
     a = lbm.Lattice(dict(p), rho0.astype(np.float32), T0.astype(np.float32))
     b = lbm.Lattice(dict(p), rho0.astype(np.float32), T0.astype(np.float32))
     a.lbm_step(13)
@@ -136,7 +140,12 @@ def test_record_leaves_the_same_state_as_stepping(thermo):
     sa, fa, ga = a.state()
     sb, fb, gb = b.state()
     assert sa == sb == lbm.OK
-    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+    if schedule == lbm.SCHED_FUSED:
+        assert np.max(np.abs(fa - fb)) <= 1e-6 * np.max(np.abs(fa))
+        assert np.max(np.abs(ga - gb)) <= 1e-6 * np.max(np.abs(ga))
+        fa, ga = fb, gb
+    else:
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
     # the adjoint leaves the recorded final state current
     seed = np.ones(b.N, dtype=np.float32)
     dev = torch.tensor(seed, device="cuda")
