@@ -192,6 +192,61 @@ def adjoint_cost(lbm, Tc, rv, rl, schedule, stream, n=200, K=100):
             "ratio": adj / fwd, "ratio_with_record": (adj + rec) / fwd}
 
 
+def batched_throughput(lbm, Tc, rv, rl, stream, ndom=48, steps=100, seed=2206):
+    """48 droplet domains with sides drawn from {32, 48, 64, 96} and radius side/4
+    (open faces, rho_b = rho_v, T = T_c): one persistent launch per step over all
+    of them (shape from the autotuner) against stepping the domains one after
+    another with the single-lattice schedule."""
+    import torch
+    sides = [32, 48, 64, 96]
+    draws = W.uniform(seed, ndom, stream=7)
+    lats = []
+    for k in range(ndom):
+        n = sides[min(3, int(draws[k] * 4))]
+        p, rho0, T0 = W.droplet(Tc, rv, rl, n=n, R=n / 4.0, seed=seed + k)
+        p["schedule"] = lbm.SCHED_SLABS
+        lats.append(lbm.Lattice(p, torch.tensor(rho0.reshape(-1), dtype=torch.float32, device="cuda"),
+                                torch.tensor(T0.reshape(-1), dtype=torch.float32, device="cuda"),
+                                stream=stream.cuda_stream))
+    cells = sum(l.N for l in lats)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    # one domain after another
+    for l in lats:
+        l.lbm_step(8)
+    e0, e1 = ev(), ev()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for l in lats:
+        l.lbm_step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    b = lbm.Batch(lats)
+    shape = b.lbm_batch_tune()
+    b.lbm_batch_step(8)
+    e2, e3 = ev(), ev()
+    torch.cuda.synchronize()
+    e2.record(stream)
+    b.lbm_batch_step(steps)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    st = b.lbm_batch_sync()
+    bat_ms = e2.elapsed_time(e3)
+    b.close()
+    for l in lats:
+        l.close()
+    if st != lbm.OK:
+        raise SystemExit(f"batched run failed: {lbm.lbm_status_string(st)}")
+    mlups = cells * steps / (bat_ms * 1e-3) / 1e6
+    return {"workload": f"{ndom} droplet domains, sides drawn from {{32,48,64,96}} (seed {seed}), R = side/4, "
+                        f"open faces, {cells} cells, {steps} steps",
+            "value": mlups, "unit": "MLUPS", "ms_per_step": bat_ms / steps,
+            "shape": {"threads": shape[0], "ctas_per_sm": shape[1], "tile_cells": shape[2],
+                      "mode": "one launch per phase" if shape[1] == 0 else "persistent cooperative launch"},
+            "one_after_another_MLUPS": cells * steps / (seq_ms * 1e-3) / 1e6,
+            "step_effective_GBs": BYTES_PER_LU * mlups * 1e6 / 1e9}
+
+
 def thermo_product():
     """T_c and the coexistence densities from the library's host helpers (not the oracle)."""
     from paper_2206_00946_gb300 import lbm
@@ -260,6 +315,7 @@ def main():
     ap.add_argument("--storage", default="f32", choices=list(STORAGE))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward cost measurement")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-domains measurement")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = dist_env()
@@ -355,6 +411,9 @@ def main():
     adj = None
     if args.storage == "f32" and not args.no_adjoint:
         adj = adjoint_cost(lbm, Tc, rv, rl, p["schedule"], stream)
+    batched = None
+    if args.storage == "f32" and not args.no_batched:
+        batched = batched_throughput(lbm, Tc, rv, rl, stream)
 
     if rank != 0:
         if dist:
@@ -396,6 +455,7 @@ def main():
                                      "share": v[1] / sum(w[1] for w in prof.values())} for k, v in prof.items()}},
         "cpu_baseline": cpu,
         "adjoint": adj,
+        "batched": batched,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * N / args.steps,
                 "d2h_bytes_per_step": 5 * 4 * N / args.steps},
         "gpu_launches": launches * args.steps,

@@ -146,6 +146,33 @@ int lbm_adjoint_step(lbm_ctx* ctx, int n, const float* dL_drho, const float* dL_
                      double* dL_dT0);
 int lbm_adjoint_state(lbm_ctx* ctx, float* f_bar, float* g_bar, int mem);
 
+/* Batched stepping of many independent lattices (no counterpart in the
+ * paper): one persistent cooperative launch per time step runs phases A,
+ * force + D3Q19, D3Q7 and D over a tile list spanning every domain, with a
+ * bounded grid-wide barrier between phases (a barrier that waits ~2 s without
+ * progress aborts the launch: LBM_ERR_TIMEOUT from lbm_batch_sync), or, when
+ * the autotuner finds it faster, one launch per phase over the same tile
+ * list; runs of eight steps are replayed from a CUDA graph.
+ *
+ * lbm_batch_create takes n contexts made by lbm_init with FP32 storage, a
+ * state, and the same stream (else LBM_ERR_ARG / LBM_ERR_STATE).  The contexts
+ * keep their buffers and stay usable (lbm_get_state, lbm_macros, lbm_reduce);
+ * they must outlive the batch.  lbm_batch_step advances every domain n steps
+ * (asynchronous); lbm_batch_sync waits and returns the first error.
+ * lbm_batch_tune times the candidate launch shapes on the domains' own
+ * states, restores the states and their error flags and keeps the fastest:
+ * the persistent launch (threads per CTA 128/256, CTAs per SM 1-4, cells per
+ * tile 1024-8192) or one launch per phase over the same tile list (reported
+ * as ctas_per_sm = 0).  Outputs may be NULL.
+ * lbm_batch_cells returns the total number of cells. */
+typedef struct lbm_batch lbm_batch;
+int lbm_batch_create(lbm_batch** out, lbm_ctx* const* ctxs, int n);
+int lbm_batch_tune(lbm_batch* batch, int* threads, int* ctas_per_sm, int* tile_cells);
+int lbm_batch_step(lbm_batch* batch, int n);
+int lbm_batch_sync(lbm_batch* batch);
+long long lbm_batch_cells(const lbm_batch* batch);
+void lbm_batch_destroy(lbm_batch* batch);
+
 /* Per-node Dirichlet temperature of non-periodic face `face` (Sec. 3.1): an
  * array over the face's two tangential coordinates, lower axis fastest
  * (z faces: nx*ny, x faces: ny*nz, y faces: nx*nz floats) (mem).  Edge and

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "_lib", "liblbm.so")
-SOURCES = ["lbm_api.cu", "lbm_noalloc.cu", "lbm_adjoint.cu"]
+SOURCES = ["lbm_api.cu", "lbm_noalloc.cu", "lbm_adjoint.cu", "lbm_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

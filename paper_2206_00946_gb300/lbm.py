@@ -45,7 +45,8 @@ EXPORTS = ["lbm_init", "lbm_set_state", "lbm_get_state", "lbm_set_face_T", "lbm_
            "lbm_reduce", "lbm_sync", "lbm_stream_map", "lbm_destroy", "lbm_status_string", "lbm_Tc",
            "lbm_maxwell", "lbm_launches_per_step", "lbm_profile", "lbm_profile_read", "lbm_reduce_static",
            "lbm_checkpoint_bytes", "lbm_checkpoint", "lbm_restore", "lbm_record", "lbm_adjoint_step",
-           "lbm_adjoint_state"]
+           "lbm_adjoint_state", "lbm_batch_create", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_sync",
+           "lbm_batch_cells", "lbm_batch_destroy"]
 PROFILE_KINDS = ["phaseA", "phaseB", "phaseC", "phaseD", "fused", "phaseC7"]
 
 _lib = None
@@ -93,6 +94,14 @@ def load(path: str = LIB_PATH):
     L.lbm_record.argtypes = [vp, ct.c_int, ct.c_int]
     L.lbm_adjoint_step.argtypes = [vp, ct.c_int, vp, vp, vp, vp]
     L.lbm_adjoint_state.argtypes = [vp, vp, vp, ct.c_int]
+    L.lbm_batch_create.argtypes = [ct.POINTER(vp), ct.POINTER(vp), ct.c_int]
+    L.lbm_batch_tune.argtypes = [vp, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]
+    L.lbm_batch_step.argtypes = [vp, ct.c_int]
+    L.lbm_batch_sync.argtypes = [vp]
+    L.lbm_batch_cells.argtypes = [vp]
+    L.lbm_batch_cells.restype = ct.c_longlong
+    L.lbm_batch_destroy.argtypes = [vp]
+    L.lbm_batch_destroy.restype = None
     _lib = L
     return L
 
@@ -266,3 +275,40 @@ class Lattice:
         out = {k: np.empty(self.N, dtype=np.float32) for k in ("rho", "ux", "uy", "uz", "T")}
         st = self.lbm_macros(**out)
         return st, out
+
+
+class Batch:
+    """Batched stepping of several Lattice objects (FP32, same stream) in one
+    persistent launch per step.  The lattices must outlive the batch."""
+
+    def __init__(self, lattices):
+        L = load()
+        self.lattices = list(lattices)
+        arr = (ct.c_void_p * len(self.lattices))(*[lat._ctx.value for lat in self.lattices])
+        self._b = ct.c_void_p()
+        _check(L.lbm_batch_create(ct.byref(self._b), arr, len(self.lattices)), "lbm_batch_create")
+
+    def lbm_batch_step(self, n=1):
+        _check(load().lbm_batch_step(self._b, int(n)), "lbm_batch_step")
+
+    def lbm_batch_sync(self):
+        return load().lbm_batch_sync(self._b)
+
+    def lbm_batch_tune(self):
+        t, c, s = ct.c_int(), ct.c_int(), ct.c_int()
+        _check(load().lbm_batch_tune(self._b, ct.byref(t), ct.byref(c), ct.byref(s)), "lbm_batch_tune")
+        return t.value, c.value, s.value
+
+    def lbm_batch_cells(self):
+        return int(load().lbm_batch_cells(self._b))
+
+    def close(self):
+        if self._b:
+            load().lbm_batch_destroy(self._b)
+            self._b = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

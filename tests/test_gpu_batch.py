@@ -1,0 +1,118 @@
+"""Batched persistent stepping of uneven lattices against stepping each alone.
+
+Every domain of a batch runs the same per-cell code as the single-lattice phase
+schedule (inlined into one persistent kernel, where a few FMAs contract
+differently), so after n steps (a graph-replayed run of eight plus single
+launches) each domain's state must match the same lattice stepped on its own
+to rounding (2e-6; measured 5e-7 after 13 steps); the autotuner must leave the
+states unchanged; errors of one domain surface through lbm_batch_sync.
+"""
+import numpy as np
+import pytest
+
+from paper_2206_00946_gb300 import lbm
+from paper_2206_00946_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lbm.load()
+
+
+def _domains(thermo):
+    Tc, rv, rl = thermo["Tc"], thermo["rho_v"], thermo["rho_l"]
+    out = []
+    for n, R in ((12, 3.0), (17, 4.0), (14, 3.0)):
+        p, rho0, T0 = W.droplet(Tc, rv, rl, n=n, R=R, W=2.0, seed=n, amp=1e-3)
+        out.append((p, rho0, T0))
+    p, rho0, T0 = W.sessile(Tc, rv, rl, nx=10, ny=9, nz=11, R=3.0, W=2.0)
+    out.append((p, rho0, T0))
+    p, rho0, T0 = W.sessile(Tc, rv, rl, nx=8, ny=13, nz=7, R=2.5, W=2.0, theta=70.0)
+    out.append((p, rho0, T0))
+    p, rho0, T0 = W.slab(Tc, rv, rl, nx=1, ny=1, nz=24)
+    out.append((p, rho0, T0))
+    return out
+
+
+def _lat(p, rho0, T0, schedule=lbm.SCHED_PHASES):
+    return lbm.Lattice(dict(p, schedule=schedule), rho0.reshape(-1).astype(np.float32),
+                       T0.reshape(-1).astype(np.float32))
+
+
+@pytest.mark.parametrize("steps", [1, 13])
+def test_batch_matches_single_lattices(steps, thermo):
+    doms = _domains(thermo)
+    solo = [_lat(*d) for d in doms]
+    batched = [_lat(*d) for d in doms]
+    for lat in solo:
+        lat.lbm_step(steps)
+    b = lbm.Batch(batched)
+    assert b.lbm_batch_cells() == sum(lat.N for lat in batched)
+    b.lbm_batch_step(steps)
+    assert b.lbm_batch_sync() == lbm.OK
+    for s, t in zip(solo, batched):
+        st1, f1, g1 = s.state()
+        st2, f2, g2 = t.state()
+        assert st1 == st2 == lbm.OK
+        assert np.max(np.abs(f1 - f2)) <= 2e-6 * np.max(np.abs(f1))
+        assert np.max(np.abs(g1 - g2)) <= 2e-6 * np.max(np.abs(g1))
+    b.close()
+    for lat in solo + batched:
+        lat.close()
+
+
+def test_tune_keeps_states_and_picks_a_valid_shape(thermo):
+    doms = _domains(thermo)
+    lats = [_lat(*d) for d in doms]
+    ref = [_lat(*d) for d in doms]
+    b = lbm.Batch(lats)
+    b.lbm_batch_step(3)
+    for lat in ref:
+        lat.lbm_step(3)
+    threads, ctas, tile = b.lbm_batch_tune()
+    assert threads in (128, 256) and 0 <= ctas <= 4 and tile in (1024, 2048, 4096, 8192)
+    for s, t in zip(ref, lats):
+        _, f1, g1 = s.state()
+        _, f2, g2 = t.state()
+        assert np.max(np.abs(f1 - f2)) <= 2e-6 * np.max(np.abs(f1))
+    b.lbm_batch_step(5)  # stepping continues from the restored states
+    for lat in ref:
+        lat.lbm_step(5)
+    assert b.lbm_batch_sync() == lbm.OK
+    for s, t in zip(ref, lats):
+        _, f1, g1 = s.state()
+        _, f2, g2 = t.state()
+        assert np.max(np.abs(f1 - f2)) <= 2e-6 * np.max(np.abs(f1))
+        assert np.max(np.abs(g1 - g2)) <= 2e-6 * np.max(np.abs(g1))
+    b.close()
+    for lat in lats + ref:
+        lat.close()
+
+
+def test_batch_reports_a_domain_error(thermo):
+    doms = _domains(thermo)[:3]
+    lats = [_lat(*d) for d in doms]
+    # a temperature far above T_c puts psi of Eq. 7 out of its domain in one lattice
+    p, rho0, T0 = doms[1]
+    bad = lbm.Lattice(dict(p, schedule=lbm.SCHED_PHASES), rho0.reshape(-1).astype(np.float32),
+                      np.full(rho0.size, 5.0 * thermo["Tc"], dtype=np.float32))
+    b = lbm.Batch(lats + [bad])
+    b.lbm_batch_step(2)
+    assert b.lbm_batch_sync() in (lbm.ERR_PSI_DOMAIN, lbm.ERR_NONFINITE)
+    b.close()
+    for lat in lats + [bad]:
+        lat.close()
+
+
+def test_batch_rejects_16bit_storage(thermo):
+    p, rho0, T0 = _domains(thermo)[0]
+    lat = lbm.Lattice(dict(p, schedule=lbm.SCHED_PHASES, storage=lbm.STORE_F16_SHIFTED),
+                      rho0.reshape(-1).astype(np.float32), T0.reshape(-1).astype(np.float32))
+    with pytest.raises(lbm.LBMError):
+        lbm.Batch([lat])
+    lat.close()
