@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256, LBM_PHASEC_MINBLOCKS) k_phaseBC19(Params 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_phaseC7(Params P, const T* __restrict__ gA, T* gB, Aux X, int c0, int c1) {
+__global__ void __launch_bounds__(256, 4) k_phaseC7(Params P, const T* __restrict__ gA, T* gB, Aux X, int c0, int c1) {
   for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x)
     phaseC7(P, c, gA, gB, X);
 }
@@ -289,6 +289,7 @@ Params make_device_params(const lbm_params& p) {
   P.rho_v = (float)p.rho_v;
   P.inv_drho = (p.rho_l > p.rho_v) ? (float)(1.0 / (p.rho_l - p.rho_v)) : 0.f;
   P.lam_uniform = p.lambda_l == p.lambda_v;
+  P.fast19 = p.s_q == 1.0 && p.s_pi == 1.0 && !p.meq_printed;
   // shifts of the 16-bit storage; defaults: rho_v, and the mean Dirichlet face temperature
   // (else 0.9 T_c for the Peng-Robinson fluid, else 1)
   double tref = p.store_T_ref;

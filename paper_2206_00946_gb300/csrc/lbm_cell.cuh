@@ -91,6 +91,7 @@ struct Params {
   float lambda_l, lambda_v, rho_l, rho_v, inv_drho;
   float rho_ref, T_ref;  // shifts of the 16-bit population storage
   int lam_uniform;
+  int fast19;  // s_q = s_pi = 1 and m^eq = M-hat f^eq: collide19_fast is exact
   int face_kind[6];
   float face_rho[6];
   float tan_wet[6];  // tan(pi/2 - theta) of each wall face (Eq. 36)
@@ -247,6 +248,88 @@ LBM_HD void feq19(R rho, R ux, R uy, R uz, R* fe) {
   for (int i = 0; i < 19; ++i) {
     const R cu = c19x(i) * ux + c19y(i) * uy + c19z(i) * uz;
     fe[i] = w19(i) * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+  }
+}
+
+// The same collision when s_q = s_pi = 1 and m^eq = M-hat f^eq (the default
+// reading): every moment of rate 1, the conserved ones included, leaves the
+// collision as m^eq(rho, u + F/rho), so f* = f^eq(rho, u + F/rho) plus the
+// relaxed non-equilibrium parts (1 - s_k)(m_k - m^eq_k(u)) of the six second-
+// order moments, mapped back through their columns of M-hat^-1: the rest and
+// axis populations for e and the normal stresses, one diagonal pair per
+// shear component.  An exact identity, cheaper than the general transform.
+template <typename R>
+LBM_HD void collide19_fast(const Params& P, const R* f, R rho, R ux, R uy, R uz, R Fx, R Fy, R Fz, R* fs) {
+  const R s7_10 = f[7] + f[8] + f[9] + f[10];
+  const R s11_14 = f[11] + f[12] + f[13] + f[14];
+  const R s15_18 = f[15] + f[16] + f[17] + f[18];
+  const R Sxx = (f[1] + f[2]) + s7_10 + s11_14;
+  const R Syy = (f[3] + f[4]) + s7_10 + s15_18;
+  const R Szz = (f[5] + f[6]) + s11_14 + s15_18;
+  const R uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
+  const R ce = R(1) - R(P.s_e), cv = R(1) - R(P.s_v);
+  // relaxed non-equilibrium moments (1 - s_k)(m_k - rho e_k(u))
+  const R A4 = ce * (Sxx + Syy + Szz - rho * (R(1) + uxx + uyy + uzz));
+  const R A5 = cv * (R(2) * Sxx - Syy - Szz - rho * (R(2) * uxx - uyy - uzz));
+  const R A6 = cv * (Syy - Szz - rho * (uyy - uzz));
+  const R A7 = cv * ((f[7] + f[8]) - (f[9] + f[10]) - rho * ux * uy);
+  const R A8 = cv * ((f[11] + f[12]) - (f[13] + f[14]) - rho * ux * uz);
+  const R A9 = cv * ((f[15] + f[16]) - (f[17] + f[18]) - rho * uy * uz);
+  // f^eq(rho, u') with u' = u + F/rho, pair by pair: w rho (1 + 4.5 cu^2 - 1.5 u'^2) +- 3 w rho cu
+  const R ir = rcp(rho);
+  const R vx = ux + Fx * ir, vy = uy + Fy * ir, vz = uz + Fz * ir;
+  const R base = rho * (R(1) - R(1.5) * (vx * vx + vy * vy + vz * vz));
+  const R r45 = R(4.5) * rho, r3 = R(3) * rho;
+  const R w0 = R(1) / R(3), w1 = R(1) / R(18), w2 = R(1) / R(36);
+  fs[0] = w0 * base - A4;
+  {
+    const R e = w1 * (base + r45 * vx * vx) + (A4 + A5) * (R(1) / R(6)), o = w1 * r3 * vx;
+    fs[1] = e + o;
+    fs[2] = e - o;
+  }
+  {
+    const R e = w1 * (base + r45 * vy * vy) + A4 * (R(1) / R(6)) - A5 * (R(1) / R(12)) + A6 * R(0.25),
+            o = w1 * r3 * vy;
+    fs[3] = e + o;
+    fs[4] = e - o;
+  }
+  {
+    const R e = w1 * (base + r45 * vz * vz) + A4 * (R(1) / R(6)) - A5 * (R(1) / R(12)) - A6 * R(0.25),
+            o = w1 * r3 * vz;
+    fs[5] = e + o;
+    fs[6] = e - o;
+  }
+  // diagonal pairs (c, -c): c = (1,1,0), (1,-1,0), (1,0,1), (1,0,-1), (0,1,1), (0,1,-1)
+  const R p7 = vx + vy, p9 = vx - vy, p11 = vx + vz, p13 = vx - vz, p15 = vy + vz, p17 = vy - vz;
+  {
+    const R e = w2 * (base + r45 * p7 * p7) + A7 * R(0.25), o = w2 * r3 * p7;
+    fs[7] = e + o;
+    fs[8] = e - o;
+  }
+  {
+    const R e = w2 * (base + r45 * p9 * p9) - A7 * R(0.25), o = w2 * r3 * p9;
+    fs[9] = e + o;
+    fs[10] = e - o;
+  }
+  {
+    const R e = w2 * (base + r45 * p11 * p11) + A8 * R(0.25), o = w2 * r3 * p11;
+    fs[11] = e + o;
+    fs[12] = e - o;
+  }
+  {
+    const R e = w2 * (base + r45 * p13 * p13) - A8 * R(0.25), o = w2 * r3 * p13;
+    fs[13] = e + o;
+    fs[14] = e - o;
+  }
+  {
+    const R e = w2 * (base + r45 * p15 * p15) + A9 * R(0.25), o = w2 * r3 * p15;
+    fs[15] = e + o;
+    fs[16] = e - o;
+  }
+  {
+    const R e = w2 * (base + r45 * p17 * p17) - A9 * R(0.25), o = w2 * r3 * p17;
+    fs[17] = e + o;
+    fs[18] = e - o;
   }
 }
 

@@ -384,7 +384,10 @@ __device__ __forceinline__ void phaseC19_cell(const Params& P, int c, const floa
   float ux = jx * ir, uy = jy * ir, uz = jz * ir;
   if (wall && P.wall_ueq_zero) ux = uy = uz = 0.f;
   float fs[19];
-  collide19(P, fl, rho, ux, uy, uz, Fx, Fy, Fz, fs);
+  if (P.fast19)
+    collide19_fast(P, fl, rho, ux, uy, uz, Fx, Fy, Fz, fs);
+  else
+    collide19(P, fl, rho, ux, uy, uz, Fx, Fy, Fz, fs);
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     const int k = nb_kind(nb, c19x(i), c19y(i), c19z(i));
@@ -432,7 +435,10 @@ __device__ __forceinline__ void phaseBC19(const Params& P, int c, const ST* __re
   float ux = jx * ir, uy = jy * ir, uz = jz * ir;
   if (wall && P.wall_ueq_zero) ux = uy = uz = 0.f;
   float fs[19];
-  collide19(P, fl, rho, ux, uy, uz, Fx, Fy, Fz, fs);
+  if (P.fast19)
+    collide19_fast(P, fl, rho, ux, uy, uz, Fx, Fy, Fz, fs);
+  else
+    collide19(P, fl, rho, ux, uy, uz, Fx, Fy, Fz, fs);
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     const int k = nb_kind(nb, c19x(i), c19y(i), c19z(i));
@@ -473,6 +479,18 @@ __device__ __forceinline__ void phaseC7_cell(const Params& P, int c, const float
   make_nb(P, x, y, z, nb);
   const long long N = P.N;
   const Hint h = make_hint();
+  // the destinations' g_i and rho of the relaxed streaming, loaded first so that
+  // their latency overlaps the stencil and the collision (a move beyond a
+  // non-periodic face reads the cell itself and stores nothing)
+  float gold[7], ry[7];
+  int yc[7];
+#pragma unroll
+  for (int i = 1; i < 7; ++i) {
+    const bool ok = nb_kind(nb, c7x(i), c7y(i), c7z(i)) == 0;
+    yc[i] = c + (ok ? nb_off(nb, c7x(i), c7y(i), c7z(i)) : 0);
+    gold[i] = PopStore<ST>::ld(gA + i * N + yc[i], gbase(P, i), h);
+    ry[i] = ok ? ld_aux(X.rho + yc[i], h) : 0.f;
+  }
   const float rho = ld_aux(X.rho + c, h);
   const float T = sum7(gl);
   const float du = divu_at(P, c, nb, X, h);
@@ -490,10 +508,7 @@ __device__ __forceinline__ void phaseC7_cell(const Params& P, int c, const float
 #pragma unroll
   for (int i = 1; i < 7; ++i) {
     if (nb_kind(nb, c7x(i), c7y(i), c7z(i))) continue;
-    const int yc = c + nb_off(nb, c7x(i), c7y(i), c7z(i));
-    const float gold = PopStore<ST>::ld(gA + i * N + yc, gbase(P, i), h);
-    const float ry = ld_aux(X.rho + yc, h);
-    PopStore<ST>::st(gB + i * N + yc, gold + (gs[i] - gold) * rcp(ry * P.cv), gbase(P, i));
+    PopStore<ST>::st(gB + i * N + yc[i], gold[i] + (gs[i] - gold[i]) * rcp(ry[i] * P.cv), gbase(P, i));
   }
 }
 

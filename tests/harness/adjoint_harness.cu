@@ -33,6 +33,19 @@ void a_collide19(const double* d, const int* k, const double* f, int ueq_from_f,
   const double u[3] = {ueq_from_f ? j[0] / rho : 0.0, ueq_from_f ? j[1] / rho : 0.0, ueq_from_f ? j[2] / rho : 0.0};
   collide19(P, f, rho, u[0], u[1], u[2], F[0], F[1], F[2], fs);
 }
+// the closed-form collision of the rate-1 case, same inputs as a_collide19
+void a_collide19_fast(const double* d, const int* k, const double* f, int ueq_from_f, const double* F, double* fs) {
+  Params P = make(d, k);
+  double rho = 0, j[3] = {0, 0, 0};
+  for (int i = 0; i < 19; ++i) {
+    rho += f[i];
+    j[0] += c19x(i) * f[i];
+    j[1] += c19y(i) * f[i];
+    j[2] += c19z(i) * f[i];
+  }
+  const double u[3] = {ueq_from_f ? j[0] / rho : 0.0, ueq_from_f ? j[1] / rho : 0.0, ueq_from_f ? j[2] / rho : 0.0};
+  collide19_fast(P, f, rho, u[0], u[1], u[2], F[0], F[1], F[2], fs);
+}
 void a_collide19_vjp(const double* d, const int* k, const double* f, int ueq_from_f, const double* F,
                      const double* fsb, double* fb, double* Fb) {
   Params P = make(d, k);

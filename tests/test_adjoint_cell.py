@@ -157,3 +157,24 @@ def test_psi_dpdT_vjp(H, eos_kind, rho, thermo):
         return out
 
     _check(fwd, vjp, x, 2, rng)
+
+
+@pytest.mark.parametrize("ueq_from_f", [1, 0])
+def test_closed_form_collision_equals_the_moment_form(H, ueq_from_f):
+    """With s_q = s_pi = 1 and m^eq = M-hat f^eq the step uses the closed form
+    f^eq(rho, u + F/rho) + relaxed second-order non-equilibrium; in double it must
+    equal the moment-space collision to rounding, for any s_e, s_v."""
+    for se, sv in ((1.25, 0.8), (0.6, 1.7)):
+        p = W.base_params(2, 2, 2, s_e=se, s_v=sv, s_q=1.0, s_pi=1.0)
+        d, k = _dk(p)
+        ki = k.ctypes.data_as(ct.POINTER(ct.c_int))
+        rng = np.random.default_rng(int(10 * se) + ueq_from_f)
+        w = np.array(W.W19)
+        for rho in (0.4, 6.3):
+            for _ in range(20):
+                f = np.ascontiguousarray(w * rho * (1 + 0.1 * rng.standard_normal(19)))
+                F = np.ascontiguousarray(0.02 * rng.standard_normal(3))
+                a, b = np.empty(19), np.empty(19)
+                H.a_collide19(P_(d), ki, P_(f), ueq_from_f, P_(F), P_(a))
+                H.a_collide19_fast(P_(d), ki, P_(f), ueq_from_f, P_(F), P_(b))
+                assert np.max(np.abs(a - b)) <= 1e-13 * rho, np.max(np.abs(a - b))
