@@ -32,6 +32,13 @@ LBM_HD int node_faces(const Params& P, int x, int y, int z) {
   return m;
 }
 
+LBM_HD bool on_open(const Params& P, int m) {
+  bool o = false;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) o |= ((m >> f) & 1) && P.face_kind[f] == FACE_OPEN;
+  return o;
+}
+
 LBM_HD bool on_wall(const Params& P, int m) {
   bool w = false;
 #pragma unroll

@@ -552,8 +552,10 @@ __device__ __forceinline__ void phaseD(const Params& P, int c, int x, int y, int
                                        const Aux& X) {
   const long long N = P.N;
   float fl[19], gl[7];
+  // only the open-face rule reads f, and only its known populations
+  const unsigned skip = on_open(P, m) ? unknown19(P, x, y, z) : 0x7ffffu;
 #pragma unroll
-  for (int i = 0; i < 19; ++i) fl[i] = PopStore<ST>::ld_plain(fB + i * N + c, fbase(P, i));
+  for (int i = 0; i < 19; ++i) fl[i] = ((skip >> i) & 1u) ? 0.f : PopStore<ST>::ld_plain(fB + i * N + c, fbase(P, i));
   boundary_rules<ST>(P, c, x, y, z, m, fl, gl, fB, gB, X);
 }
 
