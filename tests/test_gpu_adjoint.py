@@ -36,6 +36,10 @@ def _case(kind, thermo):
         p, rho0, T0 = W.droplet(Tc, rv, rl, n=8, R=2.5, W=2.0, seed=4, amp=1e-3)
         p.update(lambda_l=0.4, lambda_v=0.2)
         face = 4
+    elif kind == "open12":
+        p, rho0, T0 = W.droplet(Tc, rv, rl, n=12, R=3.0, W=2.0, seed=5, amp=1e-3)
+        p.update(lambda_l=0.4, lambda_v=0.2)
+        face = 1
     else:  # heated bottom wall, open top, periodic in x and y
         p, rho0, T0 = W.sessile(Tc, rv, rl, nx=8, ny=7, nz=9, R=3.0, W=2.0)
         face = 4
@@ -79,10 +83,9 @@ def _ref_grads(p, rho0, T0, face, Tb, wT, n):
     return float(L), T0_t.grad.numpy(), Tb_t.grad.numpy()
 
 
-@pytest.mark.parametrize("kind", ["open", "wall_open"])
-def test_adjoint_matches_fp64_autograd(kind, thermo):
+@pytest.mark.parametrize("kind,n,K", [("open", 12, 5), ("wall_open", 12, 5), ("open12", 20, 7)])
+def test_adjoint_matches_fp64_autograd(kind, n, K, thermo):
     p, rho0, T0, face, Tb, wT = _case(kind, thermo)
-    n, K = 12, 5
     Lg, dT0_g, dTb_g = _gpu_grads(p, rho0, T0, face, Tb, wT, n, K)
     Lr, dT0_r, dTb_r = _ref_grads(p, rho0, T0, face, Tb, wT, n)
     assert abs(Lg - Lr) < 1e-5 * abs(Lr)

@@ -404,3 +404,28 @@ def test_one_step_general_collision_matches_oracle(name, rates, thermo):
     assert st == lbm.OK
     assert pop_err(fg, fo, thermo) < 1e-5
     assert pop_err(gg, go, thermo) < 1e-5
+
+
+@pytest.mark.parametrize("storage", [lbm.STORE_F16_SHIFTED, lbm.STORE_BF16_SHIFTED])
+def test_full_size_16bit_one_step_within_half_ulp(storage, thermo):
+    """One step of the 128^3 droplet with 16-bit shifted storage in the benchmark's slab
+    schedule: every population within half an ulp of its stored deviation of the oracle's
+    step from the same (quantised) state; default shifts rho_ref = rho_v, T_ref = face T."""
+    p, f0, g0, _, _ = _full_size_oracle("d2_128", thermo)
+    q = dict(p, storage=storage, schedule=lbm.SCHED_SLABS)
+    lat = lbm.Lattice(q)
+    lat.lbm_set_state(f0, g0)
+    st, fq, gq = lat.state()
+    assert st == lbm.OK
+    lat.lbm_step(1)
+    st, fg, gg = lat.state()
+    lat.close()
+    assert st == lbm.OK
+    st_o, fo, go = Oracle(p).step(fq.astype(np.float64), gq.astype(np.float64))
+    assert st_o == 0
+    rho_ref = float(np.float32(p["rho_v"]))
+    T_ref = float(np.float32(np.mean([t for t, k in zip(p["face_T"], p["face_kind"]) if k != 0])))
+    face = _face_nodes(p)
+    ex_f, rel_f = _storage_bound_ok(fg, fo, W.W19 * rho_ref, HALF_ULP[storage], thermo, face)
+    ex_g, rel_g = _storage_bound_ok(gg, go, W7 * T_ref, HALF_ULP[storage], thermo, face)
+    assert ex_f <= 0 and ex_g <= 0, (rel_f, rel_g)
