@@ -150,7 +150,7 @@ def job_throughput(dist, local_s: float, units_per_rank: int, device="cpu"):
     return local_s, world * units_per_rank / local_s
 
 
-def adjoint_cost(lbm, Tc, rv, rl, schedule, stream, n=200, K=100):
+def adjoint_cost(lbm, Tc, rv, rl, schedule, stream, n=2000, K=100):
     """Adjoint / forward cost on a 64^3 droplet of radius 10 with open faces: the
     time of lbm_adjoint_step over n recorded steps (segment recompute included)
     over the time of n forward steps, both CUDA events on the context stream."""

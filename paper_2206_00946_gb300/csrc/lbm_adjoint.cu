@@ -78,6 +78,10 @@ struct DT6 {
   double* p[6];
 };
 
+// PART 0: the extrapolation of g (touches only the g adjoint and the face
+// gradients); PART 1: the open-face rule (only the f adjoint and d L / d F).  The
+// two parts run on different streams, each ahead of its lattice's transpose.
+template <int PART>
 __global__ void k_adj_faces(Params P, float* fb, float* gb, Aux X, float* Fb, DT6 dTf) {
   const long long N = P.N;
   const float w0 = 1.f - P.wbar, w1 = P.wbar * (1.f / 6.f);
@@ -98,25 +102,28 @@ __global__ void k_adj_faces(Params P, float* fb, float* gb, Aux X, float* Fb, DT
       }
       q[fc >> 1] += (fc & 1) ? -1 : 1;
     }
-    // extrapolation: g_k(x_b) = w_k T_b + g_k(x_f) - w_k sum_j g_j(x_f)
-    float a[7], Tb = 0.f;
+    if (PART == 0) {
+      // extrapolation: g_k(x_b) = w_k T_b + g_k(x_f) - w_k sum_j g_j(x_f)
+      float a[7], Tb = 0.f;
 #pragma unroll
-    for (int i = 0; i < 7; ++i) {
-      a[i] = gb[i * N + c];
-      Tb += (i == 0 ? w0 : w1) * a[i];
-    }
-    const int cf = cell_of(P, q[0], q[1], q[2]);
+      for (int i = 0; i < 7; ++i) {
+        a[i] = gb[i * N + c];
+        Tb += (i == 0 ? w0 : w1) * a[i];
+      }
+      const int cf = cell_of(P, q[0], q[1], q[2]);
 #pragma unroll
-    for (int i = 0; i < 7; ++i) {
-      gb[i * N + c] = 0.f;
-      atomicAdd(gb + i * N + cf, a[i] - Tb);
-    }
+      for (int i = 0; i < 7; ++i) {
+        gb[i * N + c] = 0.f;
+        atomicAdd(gb + i * N + cf, a[i] - Tb);
+      }
 #pragma unroll
-    for (int fc = 0; fc < 6; ++fc) {
-      if (!((m >> fc) & 1)) continue;
-      const int ax = fc >> 1;
-      const int idx = ax == 0 ? y + P.ny * z : (ax == 1 ? x + P.nx * z : x + P.nx * y);
-      dTf.p[fc][idx] += (double)Tb / nnp;  // one (face, node) entry per thread
+      for (int fc = 0; fc < 6; ++fc) {
+        if (!((m >> fc) & 1)) continue;
+        const int ax = fc >> 1;
+        const int idx = ax == 0 ? y + P.ny * z : (ax == 1 ? x + P.nx * z : x + P.nx * y);
+        dTf.p[fc][idx] += (double)Tb / nnp;  // one (face, node) entry per thread
+      }
+      continue;
     }
     if (nopen) {
       float fl[19];
@@ -547,14 +554,18 @@ int adjoint_one(lbm_ctx* c, AdjRec* r, float* s, float* fb1, float* gb1, float* 
   float* Psib = q + 12 * N;
   if (cudaMemsetAsync(A.Fb, 0, 3 * N * sizeof(float), st) != cudaSuccess) return LBM_ERR_CUDA;
   // transposes, last forward operation first
-  if (P.bd_total > 0) {
-    DT6 d;
-    for (int k = 0; k < 6; ++k) d.p[k] = r->face_off[k + 1] > r->face_off[k] ? r->dTf + r->face_off[k] : nullptr;
-    k_adj_faces<<<(int)((P.bd_total + 63) / 64), 64, 0, st>>>(P, fb1, gb1, X, A.Fb, d);
-  }
-  // the two lattices' transposes are independent: D3Q19 on a second stream
+  // the two lattices' transposes are independent: the D3Q19 chain (open-face
+  // rule, collision) on a second stream, the D3Q7 chain (extrapolation,
+  // relaxed streaming, collision) on the context stream
   cudaEventRecord(r->ev_fork, st);
   cudaStreamWaitEvent(r->side2, r->ev_fork, 0);
+  DT6 d;
+  for (int k = 0; k < 6; ++k) d.p[k] = r->face_off[k + 1] > r->face_off[k] ? r->dTf + r->face_off[k] : nullptr;
+  if (P.bd_total > 0) {
+    const int FB = (int)((P.bd_total + 63) / 64);
+    k_adj_faces<1><<<FB, 64, 0, r->side2>>>(P, fb1, gb1, X, A.Fb, d);
+    k_adj_faces<0><<<FB, 64, 0, st>>>(P, fb1, gb1, X, A.Fb, d);
+  }
   k_adj_c19<<<B, kT, 0, r->side2>>>(P, f, fb1, fb0, X, A.Fb);
   cudaEventRecord(r->ev_c19, r->side2);
   k_adj_c7<<<B, kT, 0, st>>>(P, g, gb1, gb0, X, A);
