@@ -192,12 +192,12 @@ __global__ void k_adj_c7(Params P, const float* g, const float* gb1, float* gb0,
 #pragma unroll
     for (int i = 0; i < 7; ++i) gl[i] = g[i * N + c];
     const float rho = X.rho[c], T = sum7(gl);
-    const float beta = 1.f / (rho * P.cv);
+    const float beta = rcp(rho * P.cv), ir = rcp(rho);
     // rest population: source and destination are the cell itself
     float a = gb1[c];
     gsb[0] = a * beta;
     gout[0] = (1.f - beta) * a;
-    float rhob = -a * (X.gstar[c] - gl[0]) * beta / rho;
+    float rhob = -a * (X.gstar[c] - gl[0]) * beta * ir;
 #pragma unroll
     for (int i = 1; i < 7; ++i) {
       const int ax = (i - 1) >> 1, s = (i & 1) ? 1 : 0;  // s: 1 for +c, 0 for -c
@@ -205,7 +205,7 @@ __global__ void k_adj_c7(Params P, const float* g, const float* gb1, float* gb0,
       // as a source: population i goes to y = x + c_i
       if (nb.kind[ax][s] == 0) {
         const int yd = c + nb.off[ax][s];
-        gsb[i] = gb1[i * N + yd] / (X.rho[yd] * P.cv);
+        gsb[i] = gb1[i * N + yd] * rcp(X.rho[yd] * P.cv);
       } else {
         gsb[i] = 0.f;
       }
@@ -213,7 +213,7 @@ __global__ void k_adj_c7(Params P, const float* g, const float* gb1, float* gb0,
       if (nb.kind[ax][1 - s] == 0) {
         const int sc = c + nb.off[ax][1 - s];
         gout[i] = (1.f - beta) * a;
-        rhob -= a * (X.gstar[i * N + sc] - gl[i]) * beta / rho;
+        rhob -= a * (X.gstar[i * N + sc] - gl[i]) * beta * ir;
       } else {
         gout[i] = a;
       }
@@ -334,7 +334,7 @@ __global__ void k_adj_u(Params P, Aux X, AdjAux A, float* Jb) {
     const int m = P.any_nonperiodic ? node_faces(P, q[0], q[1], q[2]) : 0;
     float j3[3] = {0.f, 0.f, 0.f};
     if (!(m && on_wall(P, m))) {
-      const float ir = 1.f / X.rho[c];
+      const float ir = rcp(X.rho[c]);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         j3[a] = ub[a] * ir;

@@ -126,7 +126,7 @@ LBM_HD void collide19_vjp(const Params& P, const R* f, bool ueq_from_f, const R*
     jy += R(c19y(i)) * f[i];
     jz += R(c19z(i)) * f[i];
   }
-  const R ir = R(1) / rho;
+  const R ir = rcp(rho);
   const R ux = ueq_from_f ? jx * ir : R(0), uy = ueq_from_f ? jy * ir : R(0), uz = ueq_from_f ? jz * ir : R(0);
   const R vx = ux + F[0] * ir, vy = uy + F[1] * ir, vz = uz + F[2] * ir;  // u' = u + F/rho
   R nb[19];
@@ -176,7 +176,7 @@ LBM_HD void collide7_vjp(const Params& P, const R* g, R rho, R T, const R* u, R 
                          R& rhob, R& Tb, R* ub, R& divub, R& dpdTb) {
   const R m1 = g[1] - g[2], m2 = g[3] - g[4], m3 = g[5] - g[6];
   const R lam = lambda_of(P, rho);
-  const R vs = R(1) / (lam * R(P.inv_cs2t) + R(0.5));
+  const R vs = rcp(lam * R(P.inv_cs2t) + R(0.5));
   const R k = -vs * R(P.inv_cs2t);
   const R um = u[0] * m1 + u[1] * m2 + u[2] * m3;
   const R ugT = k * um;
@@ -252,7 +252,7 @@ LBM_HD void zouhe_vjp(int face, R rho_b, R* fb, R* Fb) {
     }
   }
   // u_n = (sum_Z f + 2 sum_P f + F_n/2) / rho_b - 1; S_a = sum_Z c_a f
-  const R ir = R(1) / rho_b;
+  const R ir = rcp(rho_b);
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     const int c[3] = {c19x(i), c19y(i), c19z(i)};
@@ -275,18 +275,20 @@ LBM_HD void eos_derivs(const Params& P, R rho, R T, R& pr, R& pT, R& prT, R& pTT
   }
   const R Tc = R(1) / R(P.inv_Tc), kap = R(P.kappa), a = R(P.a), b = R(P.b), Rg = R(P.R);
   const R sq = sqrt(T * Tc);
-  const R s = R(1) + kap * (R(1) - sqrt(T / Tc));
+  const R s = R(1) + kap * (R(1) - sqrt(T * R(P.inv_Tc)));
   const R xi = s * s;
-  const R dxi = -kap * s / sq;
-  const R d2xi = kap * kap / (R(2) * T * Tc) + kap * s / (R(2) * T * sq);
+  const R isq = rcp(sq), ihT = rcp(R(2) * T);
+  const R dxi = -kap * s * isq;
+  const R d2xi = ihT * (kap * kap * R(P.inv_Tc) + kap * s * isq);
   const R om = R(1) - b * rho;
   const R den = R(1) + R(2) * b * rho - b * b * rho * rho;
   const R dden = R(2) * b - R(2) * b * b * rho;
-  const R q = (R(2) * rho * den - rho * rho * dden) / (den * den);  // d/drho (rho^2 / den)
-  pr = Rg * T / (om * om) - a * xi * q;
-  pT = rho * Rg / om - a * dxi * rho * rho / den;
-  prT = Rg / (om * om) - a * dxi * q;
-  pTT = -a * d2xi * rho * rho / den;
+  const R iom = rcp(om), iden = rcp(den);
+  const R q = (R(2) * rho * den - rho * rho * dden) * iden * iden;  // d/drho (rho^2 / den)
+  pr = Rg * T * iom * iom - a * xi * q;
+  pT = rho * Rg * iom - a * dxi * rho * rho * iden;
+  prT = Rg * iom * iom - a * dxi * q;
+  pTT = -a * d2xi * rho * rho * iden;
 }
 
 // Adjoint of psi(rho, T) = sqrt(2 (p - rho/3) / G) and of dp/dT(rho, T):
@@ -296,7 +298,7 @@ LBM_HD void psi_dpdT_vjp(const Params& P, R rho, R T, R psi, R psib, R dpdTb, R&
   R pr, pT, prT, pTT;
   eos_derivs(P, rho, T, pr, pT, prT, pTT);
   if (psi > R(0)) {
-    const R c = psib / (R(1) / R(P.inv_G) * psi);  // psi_b / (G psi)
+    const R c = psib * R(P.inv_G) * rcp(psi);  // psi_b / (G psi)
     rhob += c * (pr - R(1) / R(3));
     Tb += c * pT;
   }
