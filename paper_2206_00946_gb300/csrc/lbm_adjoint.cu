@@ -348,9 +348,10 @@ __global__ void k_adj_u(Params P, Aux X, AdjAux A, float* Jb) {
   }
 }
 
-// d L / d psi(y) from F(x) = -G psi(x) sum_i varpi_i psi(x + c_i) c_i: the
-// cell's own factor and the transposed stencil.
-__global__ void k_adj_psi(Params P, Aux X, AdjAux A, float* Psib) {
+// d L / d psi(y) from F(x) = -G psi(x) sum_i varpi_i psi(x + c_i) c_i (the
+// cell's own factor and the transposed stencil), then through the EOS to the
+// cell's d L / d rho (completing Rb) and d L / d T (Tbar).
+__global__ void k_adj_psi(Params P, const float* g, Aux X, AdjAux A, float* Tbar) {
   const long long N = P.N;
   const Hint h = make_hint();
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)N; c += gridDim.x * blockDim.x) {
@@ -374,22 +375,24 @@ __global__ void k_adj_psi(Params P, Aux X, AdjAux A, float* Psib) {
       if (has_extra(em, cx, cy, cz)) t += extra_sources(P, q, cx, cy, cz, ec, term);
       psib += varpi19(i) * t;
     }
-    Psib[c] = -P.G * (psib + A.Fb[c] * S[0] + A.Fb[N + c] * S[1] + A.Fb[2 * N + c] * S[2]);
-  }
-}
-
-// The EOS chain rule of psi and dp/dT to rho and T, and the macroscopic fields
-// rho = sum f, j = sum c f, T = sum g folded into the adjoint of the
-// populations at time t.
-__global__ void k_adj_fold(Params P, const float* g, Aux X, AdjAux A, const float* Jb, const float* Psib, float* fb0,
-                           float* gb0) {
-  const long long N = P.N;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)N; c += gridDim.x * blockDim.x) {
+    psib = -P.G * (psib + A.Fb[c] * S[0] + A.Fb[N + c] * S[1] + A.Fb[2 * N + c] * S[2]);
+    // the EOS chain rule of psi and dp/dT: the cell's complete d L / d rho and d L / d T
     float T = 0.f;
 #pragma unroll
     for (int i = 0; i < 7; ++i) T += g[i * N + c];
     float rhob = A.Rb[c], Tb = 0.f;
-    psi_dpdT_vjp(P, X.rho[c], T, X.psi[c], Psib[c], A.Dpb[c], rhob, Tb);
+    psi_dpdT_vjp(P, X.rho[c], T, X.psi[c], psib, A.Dpb[c], rhob, Tb);
+    A.Rb[c] = rhob;
+    Tbar[c] = Tb;
+  }
+}
+
+// The macroscopic fields rho = sum f, j = sum c f, T = sum g folded into the
+// adjoint of the populations at time t (a streaming update).
+__global__ void k_adj_fold(Params P, AdjAux A, const float* Jb, const float* Tbar, float* fb0, float* gb0) {
+  const long long N = P.N;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)N; c += gridDim.x * blockDim.x) {
+    const float rhob = A.Rb[c], Tb = Tbar[c];
     const float jx = Jb[c], jy = Jb[N + c], jz = Jb[2 * N + c];
 #pragma unroll
     for (int i = 0; i < 19; ++i) fb0[i * N + c] += rhob + c19x(i) * jx + c19y(i) * jy + c19z(i) * jz;
@@ -551,7 +554,7 @@ int adjoint_one(lbm_ctx* c, AdjRec* r, float* s, float* fb1, float* gb1, float* 
   A.Divb = q + 7 * N;
   A.Dpb = q + 8 * N;
   float* Jb = q + 9 * N;
-  float* Psib = q + 12 * N;
+  float* Psib = q + 12 * N;  // d L / d T of the EOS chain
   if (cudaMemsetAsync(A.Fb, 0, 3 * N * sizeof(float), st) != cudaSuccess) return LBM_ERR_CUDA;
   // transposes, last forward operation first
   // the two lattices' transposes are independent: the D3Q19 chain (open-face
@@ -571,8 +574,8 @@ int adjoint_one(lbm_ctx* c, AdjRec* r, float* s, float* fb1, float* gb1, float* 
   k_adj_c7<<<B, kT, 0, st>>>(P, g, gb1, gb0, X, A);
   cudaStreamWaitEvent(st, r->ev_c19, 0);
   k_adj_u<<<B, kT, 0, st>>>(P, X, A, Jb);
-  k_adj_psi<<<B, kT, 0, st>>>(P, X, A, Psib);
-  k_adj_fold<<<B, kT, 0, st>>>(P, g, X, A, Jb, Psib, fb0, gb0);
+  k_adj_psi<<<B, kT, 0, st>>>(P, g, X, A, Psib);
+  k_adj_fold<<<B, kT, 0, st>>>(P, A, Jb, Psib, fb0, gb0);
   return cst(cudaGetLastError());
 }
 
