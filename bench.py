@@ -9,6 +9,14 @@ job, and the fraction of the measured HBM copy bandwidth that the 208 bytes of
 algorithmic traffic per lattice update reach.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--storage f32|f16|bf16] [--schedule slabs|phases|fused]
+
+The JSON line also carries the roofline of the dominant kernel (each kernel timed
+alone with CUDA events in the phase schedule, charged its own algorithmic bytes),
+the end-to-end rate through host buffers, the FP64 CPU oracle on a bounded sample
+(cpu_baseline), the adjoint/forward cost on a 64^3 droplet over 2000 steps with
+checkpoints every 100 (adjoint), and 48 uneven droplet domains stepped as one
+batch (batched); --no-adjoint / --no-batched / --no-cpu-baseline skip those.
 
 N > 1 (torchrun, one rank per GPU) runs N independent replicas of the domain
 (weak scaling, no collective on the data path).  --impl reference times the

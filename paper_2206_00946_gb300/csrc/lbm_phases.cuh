@@ -1,5 +1,6 @@
-// The four phases of one time step, written per cell so that the one-launch-
-// per-phase schedule and the fused pipelined kernel run the same code.
+// The phases of one time step, written per cell so that every schedule (one
+// launch per phase, per-slab launches, the persistent pipelined kernel, the
+// batched kernels, the adjoint's recomputation) runs the same code.
 //   A  macro: rho, j = sum c f, T = sum g, p_EOS, psi          (Eqs. 3, 7, 37)
 //   B  force: F = -G psi sum varpi psi(x+c) c, u = (j + F/2)/rho (Eqs. 5, 6, 36)
 //   C  collide + stream: D3Q19 MRT-EDM collision pushed to x+c (bounce-back at
@@ -7,6 +8,8 @@
 //      (Eqs. 8, 13-15, 27-29, 34)
 //   D  boundary: constant-pressure open faces (Sec. 3.3) and non-equilibrium
 //      extrapolation of g at Dirichlet nodes (Sec. 3.1), on the new state
+// The time-stepping schedules run B inside the D3Q19 part of C (phaseBC19); B
+// alone serves lbm_macros and the persistent kernel.
 #pragma once
 
 #include <cuda_bf16.h>
