@@ -168,7 +168,10 @@ __global__ void __launch_bounds__(256, 2) k_adj_c19(Params P, const float* f, co
     }
     const int m = P.any_nonperiodic ? node_faces(P, x, y, z) : 0;
     const bool wall = m && on_wall(P, m);
-    collide19_vjp(P, fl, !(wall && P.wall_ueq_zero), F3, fsb, fbo, Fo);
+    if (P.fast19)  // the closed form of the rate-1 case, as in the forward step
+      collide19_fast_vjp(P, fl, !(wall && P.wall_ueq_zero), F3, fsb, fbo, Fo);
+    else
+      collide19_vjp(P, fl, !(wall && P.wall_ueq_zero), F3, fsb, fbo, Fo);
 #pragma unroll
     for (int i = 0; i < 19; ++i) fb0[i * N + c] = fbo[i];
     Fb[c] += Fo[0];

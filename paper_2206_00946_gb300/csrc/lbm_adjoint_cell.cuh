@@ -168,6 +168,85 @@ LBM_HD void collide19_vjp(const Params& P, const R* f, bool ueq_from_f, const R*
   mhat_T_add(mb, fb);
 }
 
+// The same product for the closed form of the rate-1 case (collide19_fast):
+// f* = f^eq(rho, u') + sum_k A_k col_k, u' = u + F/rho, A_k = (1 - s_k)(m_k - rho e_k(u))
+// for the six second-order moments k = 4..9 and their M-hat^-1 columns col_k.
+template <typename R>
+LBM_HD void collide19_fast_vjp(const Params& P, const R* f, bool ueq_from_f, const R* F, const R* b, R* fb,
+                               R* Fb) {
+  R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    rho += f[i];
+    jx += R(c19x(i)) * f[i];
+    jy += R(c19y(i)) * f[i];
+    jz += R(c19z(i)) * f[i];
+  }
+  const R ir = rcp(rho);
+  const R ux = ueq_from_f ? jx * ir : R(0), uy = ueq_from_f ? jy * ir : R(0), uz = ueq_from_f ? jz * ir : R(0);
+  const R vx = ux + F[0] * ir, vy = uy + F[1] * ir, vz = uz + F[2] * ir;
+  const R vv = vx * vx + vy * vy + vz * vz;
+  // f^eq(rho, u'): d/d rho = f^eq / rho; d/d u' = w rho (3 c + 9 (c.u') c - 3 u')
+  R rhob = R(0), swb = R(0), s1x = R(0), s1y = R(0), s1z = R(0), s2x = R(0), s2y = R(0), s2z = R(0);
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    const R cx = R(c19x(i)), cy = R(c19y(i)), cz = R(c19z(i));
+    const R cu = cx * vx + cy * vy + cz * vz;
+    const R wi = i == 0 ? R(1) / R(3) : (i < 7 ? R(1) / R(18) : R(1) / R(36));  // as in collide19_fast
+    const R wb = wi * b[i];
+    rhob += wb * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * vv);
+    swb += wb;
+    s1x += wb * cx;
+    s1y += wb * cy;
+    s1z += wb * cz;
+    s2x += wb * cu * cx;
+    s2y += wb * cu * cy;
+    s2z += wb * cu * cz;
+  }
+  const R vbx = rho * (R(3) * s1x + R(9) * s2x - R(3) * vx * swb);
+  const R vby = rho * (R(3) * s1y + R(9) * s2y - R(3) * vy * swb);
+  const R vbz = rho * (R(3) * s1z + R(9) * s2z - R(3) * vz * swb);
+  // u' = u + F/rho
+  Fb[0] = vbx * ir;
+  Fb[1] = vby * ir;
+  Fb[2] = vbz * ir;
+  rhob -= (vbx * F[0] + vby * F[1] + vbz * F[2]) * ir * ir;
+  R ubx = vbx, uby = vby, ubz = vbz;
+  // the columns of the relaxed moments (transposed): dL/dA_k
+  const R s6 = R(1) / R(6), s12 = R(1) / R(12), q = R(0.25);
+  const R A4b = -b[0] + s6 * (b[1] + b[2] + b[3] + b[4] + b[5] + b[6]);
+  const R A5b = s6 * (b[1] + b[2]) - s12 * (b[3] + b[4] + b[5] + b[6]);
+  const R A6b = q * (b[3] + b[4] - b[5] - b[6]);
+  const R A7b = q * (b[7] + b[8] - b[9] - b[10]);
+  const R A8b = q * (b[11] + b[12] - b[13] - b[14]);
+  const R A9b = q * (b[15] + b[16] - b[17] - b[18]);
+  const R ce = R(1) - R(P.s_e), cv = R(1) - R(P.s_v);
+  const R m4 = ce * A4b, m5 = cv * A5b, m6 = cv * A6b, m7 = cv * A7b, m8 = cv * A8b, m9 = cv * A9b;
+  // A_k = c_k (m_k - rho e_k(u)): e4 = 1 + |u|^2, e5 = 2ux^2 - uy^2 - uz^2, e6 = uy^2 - uz^2,
+  // e7 = ux uy, e8 = ux uz, e9 = uy uz
+  const R uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
+  rhob -= m4 * (R(1) + uxx + uyy + uzz) + m5 * (R(2) * uxx - uyy - uzz) + m6 * (uyy - uzz) + m7 * ux * uy +
+          m8 * ux * uz + m9 * uy * uz;
+  ubx -= rho * (R(2) * ux * m4 + R(4) * ux * m5 + uy * m7 + uz * m8);
+  uby -= rho * (R(2) * uy * m4 - R(2) * uy * m5 + R(2) * uy * m6 + ux * m7 + uz * m9);
+  ubz -= rho * (R(2) * uz * m4 - R(2) * uz * m5 - R(2) * uz * m6 + ux * m8 + uy * m9);
+  R jbx = R(0), jby = R(0), jbz = R(0);
+  if (ueq_from_f) {  // u = j / rho
+    jbx = ubx * ir;
+    jby = uby * ir;
+    jbz = ubz * ir;
+    rhob -= (ubx * ux + uby * uy + ubz * uz) * ir;
+  }
+  // m_k = rows 4..9 of M-hat applied to f
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    const R x = R(c19x(i)), y = R(c19y(i)), z = R(c19z(i));
+    const R xx = x * x, yy = y * y, zz = z * z;
+    fb[i] = rhob + x * jbx + y * jby + z * jbz + m4 * (xx + yy + zz) + m5 * (R(2) * xx - yy - zz) +
+            m6 * (yy - zz) + m7 * x * y + m8 * x * z + m9 * y * z;
+  }
+}
+
 // ------------------------------------------ D3Q7 collision + source (Eq. 13) --
 // Adjoint of g* = collide7(g, rho, T, u, div u, dp/dT) with gsb = d L / d g*.
 // T is an input of its own here (the caller adds Tb to every d L / d g_i).

@@ -51,6 +51,11 @@ void a_collide19_vjp(const double* d, const int* k, const double* f, int ueq_fro
   Params P = make(d, k);
   collide19_vjp(P, f, ueq_from_f != 0, F, fsb, fb, Fb);
 }
+void a_collide19_fast_vjp(const double* d, const int* k, const double* f, int ueq_from_f, const double* F,
+                          const double* fsb, double* fb, double* Fb) {
+  Params P = make(d, k);
+  collide19_fast_vjp(P, f, ueq_from_f != 0, F, fsb, fb, Fb);
+}
 // forward: x = (g[7], rho, u[3], divu, dpdT) -> g* (7), T = sum g
 void a_collide7(const double* d, const int* k, const double* x, double* gs) {
   Params P = make(d, k);

@@ -178,3 +178,41 @@ def test_closed_form_collision_equals_the_moment_form(H, ueq_from_f):
                 H.a_collide19(P_(d), ki, P_(f), ueq_from_f, P_(F), P_(a))
                 H.a_collide19_fast(P_(d), ki, P_(f), ueq_from_f, P_(F), P_(b))
                 assert np.max(np.abs(a - b)) <= 1e-13 * rho, np.max(np.abs(a - b))
+
+
+@pytest.mark.parametrize("ueq_from_f", [1, 0])
+def test_closed_form_collision_vjp(H, ueq_from_f):
+    """The product of the closed form equals the general product (rate-1 case) and
+    central differences of the forward."""
+    for se, sv in ((1.25, 0.8), (0.6, 1.7)):
+        p = W.base_params(2, 2, 2, s_e=se, s_v=sv, s_q=1.0, s_pi=1.0)
+        d, k = _dk(p)
+        ki = k.ctypes.data_as(ct.POINTER(ct.c_int))
+        rng = np.random.default_rng(int(10 * sv) + 3 * ueq_from_f)
+        w = np.array(W.W19)
+        for rho in (0.4, 6.3):
+            f = np.ascontiguousarray(w * rho * (1 + 0.1 * rng.standard_normal(19)))
+            F = np.ascontiguousarray(0.02 * rng.standard_normal(3))
+            x = np.concatenate([f, F])
+            for _ in range(4):
+                b = np.ascontiguousarray(rng.standard_normal(19))
+                fb1, Fb1, fb2, Fb2 = np.empty(19), np.empty(3), np.empty(19), np.empty(3)
+                H.a_collide19_vjp(P_(d), ki, P_(f), ueq_from_f, P_(F), P_(b), P_(fb1), P_(Fb1))
+                H.a_collide19_fast_vjp(P_(d), ki, P_(f), ueq_from_f, P_(F), P_(b), P_(fb2), P_(Fb2))
+                assert np.max(np.abs(fb1 - fb2)) <= 1e-12 * max(1.0, np.max(np.abs(fb1)))
+                assert np.max(np.abs(Fb1 - Fb2)) <= 1e-12 * max(1.0, np.max(np.abs(Fb1)))
+
+            def fwd(x):
+                fs = np.empty(19)
+                H.a_collide19_fast(P_(d), ki, P_(np.ascontiguousarray(x[:19])), ueq_from_f,
+                                   P_(np.ascontiguousarray(x[19:])), P_(fs))
+                return fs
+
+            def vjp(x, b):
+                fb, Fb = np.empty(19), np.empty(3)
+                H.a_collide19_fast_vjp(P_(d), ki, P_(np.ascontiguousarray(x[:19])), ueq_from_f,
+                                       P_(np.ascontiguousarray(x[19:])), P_(np.ascontiguousarray(b)), P_(fb),
+                                       P_(Fb))
+                return np.concatenate([fb, Fb])
+
+            _check(fwd, vjp, x, 19, rng)
