@@ -10,8 +10,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "lbm.h"
@@ -26,6 +28,29 @@ int blocks_for(long long n) {
   long long b = (n + kT - 1) / kT;
   if (b > 152LL * 32) b = 152LL * 32;
   return (int)(b < 1 ? 1 : b);
+}
+
+// Programmatic dependent launch: a kernel launched after another on the same
+// stream with launch_pdl may start while that kernel finishes.  It reads the
+// earlier kernel's results only after griddep_wait, which returns once that grid
+// has completed and its writes are visible (at once for an ordinary launch).
+// griddep_launch lets the next such kernel be scheduled.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... K, typename... A>
+cudaError_t launch_pdl(bool pdl, void (*kern)(K...), int grid, int block, cudaStream_t s, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
 }
 
 // adjoint scratch fields, N floats each unless noted
@@ -85,6 +110,7 @@ template <int PART>
 __global__ void k_adj_faces(Params P, float* fb, float* gb, Aux X, float* Fb, DT6 dTf) {
   const long long N = P.N;
   const float w0 = 1.f - P.wbar, w1 = P.wbar * (1.f / 6.f);
+  griddep_launch();
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < (int)P.bd_total; k += gridDim.x * blockDim.x) {
     int x, y, z;
     boundary_candidate(P, k, x, y, z);
@@ -132,9 +158,9 @@ __global__ void k_adj_faces(Params P, float* fb, float* gb, Aux X, float* Fb, DT
       if (nnp == 1) {
         float F3[3] = {0.f, 0.f, 0.f};
         zouhe_vjp(oface, P.face_rho[oface], fl, F3);
-        Fb[c] += F3[0];
-        Fb[N + c] += F3[1];
-        Fb[2 * N + c] += F3[2];
+        Fb[c] = F3[0];  // the first term of d L / d F at this node (k_adj_c19 adds its own)
+        Fb[N + c] = F3[1];
+        Fb[2 * N + c] = F3[2];
       } else {
         const unsigned unk = unknown19(P, x, y, z);
 #pragma unroll
@@ -160,8 +186,10 @@ __global__ void __launch_bounds__(256, 2) k_adj_c19(Params P, const float* f, co
     make_nb(P, x, y, z, nb);
     float fl[19], fsb[19], fbo[19], F3[3] = {X.Fx[c], X.Fy[c], X.Fz[c]}, Fo[3];
 #pragma unroll
+    for (int i = 0; i < 19; ++i) fl[i] = f[i * N + c];
+    griddep_wait();  // the open-face transpose before this kernel wrote fb1 and Fb
+#pragma unroll
     for (int i = 0; i < 19; ++i) {
-      fl[i] = f[i * N + c];
       const int k = nb_kind(nb, c19x(i), c19y(i), c19z(i));
       fsb[i] = k == 0 ? fb1[i * N + c + nb_off(nb, c19x(i), c19y(i), c19z(i))]
                       : ((k & FACE_WALL) ? fb1[opp19(i) * N + c] : 0.f);
@@ -174,9 +202,16 @@ __global__ void __launch_bounds__(256, 2) k_adj_c19(Params P, const float* f, co
       collide19_vjp(P, fl, !(wall && P.wall_ueq_zero), F3, fsb, fbo, Fo);
 #pragma unroll
     for (int i = 0; i < 19; ++i) fb0[i * N + c] = fbo[i];
-    Fb[c] += Fo[0];
-    Fb[N + c] += Fo[1];
-    Fb[2 * N + c] += Fo[2];
+    // d L / d F starts here, except at nodes of a single open face, where the
+    // open-face rule's transpose (same stream, launched before) stored its term
+    if (m && __popc(m) == 1 && on_open(P, m)) {
+      Fo[0] += Fb[c];
+      Fo[1] += Fb[N + c];
+      Fo[2] += Fb[2 * N + c];
+    }
+    Fb[c] = Fo[0];
+    Fb[N + c] = Fo[1];
+    Fb[2 * N + c] = Fo[2];
   }
 }
 
@@ -196,6 +231,7 @@ __global__ void k_adj_c7(Params P, const float* g, const float* gb1, float* gb0,
     for (int i = 0; i < 7; ++i) gl[i] = g[i * N + c];
     const float rho = X.rho[c], T = sum7(gl);
     const float beta = rcp(rho * P.cv), ir = rcp(rho);
+    griddep_wait();  // the extrapolation transpose before this kernel wrote gb1
     // rest population: source and destination are the cell itself
     float a = gb1[c];
     gsb[0] = a * beta;
@@ -316,6 +352,7 @@ __device__ __forceinline__ bool has_extra(unsigned m, int cx, int cy, int cz) {
 // then u = (j + F/2) / rho (zero at walls): d L / d j, d L / d F, d L / d rho.
 __global__ void k_adj_u(Params P, Aux X, AdjAux A, float* Jb) {
   const long long N = P.N;
+  griddep_launch();
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)N; c += gridDim.x * blockDim.x) {
     int q[3];
     cell_xyz(P, c, q[0], q[1], q[2]);
@@ -353,7 +390,7 @@ __global__ void k_adj_u(Params P, Aux X, AdjAux A, float* Jb) {
 
 // d L / d psi(y) from F(x) = -G psi(x) sum_i varpi_i psi(x + c_i) c_i (the
 // cell's own factor and the transposed stencil), then through the EOS to the
-// cell's d L / d rho (completing Rb) and d L / d T (Tbar).
+// cell's complete d L / d rho (Rb) and d L / d T (Tbar).
 __global__ void k_adj_psi(Params P, const float* g, Aux X, AdjAux A, float* Tbar) {
   const long long N = P.N;
   const Hint h = make_hint();
@@ -365,7 +402,6 @@ __global__ void k_adj_psi(Params P, const float* g, Aux X, AdjAux A, float* Tbar
     int ec[3][2];
     const unsigned em = P.any_nonperiodic ? extra_table(P, q, 0, ec) : 0u;
     float S[3] = {0.f, 0.f, 0.f};
-    float psib = 0.f;
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
       const int cx = c19x(i), cy = c19y(i), cz = c19z(i);
@@ -373,6 +409,16 @@ __global__ void k_adj_psi(Params P, const float* g, Aux X, AdjAux A, float* Tbar
       S[0] += cx * v;
       S[1] += cy * v;
       S[2] += cz * v;
+    }
+    float T = 0.f;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) T += g[i * N + c];
+    griddep_wait();  // d L / d F, rho and dp/dT of the kernels before
+    griddep_launch();
+    float psib = 0.f;
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+      const int cx = c19x(i), cy = c19y(i), cz = c19z(i);
       auto term = [&](int x) { return X.psi[x] * (cx * A.Fb[x] + cy * A.Fb[N + x] + cz * A.Fb[2 * N + x]); };
       float t = nb_kind(nb, -cx, -cy, -cz) == 0 ? term(c + nb_off(nb, -cx, -cy, -cz)) : 0.f;
       if (has_extra(em, cx, cy, cz)) t += extra_sources(P, q, cx, cy, cz, ec, term);
@@ -380,9 +426,6 @@ __global__ void k_adj_psi(Params P, const float* g, Aux X, AdjAux A, float* Tbar
     }
     psib = -P.G * (psib + A.Fb[c] * S[0] + A.Fb[N + c] * S[1] + A.Fb[2 * N + c] * S[2]);
     // the EOS chain rule of psi and dp/dT: the cell's complete d L / d rho and d L / d T
-    float T = 0.f;
-#pragma unroll
-    for (int i = 0; i < 7; ++i) T += g[i * N + c];
     float rhob = A.Rb[c], Tb = 0.f;
     psi_dpdT_vjp(P, X.rho[c], T, X.psi[c], psib, A.Dpb[c], rhob, Tb);
     A.Rb[c] = rhob;
@@ -391,16 +434,24 @@ __global__ void k_adj_psi(Params P, const float* g, Aux X, AdjAux A, float* Tbar
 }
 
 // The macroscopic fields rho = sum f, j = sum c f, T = sum g folded into the
-// adjoint of the populations at time t (a streaming update).
+// adjoint of the populations at time t (a streaming update).  The lattice
+// transposes wrote fb0 and gb0 before d L / d u was taken, so they are loaded
+// while the psi transpose finishes.
 __global__ void k_adj_fold(Params P, AdjAux A, const float* Jb, const float* Tbar, float* fb0, float* gb0) {
   const long long N = P.N;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)N; c += gridDim.x * blockDim.x) {
+    float fv[19], gv[7];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) fv[i] = fb0[i * N + c];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) gv[i] = gb0[i * N + c];
+    griddep_wait();  // Rb and Tbar of the psi transpose
     const float rhob = A.Rb[c], Tb = Tbar[c];
     const float jx = Jb[c], jy = Jb[N + c], jz = Jb[2 * N + c];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) fb0[i * N + c] += rhob + c19x(i) * jx + c19y(i) * jy + c19z(i) * jz;
+    for (int i = 0; i < 19; ++i) fb0[i * N + c] = fv[i] + rhob + c19x(i) * jx + c19y(i) * jy + c19z(i) * jz;
 #pragma unroll
-    for (int i = 0; i < 7; ++i) gb0[i * N + c] += Tb;
+    for (int i = 0; i < 7; ++i) gb0[i * N + c] = gv[i] + Tb;
   }
 }
 
@@ -434,7 +485,67 @@ struct AdjRec {
   float* scr = nullptr;      // AdjAux fields + d L / d j
   double* dTf = nullptr;     // per-face accumulators, faces concatenated
   long long face_off[7] = {0, 0, 0, 0, 0, 0, 0};
+  bool pdl = true;  // programmatic dependent launches within an adjoint step
+  // K-step segments replayed from CUDA graphs, captured on first use from the
+  // parameters below: the adjoint of a segment per (segment buffer, which of the
+  // two adjoint buffers holds the newest adjoint), its recomputation per buffer
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gx[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  cudaGraphExec_t gr[2] = {nullptr, nullptr};
+  Params gP{};
+  Aux gX{};
+  bool gpdl = true;
 };
+
+void adj_drop_graphs(AdjRec* r) {
+  for (int b = 0; b < 2; ++b) {
+    for (int k = 0; k < 2; ++k)
+      if (r->gx[b][k]) {
+        cudaGraphExecDestroy(r->gx[b][k]);
+        r->gx[b][k] = nullptr;
+      }
+    if (r->gr[b]) {
+      cudaGraphExecDestroy(r->gr[b]);
+      r->gr[b] = nullptr;
+    }
+  }
+}
+
+// The graphs hold the parameters and scratch pointers they were captured with.
+void adj_graph_key(lbm_ctx* c, AdjRec* r) {
+  if (std::memcmp(&r->gP, &c->P, sizeof(Params)) || std::memcmp(&r->gX, &c->X, sizeof(Aux)) || r->gpdl != r->pdl) {
+    adj_drop_graphs(r);
+    std::memcpy(&r->gP, &c->P, sizeof(Params));
+    std::memcpy(&r->gX, &c->X, sizeof(Aux));
+    r->gpdl = r->pdl;
+  }
+}
+
+// Captures the launches that `issue` makes on the private capture stream (the
+// context stream may be the legacy default stream, which cannot be captured)
+// into *gx.  Returns false, with nothing launched, when that fails.
+template <typename F>
+bool adj_capture(AdjRec* r, cudaGraphExec_t* gx, F issue) {
+  if (!r->cap && cudaStreamCreateWithFlags(&r->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cudaStreamBeginCapture(r->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int e = issue(r->cap);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(r->cap, &g);
+  bool ok = !e && ce == cudaSuccess && g;
+  if (ok) ok = cudaGraphInstantiate(gx, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    *gx = nullptr;
+    cudaGetLastError();
+  }
+  return ok;
+}
 
 void adj_free(lbm_ctx* c) {
   if (!c || !c->adj) return;
@@ -462,6 +573,8 @@ void adj_free(lbm_ctx* c) {
   }
   cudaFree(r->scr);
   cudaFree(r->dTf);
+  adj_drop_graphs(r);
+  if (r->cap) cudaStreamDestroy(r->cap);
   delete r;
   c->adj = nullptr;
 }
@@ -509,10 +622,9 @@ int flags(lbm_ctx* c) {
 // scratch (rho, psi, F, u) the step computed from it.  The phase kernels write
 // straight into the slots (the context's buffers are pointed at them).
 // The launches go to `stream` (the context's stream is swapped for it meanwhile).
-int recompute(lbm_ctx* c, float* seg, const float* ck, int len, cudaStream_t stream) {
+int recompute_steps(lbm_ctx* c, float* seg, int len, cudaStream_t stream) {
   const long long N = c->N;
-  int st = cst(cudaMemcpyAsync(seg, ck, 26ull * N * sizeof(float), cudaMemcpyDeviceToDevice, stream));
-  if (st) return st;
+  int st = LBM_OK;
   void* f0[2] = {c->f[0], c->f[1]};
   void* g0[2] = {c->g[0], c->g[1]};
   const Aux X0 = c->X;
@@ -539,6 +651,19 @@ int recompute(lbm_ctx* c, float* seg, const float* ck, int len, cudaStream_t str
   return st;
 }
 
+// With gx (full segments of the adjoint), the steps after the copy of the
+// checkpoint are replayed from a graph, captured on first use.
+int recompute(lbm_ctx* c, float* seg, const float* ck, int len, cudaStream_t stream, AdjRec* r = nullptr,
+              cudaGraphExec_t* gx = nullptr) {
+  int st = cst(cudaMemcpyAsync(seg, ck, 26ull * c->N * sizeof(float), cudaMemcpyDeviceToDevice, stream));
+  if (st) return st;
+  if (gx && !c->profiling &&
+      (*gx || adj_capture(r, gx, [&](cudaStream_t cs) { return recompute_steps(c, seg, len, cs); })) &&
+      cudaGraphLaunch(*gx, stream) == cudaSuccess)
+    return LBM_OK;
+  return recompute_steps(c, seg, len, stream);
+}
+
 // One adjoint step through the step from slot s:
 // (fb1, gb1) = d L / d state(t+1) -> (fb0, gb0) = d L / d state(t).
 int adjoint_one(lbm_ctx* c, AdjRec* r, float* s, float* fb1, float* gb1, float* fb0, float* gb0) {
@@ -557,8 +682,7 @@ int adjoint_one(lbm_ctx* c, AdjRec* r, float* s, float* fb1, float* gb1, float* 
   A.Divb = q + 7 * N;
   A.Dpb = q + 8 * N;
   float* Jb = q + 9 * N;
-  float* Psib = q + 12 * N;  // d L / d T of the EOS chain
-  if (cudaMemsetAsync(A.Fb, 0, 3 * N * sizeof(float), st) != cudaSuccess) return LBM_ERR_CUDA;
+  float* Tbar = q + 12 * N;  // d L / d T of the EOS chain
   // transposes, last forward operation first
   // the two lattices' transposes are independent: the D3Q19 chain (open-face
   // rule, collision) on a second stream, the D3Q7 chain (extrapolation,
@@ -572,14 +696,42 @@ int adjoint_one(lbm_ctx* c, AdjRec* r, float* s, float* fb1, float* gb1, float* 
     k_adj_faces<1><<<FB, 64, 0, r->side2>>>(P, fb1, gb1, X, A.Fb, d);
     k_adj_faces<0><<<FB, 64, 0, st>>>(P, fb1, gb1, X, A.Fb, d);
   }
-  k_adj_c19<<<B, kT, 0, r->side2>>>(P, f, fb1, fb0, X, A.Fb);
+  // each lattice transpose overlaps the end of its face transpose
+  const bool pf = r->pdl && P.bd_total > 0;
+  cudaError_t e = launch_pdl(pf, k_adj_c19, B, kT, r->side2, P, f, (const float*)fb1, fb0, X, A.Fb);
   cudaEventRecord(r->ev_c19, r->side2);
-  k_adj_c7<<<B, kT, 0, st>>>(P, g, gb1, gb0, X, A);
+  if (e == cudaSuccess) e = launch_pdl(pf, k_adj_c7, B, kT, st, P, g, (const float*)gb1, gb0, X, A);
   cudaStreamWaitEvent(st, r->ev_c19, 0);
   k_adj_u<<<B, kT, 0, st>>>(P, X, A, Jb);
-  k_adj_psi<<<B, kT, 0, st>>>(P, g, X, A, Psib);
-  k_adj_fold<<<B, kT, 0, st>>>(P, A, Jb, Psib, fb0, gb0);
+  if (e == cudaSuccess) e = launch_pdl(r->pdl, k_adj_psi, B, kT, st, P, g, X, A, Tbar);
+  if (e == cudaSuccess) e = launch_pdl(r->pdl, k_adj_fold, B, kT, st, P, A, (const float*)Jb, (const float*)Tbar, fb0, gb0);
+  if (e != cudaSuccess) return LBM_ERR_CUDA;
   return cst(cudaGetLastError());
+}
+
+// Steps t = len-1 .. 0 of the segment in buffer seg, the newest adjoint in
+// buffers cur, launched one by one on the context stream.
+int adjoint_segment_eager(lbm_ctx* c, AdjRec* r, float* seg, int len, int cur) {
+  int s = LBM_OK;
+  for (int t = len - 1; t >= 0 && !s; --t) {
+    s = adjoint_one(c, r, seg + (size_t)kSlot * c->N * t, r->fb[cur], r->gb[cur], r->fb[1 - cur], r->gb[1 - cur]);
+    cur = 1 - cur;
+  }
+  return s;
+}
+
+// A full K-step segment from segment buffer b as one graph launch.  Returns
+// false when the graph cannot be made; nothing has been launched then.
+bool adjoint_segment_graph(lbm_ctx* c, AdjRec* r, int b, int cur) {
+  if (!r->gx[b][cur] && !adj_capture(r, &r->gx[b][cur], [&](cudaStream_t cs) {
+        cudaStream_t s0 = c->stream;
+        c->stream = cs;
+        const int e = adjoint_segment_eager(c, r, r->seg[b], r->K, cur);
+        c->stream = s0;
+        return e;
+      }))
+    return false;
+  return cudaGraphLaunch(r->gx[b][cur], c->stream) == cudaSuccess;
 }
 
 }  // namespace
@@ -672,12 +824,18 @@ extern "C" int lbm_adjoint_step(lbm_ctx* c, int n, const float* dL_drho, const f
   // Segment k is reversed from buffer set[k]; while it is, segment k-1 is
   // recomputed into the other buffer on the side stream (when there is one).
   const bool two = r->seg[1] != nullptr;
+  // for comparison: LBM_ADJ_EAGER launches every step on its own, LBM_ADJ_NOPDL
+  // launches the kernels of a step without programmatic dependencies
+  const bool graphs = std::getenv("LBM_ADJ_EAGER") == nullptr;
+  r->pdl = std::getenv("LBM_ADJ_NOPDL") == nullptr;
+  if (graphs) adj_graph_key(c, r);
   auto set_of = [&](int k) { return two ? (nseg - 1 - k) & 1 : 0; };
   auto launch_recompute = [&](int k) {
     const int b = set_of(k);
     if (two) cudaStreamWaitEvent(r->side, r->ev_adj[b], 0);  // its previous user is done
     else cudaStreamWaitEvent(r->side, r->ev_adj[0], 0);
-    int e = recompute(c, r->seg[b], r->ckpt[k], std::min(K, n - k * K), r->side);
+    const int len = std::min(K, n - k * K);
+    int e = recompute(c, r->seg[b], r->ckpt[k], len, r->side, r, graphs && len == K ? &r->gr[b] : nullptr);
     if (!e) e = cst(cudaEventRecord(r->ev_rec[b], r->side));
     return e;
   };
@@ -688,11 +846,9 @@ extern "C" int lbm_adjoint_step(lbm_ctx* c, int n, const float* dL_drho, const f
     const int t0 = k * K, len = std::min(K, n - t0), b = set_of(k);
     if (!(k == nseg - 1 && last_was_kept)) s = cst(cudaStreamWaitEvent(st, r->ev_rec[b], 0));
     if (!s && k > 0 && two) s = launch_recompute(k - 1);  // overlapped with this segment
-    for (int t = len - 1; t >= 0 && !s; --t) {
-      s = adjoint_one(c, r, r->seg[b] + (size_t)kSlot * N * t, r->fb[cur], r->gb[cur], r->fb[1 - cur],
-                      r->gb[1 - cur]);
-      cur = 1 - cur;
-    }
+    if (!(len == K && graphs && adjoint_segment_graph(c, r, b, cur)))
+      s = adjoint_segment_eager(c, r, r->seg[b], len, cur);
+    if (len & 1) cur = 1 - cur;
     if (!s) s = cst(cudaEventRecord(r->ev_adj[b], st));
     if (!s && k > 0 && !two) s = launch_recompute(k - 1);  // serial: after this segment
   }

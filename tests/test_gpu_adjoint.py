@@ -169,3 +169,23 @@ def test_record_rejects_16bit_storage(thermo):
         lat.lbm_record(4, 2)
     assert e.value.status == lbm.ERR_ARG
     lat.close()
+
+
+def test_segment_graphs_match_step_launches(thermo, monkeypatch):
+    """Full K-step segments (adjoint and recomputation) replayed from CUDA graphs
+    (odd K: both parities of the adjoint buffers, both segment buffers) against
+    launching every step on its own, and with programmatic dependent launches
+    against without.  The NEE transpose adds with atomics, so all agree to
+    rounding."""
+    p, rho0, T0, face, Tb, wT = _case("open12", thermo)
+    graph = _gpu_grads(p, rho0, T0, face, Tb, wT, 20, 7)
+    monkeypatch.setenv("LBM_ADJ_EAGER", "1")
+    eager = _gpu_grads(p, rho0, T0, face, Tb, wT, 20, 7)
+    monkeypatch.setenv("LBM_ADJ_NOPDL", "1")
+    plain = _gpu_grads(p, rho0, T0, face, Tb, wT, 20, 7)
+    monkeypatch.delenv("LBM_ADJ_EAGER")
+    graph_plain = _gpu_grads(p, rho0, T0, face, Tb, wT, 20, 7)
+    for other in (eager, plain, graph_plain):
+        assert graph[0] == other[0]
+        for a, b in zip(graph[1:], other[1:]):
+            assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(b))
