@@ -42,10 +42,14 @@ LBM_HD constexpr int c7z(int i) { return i == 5 ? 1 : (i == 6 ? -1 : 0); }
 enum { FACE_PERIODIC = 0, FACE_WALL = 1, FACE_OPEN = 2 };
 enum { ERRF_NONFINITE = 1, ERRF_PSI = 2, ERRF_TIMEOUT = 4 };
 
-// Reciprocal, correctly rounded (one MUFU + Newton step on the device).
+// Reciprocal: the hardware approximation on the device, IEEE division on the host.
 LBM_HD float rcp(float x) {
 #if defined(__CUDA_ARCH__)
-  return __frcp_rn(x);
+  // the hardware reciprocal (PTX rcp.approx, about 1 ulp; every operand here is
+  // a density, a temperature or a sum of rates, never subnormal)
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 #else
   return 1.f / x;
 #endif
