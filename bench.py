@@ -15,8 +15,10 @@ The JSON line also carries the roofline of the dominant kernel (each kernel time
 alone with CUDA events in the phase schedule, charged its own algorithmic bytes),
 the end-to-end rate through host buffers, the FP64 CPU oracle on a bounded sample
 (cpu_baseline), the adjoint/forward cost on a 64^3 droplet over 2000 steps with
-checkpoints every 100 (adjoint), and 48 uneven droplet domains stepped as one
-batch (batched); --no-adjoint / --no-batched / --no-cpu-baseline skip those.
+checkpoints every 100 (adjoint), 48 uneven droplet domains stepped as one batch
+(batched), and the 512^3 heated-plate pool with 64 droplets in FP16-shifted
+storage (large); --no-adjoint / --no-batched / --no-large / --no-cpu-baseline
+skip those.
 
 N > 1 (torchrun, one rank per GPU) runs N independent replicas of the domain
 (weak scaling, no collective on the data path).  --impl reference times the
@@ -255,6 +257,42 @@ def batched_throughput(lbm, Tc, rv, rl, stream, ndom=48, steps=100, seed=2206):
             "step_effective_GBs": BYTES_PER_LU * mlups * 1e6 / 1e9}
 
 
+def large_pool(lbm, Tc, rv, rl, stream, steps=100, warmup=10):
+    """512^3 heated-plate pool with 64 droplets (R in [10, 25), seeded), periodic in
+    x and y, bottom wall at 0.96 T_c, open top, FP16-shifted storage, slab
+    schedule: throughput over `steps` steps after `warmup`, and the step's
+    effective bandwidth for its 104 algorithmic bytes per lattice update (26
+    16-bit populations read and written) against the measured HBM peak."""
+    import torch
+    p, rho0, T0 = W.pool(Tc, rv, rl)
+    p["schedule"] = lbm.SCHED_SLABS
+    rho_d = torch.from_numpy(rho0.reshape(-1)).to("cuda")
+    T_d = torch.from_numpy(T0.reshape(-1)).to("cuda")
+    del rho0, T0
+    lat = lbm.Lattice(p, rho_d, T_d, stream=stream.cuda_stream)
+    lat.lbm_step(warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat.lbm_step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = lat.lbm_sync()
+    N = lat.N
+    lat.close()
+    if st != lbm.OK:
+        raise SystemExit(f"pool run failed: {lbm.lbm_status_string(st)}")
+    ms = e0.elapsed_time(e1) / steps
+    mlups = N / (ms * 1e-3) / 1e6
+    step_bytes = 26 * 2 * STORAGE["f16"][1]
+    peak = peaks().get("hbm_gbs", 6800.0)
+    return {"workload": "heated-plate pool 512^3, 64 droplets R in [10,25) (seed 2206), periodic x/y, "
+                        "bottom wall 0.96 T_c, open top, FP16-shifted storage, slab schedule",
+            "cells": N, "steps": steps, "warmup": warmup, "value": mlups, "unit": "MLUPS", "ms_per_step": ms,
+            "step_bytes_per_lu": step_bytes, "step_effective_GBs": step_bytes * mlups * 1e6 / 1e9,
+            "step_frac": step_bytes * mlups * 1e6 / 1e9 / peak}
+
+
 def thermo_product():
     """T_c and the coexistence densities from the library's host helpers (not the oracle)."""
     from paper_2206_00946_gb300 import lbm
@@ -324,6 +362,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward cost measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-domains measurement")
+    ap.add_argument("--no-large", action="store_true", help="skip the 512^3 FP16 pool measurement")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = dist_env()
@@ -422,6 +461,9 @@ def main():
     batched = None
     if args.storage == "f32" and not args.no_batched:
         batched = batched_throughput(lbm, Tc, rv, rl, stream)
+    large = None
+    if args.storage == "f32" and not args.no_large:
+        large = large_pool(lbm, Tc, rv, rl, stream)
 
     if rank != 0:
         if dist:
@@ -464,6 +506,7 @@ def main():
         "cpu_baseline": cpu,
         "adjoint": adj,
         "batched": batched,
+        "large": large,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * N / args.steps,
                 "d2h_bytes_per_step": 5 * 4 * N / args.steps},
         "gpu_launches": launches * args.steps,

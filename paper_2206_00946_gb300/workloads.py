@@ -148,6 +148,60 @@ def sessile(Tc, rho_v, rho_l, nx=256, ny=256, nz=128, R=30.0, W=5.0, dTw=0.1, Ts
     return p, rho0, T0
 
 
+def pool_droplets(n=512, ndrop=64, Rmin=10.0, Rmax=25.0, W=5.0, seed=2206, shape=None, max_tries=100000):
+    """Centres and radii of ndrop droplets by seeded rejection sampling: R uniform in
+    [Rmin, Rmax), each surface at least W from every face, centre distances above
+    R1 + R2 + W.  Candidate k draws (R, cx, cy, cz) from uniform(seed, ., stream=11)
+    at indices 4k .. 4k+3.  Returns an array of rows (cx, cy, cz, R)."""
+    nx, ny, nz = (n, n, n) if shape is None else shape
+    u = uniform(seed, 4 * max_tries, stream=11).reshape(max_tries, 4)
+    out = []
+    for k in range(max_tries):
+        R = Rmin + (Rmax - Rmin) * u[k, 0]
+        m = R + W
+        c = [m + (L - 1 - 2 * m) * u[k, 1 + a] for a, L in enumerate((nx, ny, nz))]
+        if any(L - 1 - 2 * m <= 0 for L in (nx, ny, nz)):
+            continue
+        if all(np.sqrt(sum((c[a] - d[a]) ** 2 for a in range(3))) > R + d[3] + W for d in out):
+            out.append((c[0], c[1], c[2], R))
+            if len(out) == ndrop:
+                return np.array(out)
+    raise ValueError(f"only {len(out)} of {ndrop} droplets fit")
+
+
+def pool(Tc, rho_v, rho_l, n=512, ndrop=64, Rmin=10.0, Rmax=25.0, W=5.0, Tw_frac=0.96, Ts_frac=0.86,
+         lam=1.0 / 3.0, seed=2206, shape=None):
+    """Heated-plate pool: ndrop droplets (pool_droplets) in vapour at coexistence density.
+
+    Periodic in x, y; bounce-back wall at z = 0 held at Tw_frac Tc; constant-pressure
+    top face (rho_b = rho_v) at T_s.  Each droplet has the tanh profile of width W
+    out to 3W beyond its surface (the larger value is taken where two such shells
+    meet; the gaps of at least W keep the liquid apart).  T0 = T_s, the
+    wall layer at T_w.  Fields are FP32, z-major (nz, ny, nx).  Beyond 3W of every
+    surface the density is rho_v exactly.
+    """
+    nx, ny, nz = (n, n, n) if shape is None else shape
+    Ts, Tw = Ts_frac * Tc, Tw_frac * Tc
+    rho0 = np.full((nz, ny, nx), rho_v, dtype=np.float32)
+    for cx, cy, cz, R in pool_droplets(n, ndrop, Rmin, Rmax, W, seed, shape):
+        h = R + 3 * W
+        lo = [max(0, int(np.floor(c - h))) for c in (cx, cy, cz)]
+        hi = [min(L, int(np.ceil(c + h)) + 1) for c, L in zip((cx, cy, cz), (nx, ny, nz))]
+        z, y, x = np.meshgrid(np.arange(lo[2], hi[2]), np.arange(lo[1], hi[1]), np.arange(lo[0], hi[0]),
+                              indexing="ij")
+        r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2)
+        box = rho0[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]
+        prof = np.where(r - R <= 3 * W, tanh_profile(r - R, rho_v, rho_l, W), rho_v).astype(np.float32)
+        np.maximum(box, prof, out=box)
+    T0 = np.full((nz, ny, nx), Ts, dtype=np.float32)
+    T0[0] = Tw
+    p = base_params(nx, ny, nz, rho_l=rho_l, rho_v=rho_v, lambda_l=lam, lambda_v=lam,
+                    face_kind=[PERIODIC, PERIODIC, PERIODIC, PERIODIC, WALL, OPEN],
+                    face_T=[0, 0, 0, 0, Tw, Ts], face_rho=[0, 0, 0, 0, 0, rho_v],
+                    storage=1)
+    return p, rho0, T0
+
+
 def random_populations(nx, ny, nz, rho_base, T_base, w19, w7, amp, seed):
     """Populations w_i * base * (1 + uniform(-amp, amp)), seeded; rho_base/T_base scalars or fields."""
     N = nx * ny * nz

@@ -431,6 +431,46 @@ def test_full_size_16bit_one_step_within_half_ulp(storage, thermo):
     assert ex_f <= 0 and ex_g <= 0, (rel_f, rel_g)
 
 
+def test_full_size_pool_512(thermo):
+    """The 512^3 heated-plate pool with 64 droplets at its full size: f holds
+    19 x 512^3 = 2.55e9 values, so every population index is 64-bit.  Five steps
+    in the configuration's FP16-shifted storage and in FP32 with the pipelined slab
+    schedule (32 slabs), and in FP32 with one launch per phase: status OK and finite
+    FP64 reductions; the two FP32 schedules give the same bits; FP16 stays within
+    its storage error of FP32.  Per step a stored deviation d = f_i - w_i rho_ref
+    is rounded by at most 2^-11 |d|.  In the liquid sum_i |d_i| is rho_l - rho_v
+    plus the non-equilibrium part (taken as 20 % more), so rho moves by at most
+    1.2 x 2^-11 of rho_l per step.  For g, sum_i |d_i| is |T - T_ref| (5 % of T)
+    plus the non-equilibrium part that the wall's 0.1 T_c step sets at first
+    (taken as 15 % of T), so T moves by at most 0.2 x 2^-11 of T per step."""
+    torch = pytest.importorskip("torch")
+    p, rho0, T0 = W.pool(thermo["Tc"], thermo["rho_v"], thermo["rho_l"])
+    rho_d = torch.from_numpy(rho0.reshape(-1)).to("cuda")
+    T_d = torch.from_numpy(T0.reshape(-1)).to("cuda")
+    del rho0, T0
+    out = {}
+    for key, storage, sched in (("f16", lbm.STORE_F16_SHIFTED, lbm.SCHED_SLABS),
+                                ("f32", lbm.STORE_F32, lbm.SCHED_SLABS),
+                                ("phases", lbm.STORE_F32, lbm.SCHED_PHASES)):
+        lat = lbm.Lattice(dict(p, storage=storage, schedule=sched), rho_d, T_d)
+        lat.lbm_step(5)
+        rho, T = torch.empty_like(rho_d), torch.empty_like(T_d)
+        assert lat.lbm_macros(rho=rho, T=T) == lbm.OK
+        assert lat.lbm_sync() == lbm.OK
+        st, red = lat.lbm_reduce()
+        assert st == lbm.OK and np.all(np.isfinite(red[:3])) and red[3] == 0
+        lat.close()
+        out[key] = (rho, T)
+    assert torch.equal(out["phases"][0], out["f32"][0]) and torch.equal(out["phases"][1], out["f32"][1])
+
+    def rel(a, b):
+        return float((a - b).abs().max() / b.abs().max())
+
+    e_rho, e_T = rel(out["f16"][0], out["f32"][0]), rel(out["f16"][1], out["f32"][1])
+    print(f"pool 512^3, 5 steps, FP16 vs FP32: rho {e_rho:.2e}, T {e_T:.2e}")
+    assert e_rho < 5 * 1.2 * 2.0 ** -11 and e_T < 5 * 0.2 * 2.0 ** -11, (e_rho, e_T)
+
+
 @pytest.mark.parametrize("name", ["periodic", "open_all", "walls_z"])
 def test_bulk_staged_phase_c_matches_oracle(name, thermo, monkeypatch):
     """The opt-in phase C that stages each tile's populations in shared memory with
