@@ -160,12 +160,13 @@ def job_throughput(dist, local_s: float, units_per_rank: int, device="cpu"):
     return local_s, world * units_per_rank / local_s
 
 
-def adjoint_cost(lbm, Tc, rv, rl, schedule, stream, n=2000, K=100):
-    """Adjoint / forward cost on a 64^3 droplet of radius 10 with open faces: the
-    time of lbm_adjoint_step over n recorded steps (segment recompute included)
-    over the time of n forward steps, both CUDA events on the context stream."""
+def adjoint_cost(lbm, Tc, rv, rl, schedule, stream, n=2000, K=100, side=64):
+    """Adjoint / forward cost on a side^3 droplet of radius 10 side/64 with open
+    faces (64^3, R = 10 by default): the time of lbm_adjoint_step over n recorded
+    steps (segment recompute included) over the time of n forward steps, both CUDA
+    events on the context stream."""
     import torch
-    p, rho0, T0 = W.droplet(Tc, rv, rl, n=64, R=10.0)
+    p, rho0, T0 = W.droplet(Tc, rv, rl, n=side, R=10.0 * side / 64)
     p["schedule"] = schedule
     rho_d = torch.tensor(rho0.reshape(-1), dtype=torch.float32, device="cuda")
     T_d = torch.tensor(T0.reshape(-1), dtype=torch.float32, device="cuda")
@@ -188,7 +189,7 @@ def adjoint_cost(lbm, Tc, rv, rl, schedule, stream, n=2000, K=100):
     th = torch.tanh((rho - mid) / w)
     seed = (0.5 * (1 + th) + rho * 0.5 * (1 - th * th) / w).contiguous()  # d(liquid mass)/d rho
     dT0 = torch.empty(lat.N, dtype=torch.float64, device="cuda")
-    dTf = torch.empty(6 * 64 * 64, dtype=torch.float64, device="cuda")
+    dTf = torch.empty(6 * side * side, dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
     e[4].record(stream)
     lat.lbm_adjoint_step(n, seed, None, dTf, dT0)
@@ -196,7 +197,8 @@ def adjoint_cost(lbm, Tc, rv, rl, schedule, stream, n=2000, K=100):
     torch.cuda.synchronize()
     lat.close()
     fwd, rec, adj = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3]), e[4].elapsed_time(e[5])
-    return {"workload": f"d2-law droplet 64^3, R=10, open faces, loss = smooth liquid mass after {n} steps, "
+    return {"workload": f"d2-law droplet {side}^3, R={10.0 * side / 64:g}, open faces, loss = smooth liquid mass "
+                        f"after {n} steps, "
                         f"checkpoint every {K} steps; gradients w.r.t. T0 and the six face-temperature fields",
             "forward_ms_per_step": fwd / n, "record_ms_per_step": rec / n, "adjoint_ms_per_step": adj / n,
             "ratio": adj / fwd, "ratio_with_record": (adj + rec) / fwd}
@@ -363,6 +365,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward cost measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-domains measurement")
     ap.add_argument("--no-large", action="store_true", help="skip the 512^3 FP16 pool measurement")
+    ap.add_argument("--adjoint-side", type=int, default=64, help="cube side of the adjoint workload (64)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = dist_env()
@@ -457,7 +460,7 @@ def main():
 
     adj = None
     if args.storage == "f32" and not args.no_adjoint:
-        adj = adjoint_cost(lbm, Tc, rv, rl, p["schedule"], stream)
+        adj = adjoint_cost(lbm, Tc, rv, rl, p["schedule"], stream, side=args.adjoint_side)
     batched = None
     if args.storage == "f32" and not args.no_batched:
         batched = batched_throughput(lbm, Tc, rv, rl, stream)
