@@ -33,6 +33,16 @@
  *    LBM_MEM_DEVICE and host pointers when mem == LBM_MEM_HOST; the caller owns
  *    them.  The library owns the population and scratch buffers it allocates
  *    in lbm_init and frees in lbm_destroy.
+ *
+ * Environment (tuning and comparison only; results do not depend on them
+ * beyond rounding):
+ *   LBM_SLAB_PLANES, LBM_SLAB_STREAMS, LBM_GRAPH_STEPS  planes per slab, streams
+ *       and steps per CUDA graph of the pipelined slab schedule (read by lbm_init);
+ *   LBM_BULK  stage phase C's tiles in shared memory with cp.async.bulk (FP32,
+ *       N a multiple of 4; read by lbm_init);
+ *   LBM_ADJ_EAGER, LBM_ADJ_NOPDL  launch every adjoint step on its own instead of
+ *       replaying K-step segments from graphs / without programmatic dependent
+ *       launches (read by each lbm_adjoint_step).
  */
 #ifndef LBM_H
 #define LBM_H
@@ -124,7 +134,9 @@ int lbm_restore(lbm_ctx* ctx, const void* src, int mem);
  *
  * lbm_record advances n steps from the current state like lbm_step and keeps
  * a checkpoint of the populations every K steps (device memory: n/K + 1
- * states plus K states of recompute buffer, 104 bytes per cell each).
+ * checkpoints of 104 bytes per cell, and one or, when it fits, two segment
+ * buffers of min(K, n) + 1 slots of 168 bytes per cell: a step's state and the
+ * forward scratch computed from it).
  * Requirements: FP32 storage, vartheta = 0, wall faces at 90 degrees
  * (LBM_ERR_ARG otherwise); a state must be set (LBM_ERR_STATE).
  *
