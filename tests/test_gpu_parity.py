@@ -204,9 +204,8 @@ def test_slab_1000_steps_rho_T_match_oracle(schedule, thermo):
 _DROP = {}
 
 
-@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_PHASES, lbm.SCHED_SLABS])
-def test_open_droplet_1000_steps_rho_T_match_oracle(schedule, thermo):
-    """Evaporating droplet with constant-pressure faces on all six sides (20^3, R = 5)."""
+def _drop_oracle(thermo):
+    """The 20^3 evaporating droplet (R = 5, open faces): FP32 initial state and the oracle after 1000 steps."""
     if not _DROP:
         p, rho0, T0 = W.droplet(thermo["Tc"], thermo["rho_v"], thermo["rho_l"], n=20, R=5.0, W=3.0, seed=2206)
         o = Oracle(p)
@@ -215,7 +214,13 @@ def test_open_droplet_1000_steps_rho_T_match_oracle(schedule, thermo):
         st, fo, go = o.run(f0.astype(np.float64), g0.astype(np.float64), 1000)
         assert st == 0
         _DROP.update(p=p, f0=f0, g0=g0, fo=fo, go=go)
-    p, f0, g0, fo, go = (_DROP[k] for k in ("p", "f0", "g0", "fo", "go"))
+    return tuple(_DROP[k] for k in ("p", "f0", "g0", "fo", "go"))
+
+
+@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_PHASES, lbm.SCHED_SLABS])
+def test_open_droplet_1000_steps_rho_T_match_oracle(schedule, thermo):
+    """Evaporating droplet with constant-pressure faces on all six sides (20^3, R = 5)."""
+    p, f0, g0, fo, go = _drop_oracle(thermo)
     _, fg, gg = gpu_step(p, f0, g0, 1000, schedule)
     assert relerr(fg.sum(0), fo.sum(0)) < 1e-3
     assert relerr(gg.sum(0), go.sum(0)) < 1e-3
@@ -383,11 +388,43 @@ def test_16bit_storage_slab_1000_steps_error_vs_oracle(storage, thermo):
         _STORE_1000[storage] = (fo, go)
     fo, go = _STORE_1000[storage]
     e_rho, e_T = relerr(fg.sum(0), fo.sum(0)), relerr(gg.sum(0), go.sum(0))
-    print(f"storage {storage}: 1000-step slab error rho {e_rho:.2e}, T {e_T:.2e}")
+
+    def rel_l2(a, b):
+        return float(np.linalg.norm(a.astype(np.float64) - b) / np.linalg.norm(b))
+
+    l2_rho, l2_T = rel_l2(fg.sum(0), fo.sum(0)), rel_l2(gg.sum(0), go.sum(0))
+    print(f"storage {storage}: 1000-step slab error rho {e_rho:.2e}, T {e_T:.2e} (max relative); "
+          f"rho {l2_rho:.2e}, T {l2_T:.2e} (relative L2)")
     if storage == lbm.STORE_F16_SHIFTED:
         assert e_rho < 1.5e-2 and e_T < 5e-3, (e_rho, e_T)
     else:
         assert np.all(np.isfinite(fg)) and np.all(np.isfinite(gg)) and e_T < 0.1, (e_rho, e_T)
+
+
+@pytest.mark.parametrize("storage", [lbm.STORE_F16_SHIFTED, lbm.STORE_BF16_SHIFTED])
+def test_16bit_storage_droplet_1000_steps_error_vs_oracle(storage, thermo):
+    """Field error of the 16-bit forms after 1000 steps of the evaporating 20^3 droplet
+    (open faces) against the oracle run from the FP32 initial state: the error of a run
+    stored in 16 bits from the start.  Printed as the max relative error and the relative
+    L2 error of rho and T.  The moving interface concentrates the error, so the max error
+    is far above the L2 error.  Both forms have to stay finite; the FP16 form's T errors
+    are bounded at about twice their measured values."""
+    p, f0, g0, fo, go = _drop_oracle(thermo)
+    lat = lbm.Lattice(dict(p, storage=storage, schedule=lbm.SCHED_SLABS))
+    lat.lbm_set_state(f0, g0)
+    lat.lbm_step(1000)
+    st, fg, gg = lat.state()
+    lat.close()
+    assert st == lbm.OK
+    rho, T, rho_o, T_o = fg.sum(0), gg.sum(0), fo.sum(0), go.sum(0)
+    e_rho, e_T = relerr(rho, rho_o), relerr(T, T_o)
+    l2_rho = float(np.linalg.norm(rho.astype(np.float64) - rho_o) / np.linalg.norm(rho_o))
+    l2_T = float(np.linalg.norm(T.astype(np.float64) - T_o) / np.linalg.norm(T_o))
+    print(f"storage {storage}: 1000-step droplet error rho {e_rho:.2e}, T {e_T:.2e} (max relative); "
+          f"rho {l2_rho:.2e}, T {l2_T:.2e} (relative L2)")
+    assert np.all(np.isfinite(fg)) and np.all(np.isfinite(gg))
+    if storage == lbm.STORE_F16_SHIFTED:
+        assert e_T < 2e-2 and l2_T < 4e-3, (e_T, l2_T)  # measured 9.4e-3 and 1.9e-3
 
 
 # The collision takes a closed form when s_q = s_pi = 1 and m^eq = M-hat f^eq (the
