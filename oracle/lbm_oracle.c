@@ -319,7 +319,7 @@ static double lambda_of_rho(const orc_params* P, double rho) {
  * g* = g - M^-1 Lambda M (g - g^eq) - w Fbar,  Fbar = rho c_v u.grad T + T (dp/dT) div u,
  * grad T = -varsigma sum c_i g_i / c_s^2 (Eqs. 27-29), lambda = (1/varsigma - 1/2) c_s^2. */
 void orc_collide7(const orc_params* P, const double g[7], double rho, double T, const double u[3],
-                  double divu, double dpdT, double gstar[7]) {
+                  double divu, double dpdT, double d2T, double gstar[7]) {
   init_tables();
   double cs2 = P->wbar / 3.0;
   double w7[7];
@@ -349,7 +349,9 @@ void orc_collide7(const orc_params* P, const double g[7], double rho, double T, 
   for (int i = 0; i < 7; ++i) {
     double s = 0.0;
     for (int r = 0; r < 7; ++r) s += M7i[i][r] * ms[r];
-    gstar[i] = s - w7[i] * Fbar;
+    /* Eq. 13: + dt F_i with F_i = -w_i Fbar (Eq. 15), + vartheta dt S_i with
+       S_i = w_i rho c_v (dt/2) d^2T/dt^2 (Eq. 16), dt = 1 */
+    gstar[i] = s - w7[i] * Fbar + P->vartheta * w7[i] * rho * P->cv * 0.5 * d2T;
   }
 }
 
@@ -400,7 +402,7 @@ static int dims(const orc_params* P, int a) { return a == 0 ? P->nx : (a == 1 ? 
 
 int orc_check(const orc_params* P) {
   if (P->nx < 1 || P->ny < 1 || P->nz < 1) return ORC_ERR_ARG;
-  if (P->vartheta != 0) return ORC_ERR_ARG;
+  if (P->vartheta != 0 && P->vartheta != 1) return ORC_ERR_ARG;
   if (P->lambda_l != P->lambda_v && !(P->rho_l > P->rho_v)) return ORC_ERR_ARG;
   if (!(P->cv > 0) || !(P->wbar > 0 && P->wbar < 1) || !(P->lambda_l > 0) || !(P->lambda_v > 0)) return ORC_ERR_ARG;
   for (int a = 0; a < 3; ++a) {
@@ -688,10 +690,14 @@ int orc_macros(const orc_params* P, const double* f, const double* g, orc_fields
   return st;
 }
 
-int orc_step(const orc_params* P, const double* const* Tface, const double* f, const double* g, double* fo,
-             double* go, orc_fields* diag) {
+/* One step.  Th (2N, NULL when vartheta = 0): T at t-1 and t-2; d^2T/dt^2 at t is the
+ * backward second difference T(t) - 2 T(t-1) + T(t-2) (dt = 1).  Tho (2N): T at t and
+ * t-1 for the next step. */
+static int step_impl(const orc_params* P, const double* const* Tface, const double* f, const double* g,
+                     const double* Th, double* fo, double* go, double* Tho, orc_fields* diag) {
   init_tables();
   if (orc_check(P)) return ORC_ERR_ARG;
+  if (P->vartheta && (!Th || !Tho)) return ORC_ERR_ARG;
   const int nx = P->nx, ny = P->ny, nz = P->nz;
   const long N = (long)nx * ny * nz;
   work_t w;
@@ -785,7 +791,8 @@ int orc_step(const orc_params* P, const double* const* Tface, const double* f, c
         divu *= 3.0; /* 1 / c_s-hat^2 */
         double gl[7], gsl[7], u[3] = {w.ux[c], w.uy[c], w.uz[c]};
         for (int i = 0; i < 7; ++i) gl[i] = g[i * N + c];
-        orc_collide7(P, gl, w.rho[c], w.T[c], u, divu, w.dpdT[c], gsl);
+        const double d2T = Th ? w.T[c] - 2.0 * Th[c] + Th[N + c] : 0.0;
+        orc_collide7(P, gl, w.rho[c], w.T[c], u, divu, w.dpdT[c], d2T, gsl);
         for (int i = 0; i < 7; ++i) gs[i * N + c] = gsl[i];
       }
 
@@ -829,9 +836,47 @@ int orc_step(const orc_params* P, const double* const* Tface, const double* f, c
         }
   }
 
+  if (Tho)
+    for (long c = 0; c < N; ++c) {
+      Tho[N + c] = Th[c];
+      Tho[c] = w.T[c];
+    }
+
   free(fs);
   free(gs);
   free(w.block);
+  return st;
+}
+
+int orc_step(const orc_params* P, const double* const* Tface, const double* f, const double* g, double* fo,
+             double* go, orc_fields* diag) {
+  return step_impl(P, Tface, f, g, NULL, fo, go, NULL, diag);
+}
+
+int orc_step_hist(const orc_params* P, const double* const* Tface, const double* f, const double* g,
+                  const double* Th, double* fo, double* go, double* Tho) {
+  return step_impl(P, Tface, f, g, Th, fo, go, Tho, NULL);
+}
+
+int orc_run_hist(const orc_params* P, const double* const* Tface, double* f, double* g, double* Th, int nsteps) {
+  long N = (long)P->nx * P->ny * P->nz;
+  double* f2 = (double*)malloc(sizeof(double) * 19 * N);
+  double* g2 = (double*)malloc(sizeof(double) * 7 * N);
+  double* T2 = (double*)malloc(sizeof(double) * 2 * N);
+  int st = ORC_OK;
+  for (int s = 0; s < nsteps; ++s) {
+    int r = step_impl(P, Tface, f, g, Th, f2, g2, T2, NULL);
+    memcpy(f, f2, sizeof(double) * 19 * N);
+    memcpy(g, g2, sizeof(double) * 7 * N);
+    memcpy(Th, T2, sizeof(double) * 2 * N);
+    if (r != ORC_OK) {
+      st = r;
+      break;
+    }
+  }
+  free(f2);
+  free(g2);
+  free(T2);
   return st;
 }
 

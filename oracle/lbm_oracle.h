@@ -30,7 +30,7 @@ typedef struct {
   double cv, wbar;                   /* specific heat; D3Q7 rest-weight parameter (Eq. 14) */
   double lambda_l, lambda_v;         /* thermal conductivity of liquid / vapor */
   double rho_l, rho_v;               /* coexistence densities used to interpolate lambda */
-  int vartheta;                      /* correction-term switch of Eq. 13; only 0 is supported */
+  int vartheta;                      /* correction-term switch of Eq. 13 (0 or 1; 1 needs the T history) */
   int meq_printed;                   /* 1: rows 16-18 of m^eq exactly as printed in Eq. 9 */
   int wall_ueq_zero;                 /* 1: u^eq := 0 at bounce-back wall nodes (Sec. 3.1) */
   int eos_kind;                      /* 0: Peng-Robinson; 1: isothermal ideal gas p = c0*rho */
@@ -63,8 +63,9 @@ void orc_feq19(double rho, const double u[3], double feq[19]);
 void orc_meq19(const orc_params* P, double rho, const double u[3], double meq[19]);
 void orc_collide19(const orc_params* P, const double f[19], double rho, const double ueq[3],
                    const double F[3], double fstar[19]);
+/* d2T: d^2T/dt^2 at the cell, entering through S_i of Eq. 16 when vartheta = 1 */
 void orc_collide7(const orc_params* P, const double g[7], double rho, double T, const double u[3],
-                  double divu, double dpdT, double gstar[7]);
+                  double divu, double dpdT, double d2T, double gstar[7]);
 void orc_zouhe(const orc_params* P, int face, const double F[3], double f[19]);
 
 /* whole-lattice operations.  Tface[f] (may be NULL) holds a per-node Dirichlet
@@ -75,6 +76,12 @@ int orc_macros(const orc_params* P, const double* f, const double* g, orc_fields
 int orc_step(const orc_params* P, const double* const* Tface, const double* f, const double* g,
              double* f_out, double* g_out, orc_fields* diag);
 int orc_run(const orc_params* P, const double* const* Tface, double* f, double* g, int nsteps);
+/* vartheta = 1 (or 0): Th (2N) holds T at t-1 and t-2, and d^2T/dt^2 at t is the backward
+ * second difference T(t) - 2 T(t-1) + T(t-2); Th_out (2N) receives T at t and t-1.
+ * orc_step and orc_run take vartheta = 0 only. */
+int orc_step_hist(const orc_params* P, const double* const* Tface, const double* f, const double* g,
+                  const double* Th, double* f_out, double* g_out, double* Th_out);
+int orc_run_hist(const orc_params* P, const double* const* Tface, double* f, double* g, double* Th, int nsteps);
 int orc_stream_map19(const orc_params* P, int* dst);
 int orc_stream_map7(const orc_params* P, int* src);
 int orc_node_class(const orc_params* P, unsigned char* cls);

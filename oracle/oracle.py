@@ -62,7 +62,7 @@ def lib():
         L.orc_meq19.restype = None
         L.orc_collide19.argtypes = [P, _PD, _D, _PD, _PD, _PD]
         L.orc_collide19.restype = None
-        L.orc_collide7.argtypes = [P, _PD, _D, _D, _PD, _D, _D, _PD]
+        L.orc_collide7.argtypes = [P, _PD, _D, _D, _PD, _D, _D, _D, _PD]
         L.orc_collide7.restype = None
         L.orc_zouhe.argtypes = [P, ct.c_int, _PD, _PD]
         L.orc_zouhe.restype = None
@@ -70,6 +70,8 @@ def lib():
         L.orc_macros.argtypes = [P, _PD, _PD, ct.POINTER(OrcFields)]
         L.orc_step.argtypes = [P, ct.POINTER(_PD), _PD, _PD, _PD, _PD, ct.POINTER(OrcFields)]
         L.orc_run.argtypes = [P, ct.POINTER(_PD), _PD, _PD, ct.c_int]
+        L.orc_step_hist.argtypes = [P, ct.POINTER(_PD), _PD, _PD, _PD, _PD, _PD, _PD]
+        L.orc_run_hist.argtypes = [P, ct.POINTER(_PD), _PD, _PD, _PD, ct.c_int]
         L.orc_stream_map19.argtypes = [P, ct.POINTER(ct.c_int)]
         L.orc_stream_map7.argtypes = [P, ct.POINTER(ct.c_int)]
         L.orc_node_class.argtypes = [P, ct.POINTER(ct.c_ubyte)]
@@ -180,6 +182,32 @@ class Oracle:
         del keep
         return st, f, g
 
+    def history(self, g):
+        """T history of a state at rest before t = 0: T(t-1) = T(t-2) = T = sum g."""
+        T = np.asarray(g, dtype=np.float64).reshape(7, self.N).sum(0)
+        return np.stack([T, T])
+
+    def step_hist(self, f, g, Th):
+        """One step with the T history Th = [T(t-1), T(t-2)] (vartheta = 1 needs it);
+        returns (status, f, g, [T(t), T(t-1)])."""
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(19, self.N)
+        g = np.ascontiguousarray(g, dtype=np.float64).reshape(7, self.N)
+        Th = np.ascontiguousarray(Th, dtype=np.float64).reshape(2, self.N)
+        fo, go, Tho = np.empty_like(f), np.empty_like(g), np.empty_like(Th)
+        tf, keep = _tface_array(self.tface)
+        st = lib().orc_step_hist(ct.byref(self.p), tf, _ptr(f), _ptr(g), _ptr(Th), _ptr(fo), _ptr(go), _ptr(Tho))
+        del keep
+        return st, fo, go, Tho
+
+    def run_hist(self, f, g, Th, nsteps):
+        f = np.array(f, dtype=np.float64).reshape(19, self.N)
+        g = np.array(g, dtype=np.float64).reshape(7, self.N)
+        Th = np.array(Th, dtype=np.float64).reshape(2, self.N)
+        tf, keep = _tface_array(self.tface)
+        st = lib().orc_run_hist(ct.byref(self.p), tf, _ptr(f), _ptr(g), _ptr(Th), int(nsteps))
+        del keep
+        return st, f, g, Th
+
     def _fields_struct(self):
         out = {n: np.empty(self.N) for n, _ in OrcFields._fields_}
         s = OrcFields(*[_ptr(out[n]) for n, _ in OrcFields._fields_])
@@ -216,11 +244,11 @@ class Oracle:
         lib().orc_collide19(ct.byref(self.p), _ptr(f), rho, _ptr(ueq), _ptr(F), _ptr(out))
         return out
 
-    def collide7(self, g, rho, T, u, divu, dpdT):
+    def collide7(self, g, rho, T, u, divu, dpdT, d2T=0.0):
         g = np.ascontiguousarray(g, dtype=np.float64)
         u = np.ascontiguousarray(u, dtype=np.float64)
         out = np.empty(7)
-        lib().orc_collide7(ct.byref(self.p), _ptr(g), rho, T, _ptr(u), divu, dpdT, _ptr(out))
+        lib().orc_collide7(ct.byref(self.p), _ptr(g), rho, T, _ptr(u), divu, dpdT, d2T, _ptr(out))
         return out
 
     def zouhe(self, face, f, F):

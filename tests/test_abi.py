@@ -42,7 +42,7 @@ def test_params_struct_matches_header():
 
 @pytest.mark.parametrize("bad", [
     dict(nx=0),
-    dict(vartheta=1),
+    dict(vartheta=2),
     dict(face_kind=[1, 1, 2, 2, 0, 0]),   # wall next to an open face
     dict(face_kind=[1, 0, 0, 0, 0, 0]),   # half-periodic axis
     dict(face_kind=[0, 0, 0, 0, 2, 2], face_rho=[0] * 6),

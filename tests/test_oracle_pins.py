@@ -626,3 +626,53 @@ def test_wall_force_uses_the_wetting_ghost_layer(theta):
             Fexp = psi[0, yy, xx] * s  # -G psi sum(...) with G = -1
             c = xx + nx * yy
             np.testing.assert_allclose([m["Fx"][c], m["Fy"][c], m["Fz"][c]], Fexp, rtol=1e-12, atol=1e-15)
+
+
+# ------------------------------------------------- vartheta = 1 (Eq. 16) ----
+
+@pytest.mark.parametrize("eos_kind", [0, 1])
+def test_vartheta_correction_on_a_uniform_state_at_rest(eos_kind):
+    """Uniform, periodic, at rest: F = 0, div u = 0 and g is in equilibrium, so Eq. 13 with
+    S_i = w_i rho c_v (dt/2) d^2T/dt^2 (Eq. 16) gives g*_i = w_i (T + rho c_v d2T / 2), and the
+    relaxed streaming (divided by rho c_v) moves T by exactly d2T / 2 with d2T = T - 2 T(t-1)
+    + T(t-2); vartheta = 0 leaves T unchanged whatever the history."""
+    rho, Tm = 0.38, 0.0627
+    p = W.base_params(4, 4, 4, rho_v=0.38, rho_l=6.5, lambda_l=0.4, lambda_v=0.2, eos_kind=eos_kind, eos_c0=0.2)
+    for vt in (0, 1):
+        o = Oracle(dict(p, vartheta=vt))
+        f, g = o.init_state(np.full(64, rho), np.full(64, Tm))
+        Th = np.stack([np.full(64, Tm * 1.01), np.full(64, Tm * 0.97)])
+        st, f2, g2, Th2 = o.step_hist(f, g, Th)
+        assert st == 0
+        d2 = Tm - 2 * Tm * 1.01 + Tm * 0.97
+        np.testing.assert_allclose(g2.sum(0), Tm + vt * d2 / 2, rtol=1e-13)
+        np.testing.assert_allclose(Th2, np.stack([g.sum(0), Th[0]]), rtol=1e-15)
+        np.testing.assert_allclose(f2, f, rtol=1e-13)
+    assert Oracle(dict(p, vartheta=1)).step(f, g)[0] != 0  # the history is required
+
+
+def test_vartheta_one_removes_the_second_order_time_error_of_diffusion():
+    """Eq. 263: the recovered equation carries (vartheta - 1)(dt/2) rho c_v d^2T/dt^2.  For
+    a diffusion mode T ~ exp(-r t) sin(kz) with a = lambda k^2 / (rho c_v), d^2T/dt^2 = r^2 T,
+    so vartheta = 0 decays at r0 = a + r0^2/2 and vartheta = 1 at r1 = a (to this order):
+    r0 - r1 = a^2/2 up to O(a^3).  The lattice's spatial error shifts both rates alike and
+    cancels in the difference.  Ideal gas (no T coupling), u = 0; the history starts at
+    rest, whose transient decays as 0.5^(t/2), so the rates are fitted from t = 40 on."""
+    nz, lam, cv, rho = 16, 1.0 / 3.0, 1.0, 1.0
+    p = W.base_params(1, 1, nz, eos_kind=1, eos_c0=0.2, lambda_l=lam, lambda_v=lam, cv=cv)
+    k = 2 * np.pi / nz
+    z = np.arange(nz, dtype=float)
+    a = lam * k * k / (rho * cv)
+    rates = []
+    for vt in (0, 1):
+        o = Oracle(dict(p, vartheta=vt))
+        f, g = o.init_state(np.full(nz, rho), 1.0 + 1e-3 * np.sin(k * z))
+        Th = o.history(g)
+        st, f, g, Th = o.run_hist(f, g, Th, 40)
+        a1 = _mode(g.sum(0) - 1.0, k, z)[0]
+        st, f, g, Th = o.run_hist(f, g, Th, 80)
+        assert st == 0
+        a2 = _mode(g.sum(0) - 1.0, k, z)[0]
+        rates.append(-np.log(a2 / a1) / 80)
+    r0, r1 = rates
+    assert abs((r0 - r1) - a * a / 2) < 0.15 * a * a / 2, (r0, r1, a)
