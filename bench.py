@@ -17,8 +17,9 @@ the end-to-end rate through host buffers, the FP64 CPU oracle on a bounded sampl
 (cpu_baseline), the adjoint/forward cost on a 64^3 droplet over 2000 steps with
 checkpoints every 100 (adjoint), 48 uneven droplet domains stepped as one batch
 (batched), and the 512^3 heated-plate pool with 64 droplets in FP16-shifted
-storage (large); --no-adjoint / --no-batched / --no-large / --no-cpu-baseline
-skip those.
+storage (large), and the step time with the correction term of Eq. 16
+(vartheta = 1) against without (vartheta); --no-adjoint / --no-batched /
+--no-large / --no-vartheta / --no-cpu-baseline skip those.
 
 N > 1 (torchrun, one rank per GPU) runs N independent replicas of the domain
 (weak scaling, no collective on the data path).  --impl reference times the
@@ -295,6 +296,31 @@ def large_pool(lbm, Tc, rv, rl, stream, steps=100, warmup=10):
             "step_frac": step_bytes * mlups * 1e6 / 1e9 / peak}
 
 
+def vartheta_cost(lbm, p, rho0, T0, stream, steps=2000, warmup=50):
+    """Step time of the workload with the correction term of Eq. 16 (vartheta = 1) against
+    without, both in the slab schedule; the paper compares the two in CPU time (Table 1)."""
+    import torch
+    rho_d = torch.tensor(rho0.reshape(-1), dtype=torch.float32, device="cuda")
+    T_d = torch.tensor(T0.reshape(-1), dtype=torch.float32, device="cuda")
+    ms = {}
+    for vt in (0, 1):
+        lat = lbm.Lattice(dict(p, vartheta=vt, schedule=lbm.SCHED_SLABS), rho_d, T_d, stream=stream.cuda_stream)
+        lat.lbm_step(warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lat.lbm_step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = lat.lbm_sync()
+        lat.close()
+        if st != lbm.OK:
+            raise SystemExit(f"vartheta={vt} run failed: {lbm.lbm_status_string(st)}")
+        ms[vt] = e0.elapsed_time(e1) / steps
+    return {"ms_per_step_vartheta0": ms[0], "ms_per_step_vartheta1": ms[1], "ratio": ms[1] / ms[0],
+            "paper_cpu_ratio": 55983.6 / 54461.5, "steps": steps}
+
+
 def thermo_product():
     """T_c and the coexistence densities from the library's host helpers (not the oracle)."""
     from paper_2206_00946_gb300 import lbm
@@ -366,6 +392,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-domains measurement")
     ap.add_argument("--no-large", action="store_true", help="skip the 512^3 FP16 pool measurement")
     ap.add_argument("--adjoint-side", type=int, default=64, help="cube side of the adjoint workload (64)")
+    ap.add_argument("--no-vartheta", action="store_true", help="skip the vartheta = 1 cost measurement")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = dist_env()
@@ -467,6 +494,9 @@ def main():
     large = None
     if args.storage == "f32" and not args.no_large:
         large = large_pool(lbm, Tc, rv, rl, stream)
+    vartheta = None
+    if args.storage == "f32" and not args.no_vartheta:
+        vartheta = vartheta_cost(lbm, p, rho0, T0, stream)
 
     if rank != 0:
         if dist:
@@ -510,6 +540,7 @@ def main():
         "adjoint": adj,
         "batched": batched,
         "large": large,
+        "vartheta": vartheta,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * N / args.steps,
                 "d2h_bytes_per_step": 5 * 4 * N / args.steps},
         "gpu_launches": launches * args.steps,

@@ -82,7 +82,12 @@ typedef struct lbm_params {
                                     linearly in the liquid fraction (rho-rho_v)/(rho_l-rho_v), and
                                     varsigma_{1,2,3} = 1 / (lambda / c_s^2 + 1/2) (Sec. 2.2) */
   double rho_l, rho_v;           /* coexistence densities used by that interpolation */
-  int vartheta;                  /* correction switch of Eq. 13; only 0 (the paper's choice) */
+  int vartheta;                  /* correction switch of Eq. 13: 0 (the paper's choice) or 1, the
+                                    S_i of Eq. 16 with d^2T/dt^2 the backward second difference of
+                                    the per-cell T of the two previous steps (kept by the library,
+                                    8 bytes per cell; a state set by lbm_init or lbm_set_state is
+                                    taken to be at rest before, and checkpoints carry the history);
+                                    lbm_record and batching need 0 */
   int meq_printed;               /* 0: m^eq = M-hat f^eq; 1: rows 16-18 exactly as printed in Eq. 9 */
   int wall_ueq_zero;             /* 1: u^eq = 0 and u = 0 at bounce-back wall nodes (Sec. 3.1) */
   int eos_kind;                  /* 0: Peng-Robinson; 1: ideal gas p = eos_c0 * rho (verification) */

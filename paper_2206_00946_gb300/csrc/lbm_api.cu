@@ -89,10 +89,19 @@ __global__ void __launch_bounds__(256, LBM_PHASEC_MINBLOCKS) k_phaseBC19(Params 
     phaseBC19(P, c, fA, fB, X);
 }
 
-template <typename T>
+// VT: vartheta of the context (a separate instantiation each, launched by launch_c7)
+template <typename T, int VT>
 __global__ void __launch_bounds__(256, 4) k_phaseC7(Params P, const T* __restrict__ gA, T* gB, Aux X, int c0, int c1) {
   for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x)
-    phaseC7(P, c, gA, gB, X);
+    phaseC7<T, VT>(P, c, gA, gB, X);
+}
+
+template <typename T>
+void launch_c7(const lbm_ctx* c, int blocks, cudaStream_t st, const T* gA, T* gB, int c0, int c1) {
+  if (c->P.vartheta)
+    k_phaseC7<T, 1><<<blocks, kThreads, 0, st>>>(c->P, gA, gB, c->X, c0, c1);
+  else
+    k_phaseC7<T, 0><<<blocks, kThreads, 0, st>>>(c->P, gA, gB, c->X, c0, c1);
 }
 
 // one thread per boundary candidate (boundary_candidate enumerates them)
@@ -219,7 +228,7 @@ int check_params(const lbm_params* p) {
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) return LBM_ERR_ARG;
   const long long N = (long long)p->nx * p->ny * p->nz;
   if (N > (1LL << 31) - 1) return LBM_ERR_ARG;
-  if (p->vartheta != 0) return LBM_ERR_ARG;
+  if (p->vartheta != 0 && p->vartheta != 1) return LBM_ERR_ARG;
   if (p->storage != LBM_STORE_F32 && p->storage != LBM_STORE_F16_SHIFTED && p->storage != LBM_STORE_BF16_SHIFTED)
     return LBM_ERR_ARG;
   if (p->storage != LBM_STORE_F32 && p->schedule == LBM_SCHED_FUSED) return LBM_ERR_ARG;  // FP32 only
@@ -266,6 +275,7 @@ Params make_device_params(const lbm_params& p) {
   }
   P.meq_printed = p.meq_printed;
   P.wall_ueq_zero = p.wall_ueq_zero;
+  P.vartheta = p.vartheta;
   P.eos_kind = p.eos_kind;
   P.a = (float)p.a;
   P.b = (float)p.b;
@@ -445,7 +455,7 @@ int step_phases_t(lbm_ctx* c) {
     prof_end(c, 2, e);
     // the D3Q7 phase needs the velocity of the neighbours: after the whole D3Q19 pass
     e = prof_begin(c);
-    k_phaseC7<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, gbuf<T>(c, a), gbuf<T>(c, b), c->X, 0, (int)c->N);
+    launch_c7<T>(c, c->grid, c->stream, gbuf<T>(c, a), gbuf<T>(c, b), 0, (int)c->N);
     prof_end(c, 5, e);
   }
   if (c->P.bd_total > 0) {
@@ -627,7 +637,7 @@ int slab_enqueue_step_t(lbm_ctx* c, bool first) {
         k_phaseBC19<T><<<blocks, kThreads, 0, st>>>(c->P, fbuf<T>(c, a), fbuf<T>(c, b), c->X, c0, c1);
         break;
       case SPH_C7:
-        k_phaseC7<T><<<blocks, kThreads, 0, st>>>(c->P, gbuf<T>(c, a), gbuf<T>(c, b), c->X, c0, c1);
+        launch_c7<T>(c, blocks, st, gbuf<T>(c, a), gbuf<T>(c, b), c0, c1);
         break;
       default: {
         int maxcnt = 0;
@@ -749,6 +759,21 @@ int convert_state(lbm_ctx* c, float* f, float* g, int mem, bool in) {
 
 }  // namespace
 
+namespace {
+
+// vartheta = 1: the T history of a state taken to be at rest before now,
+// T(t-1) = T(t-2) = T = sum g of the current populations.
+template <typename T>
+int hist_reset_t(lbm_ctx* c) {
+  k_sumT<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, gbuf<T>(c, c->cur), c->X.T1);
+  if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
+  return cuda_status(cudaMemcpyAsync(c->X.T2, c->X.T1, sizeof(float) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+}
+
+int hist_reset(lbm_ctx* c) { return c->hist ? LBM_WITH_STORAGE(c, hist_reset_t, c) : LBM_OK; }
+
+}  // namespace
+
 extern "C" {
 
 const char* lbm_status_string(int s) {
@@ -858,6 +883,7 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
     ok = ok && cudaMalloc(&c->g[k], c->esize * 7 * N) == cudaSuccess;
   }
   ok = ok && cudaMalloc(&c->aux, sizeof(float) * 11 * N) == cudaSuccess;
+  if (p->vartheta) ok = ok && cudaMalloc(&c->hist, sizeof(float) * 2 * N) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
@@ -882,6 +908,10 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
   }
   float* a = c->aux;
   c->X = Aux{a, a + N, a + 2 * N, a + 3 * N, a + 4 * N, a + 5 * N, a + 6 * N, a + 7 * N, a + 8 * N, a + 9 * N, a + 10 * N};
+  if (c->hist) {
+    c->X.T1 = c->hist;
+    c->X.T2 = c->hist + N;
+  }
   if (cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream) != cudaSuccess) {
     lbm_destroy(c);
     return LBM_ERR_CUDA;
@@ -931,7 +961,7 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
                                                                  gbuf<__nv_bfloat16>(c, 0));
     else
       k_init<float><<<c->grid, kThreads, 0, c->stream>>>(c->P, r, t, fbuf<float>(c, 0), gbuf<float>(c, 0));
-    if (cudaGetLastError() != cudaSuccess) {
+    if (cudaGetLastError() != cudaSuccess || hist_reset(c) != LBM_OK) {
       lbm_destroy(c);
       return LBM_ERR_CUDA;
     }
@@ -950,6 +980,7 @@ int lbm_set_state(lbm_ctx* c, const float* f, const float* g, int mem) {
   } else {
     st = convert_state(c, const_cast<float*>(f), const_cast<float*>(g), mem, true);
   }
+  if (!st) st = hist_reset(c);
   if (!st && mem == LBM_MEM_HOST) st = cuda_status(cudaStreamSynchronize(c->stream));
   if (!st && fused_reset(&c->plan, c->P, c->stream)) st = LBM_ERR_CUDA;
   if (!st) st = cuda_status(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream));
@@ -973,12 +1004,14 @@ int lbm_get_state(lbm_ctx* c, float* f, float* g, int mem) {
 
 namespace {
 
-// Checkpoint image: this header, then f (19 N) and g (7 N) in the storage format.
+// Checkpoint image: this header, then f (19 N) and g (7 N) in the storage format,
+// then, for vartheta = 1, the T history (2 N floats).
 struct CkptHeader {
   char magic[8];
   int32_t version, nx, ny, nz, storage, esize;
   float rho_ref, T_ref;
-  int32_t pad[64 - 10];
+  int32_t vartheta;
+  int32_t pad[64 - 11];
 };
 static_assert(sizeof(CkptHeader) == 256, "checkpoint header is 256 bytes");
 constexpr char kCkptMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '1'};
@@ -994,6 +1027,7 @@ CkptHeader ckpt_header(const lbm_ctx* c) {
   h.esize = (int32_t)c->esize;
   h.rho_ref = c->P.rho_ref;
   h.T_ref = c->P.T_ref;
+  h.vartheta = c->P.vartheta;
   return h;
 }
 
@@ -1001,7 +1035,8 @@ CkptHeader ckpt_header(const lbm_ctx* c) {
 
 long long lbm_checkpoint_bytes(const lbm_ctx* c) {
   if (!c) return 0;
-  return (long long)sizeof(CkptHeader) + 26LL * c->N * (long long)c->esize;
+  return (long long)sizeof(CkptHeader) + 26LL * c->N * (long long)c->esize +
+         (c->hist ? 2LL * c->N * (long long)sizeof(float) : 0LL);
 }
 
 int lbm_checkpoint(lbm_ctx* c, void* dst, int mem) {
@@ -1013,6 +1048,7 @@ int lbm_checkpoint(lbm_ctx* c, void* dst, int mem) {
   const size_t fb = 19ull * c->N * c->esize, gb = 7ull * c->N * c->esize;
   LBM_TRY(cudaMemcpyAsync(d + sizeof(h), c->f[c->cur], fb, kd, c->stream));
   LBM_TRY(cudaMemcpyAsync(d + sizeof(h) + fb, c->g[c->cur], gb, kd, c->stream));
+  if (c->hist) LBM_TRY(cudaMemcpyAsync(d + sizeof(h) + fb + gb, c->hist, 2ull * c->N * sizeof(float), kd, c->stream));
   if (mem == LBM_MEM_HOST) {
     std::memcpy(d, &h, sizeof(h));
   } else {
@@ -1033,12 +1069,14 @@ int lbm_restore(lbm_ctx* c, const void* src, int mem) {
   }
   const CkptHeader e = ckpt_header(c);
   if (std::memcmp(h.magic, e.magic, 8) != 0 || h.version != e.version || h.nx != e.nx || h.ny != e.ny ||
-      h.nz != e.nz || h.storage != e.storage || h.esize != e.esize || h.rho_ref != e.rho_ref || h.T_ref != e.T_ref)
+      h.nz != e.nz || h.storage != e.storage || h.esize != e.esize || h.rho_ref != e.rho_ref || h.T_ref != e.T_ref ||
+      h.vartheta != e.vartheta)
     return LBM_ERR_ARG;
   const cudaMemcpyKind kd = mem == LBM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   const size_t fb = 19ull * c->N * c->esize, gb = 7ull * c->N * c->esize;
   LBM_TRY(cudaMemcpyAsync(c->f[c->cur], s + sizeof(h), fb, kd, c->stream));
   LBM_TRY(cudaMemcpyAsync(c->g[c->cur], s + sizeof(h) + fb, gb, kd, c->stream));
+  if (c->hist) LBM_TRY(cudaMemcpyAsync(c->hist, s + sizeof(h) + fb + gb, 2ull * c->N * sizeof(float), kd, c->stream));
   if (mem == LBM_MEM_HOST) LBM_TRY(cudaStreamSynchronize(c->stream));
   if (fused_reset(&c->plan, c->P, c->stream)) return LBM_ERR_CUDA;
   LBM_TRY(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream));
@@ -1197,6 +1235,7 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->g[k]);
   }
   cudaFree(c->aux);
+  cudaFree(c->hist);
   if (c->side) cudaStreamSynchronize(c->side);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);

@@ -283,7 +283,7 @@ extern "C" int lbm_batch_create(lbm_batch** out, lbm_ctx* const* ctxs, int n) {
   *out = nullptr;
   for (int d = 0; d < n; ++d) {
     const lbm_ctx* c = ctxs[d];
-    if (!c || c->hp.storage != LBM_STORE_F32 || c->stream != ctxs[0]->stream) return LBM_ERR_ARG;
+    if (!c || c->hp.storage != LBM_STORE_F32 || c->hp.vartheta || c->stream != ctxs[0]->stream) return LBM_ERR_ARG;
     if (!c->has_state) return LBM_ERR_STATE;
   }
   lbm_batch* b = new (std::nothrow) lbm_batch();

@@ -87,6 +87,7 @@ struct Params {
   unsigned dpl_mul, dpl_shr, dper_mul, dper_shr;
   long long bd_total;
   int meq_printed, wall_ueq_zero, eos_kind;
+  int vartheta;  // 1: the correction S_i of Eqs. 13 and 16 (needs the T history of Aux)
   float a, b, R, kappa, inv_Tc, G, inv_G, eos_c0;
   float s_e, s_v, s_q, s_pi;
   float cv, inv_cv, wbar, inv_cs2t;  // c_s^2 of D3Q7 = wbar/3
@@ -344,17 +345,20 @@ LBM_HD R lambda_of(const Params& P, R rho) {
   return P.lambda_v + (P.lambda_l - P.lambda_v) * phi;
 }
 
-// Eq. 13 collision with the source of Eq. 15: g* = g - M^-1 Lambda M (g - w T) - w Fbar,
+// Eq. 13 collision with the source of Eq. 15: g* = g - M^-1 Lambda M (g - w T) - w Fbar
+// (+ vartheta w rho c_v d2T / 2, the S_i of Eq. 16 with dt = 1; d2T = d^2T/dt^2),
 // Lambda = diag(1, vs, vs, vs, 1, 1, 1), vs from lambda, grad T = -vs m_alpha / c_s^2.
-template <typename R>
+// VT: vartheta known at compile time (0 or 1), or -1 to read it from P.
+template <typename R, int VT = -1>
 LBM_HD void collide7(const Params& P, const R* g, R rho, R T, R ux, R uy, R uz, R divu,
-                     R dpdT, R* gs) {
+                     R dpdT, R d2T, R* gs) {
   const R m1 = g[1] - g[2], m2 = g[3] - g[4], m3 = g[5] - g[6];
   const R vs = rcp(lambda_of(P, rho) * P.inv_cs2t + R(0.5));
   const R k = -vs * P.inv_cs2t;
   const R ugT = k * (ux * m1 + uy * m2 + uz * m3);
   const R Fbar = rho * P.cv * ugT + T * dpdT * divu;
-  const R h = T - Fbar;
+  R h = T - Fbar;
+  if (VT < 0 ? P.vartheta != 0 : VT != 0) h += R(0.5) * rho * P.cv * d2T;
   const R w0 = R(1) - P.wbar, w1 = P.wbar * (R(1) / R(6));
   const R r = R(0.5) * (R(1) - vs);
   gs[0] = w0 * h;

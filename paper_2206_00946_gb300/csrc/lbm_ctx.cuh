@@ -56,6 +56,7 @@ struct lbm_ctx {
   size_t esize;
   int cur;
   float* aux;
+  float* hist;  // vartheta = 1: T at the two previous steps (2N floats, X.T1 and X.T2)
   Aux X;
   float* tface[6];
   long long tface_n[6];

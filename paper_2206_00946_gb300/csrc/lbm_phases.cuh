@@ -23,6 +23,7 @@ struct Aux {
   float *rho, *jx, *jy, *jz, *psi;  // phase A
   float *Fx, *Fy, *Fz, *ux, *uy, *uz;  // phase B
   float *gstar, *divu;  // optional (NULL): the D3Q7 phase also stores g* (7N) and div u
+  float *T1, *T2;       // vartheta = 1: T at the two previous steps, kept by the D3Q7 phase
 };
 
 // L2 residency: population loads stream through once per kernel (evict-first),
@@ -473,9 +474,11 @@ __device__ __forceinline__ float divu_at(const Params& P, int c, const Nb& nb, c
 // Phase C, D3Q7 part: div u by the isotropic D3Q19 difference, grad T from the
 // local moments, collision with the source, relaxed push streaming.  rho and the
 // real velocity of the cell come from phases A and B.
-template <typename ST>
+// VT: vartheta known at compile time (0 or 1), or -1 to read it from P.
+template <typename ST, int VT = -1>
 __device__ __forceinline__ void phaseC7_cell(const Params& P, int c, const float* gl, const ST* __restrict__ gA, ST* gB,
                                              const Aux& X) {
+  const bool vt = VT < 0 ? P.vartheta != 0 : VT != 0;
   int x, y, z;
   cell_xyz(P, c, x, y, z);
   Nb nb;
@@ -496,11 +499,19 @@ __device__ __forceinline__ void phaseC7_cell(const Params& P, int c, const float
   }
   const float rho = ld_aux(X.rho + c, h);
   const float T = sum7(gl);
+  // vartheta = 1: d^2T/dt^2 as the backward difference T - 2 T(t-1) + T(t-2); the cell's
+  // history moves on by one step after the populations are stored
+  float d2T = 0.f, T1 = 0.f;
+  if (vt) {
+    T1 = X.T1[c];
+    d2T = T - 2.f * T1 + X.T2[c];
+  }
   const float du = divu_at(P, c, nb, X, h);
   float p, dpdT;
   eos_pr(P, rho, T, p, dpdT);
   float gs[7];
-  collide7(P, gl, rho, T, ld_aux(X.ux + c, h), ld_aux(X.uy + c, h), ld_aux(X.uz + c, h), du, dpdT, gs);
+  collide7<float, VT>(P, gl, rho, T, ld_aux(X.ux + c, h), ld_aux(X.uy + c, h), ld_aux(X.uz + c, h), du, dpdT, d2T,
+                      gs);
   if (X.gstar) {  // kept for the adjoint's recomputed steps
     X.divu[c] = du;
 #pragma unroll
@@ -512,6 +523,10 @@ __device__ __forceinline__ void phaseC7_cell(const Params& P, int c, const float
   for (int i = 1; i < 7; ++i) {
     if (nb_kind(nb, c7x(i), c7y(i), c7z(i))) continue;
     PopStore<ST>::st(gB + i * N + yc[i], gold[i] + (gs[i] - gold[i]) * rcp(ry[i] * P.cv), gbase(P, i));
+  }
+  if (vt) {
+    X.T2[c] = T1;
+    X.T1[c] = T;
   }
 }
 
@@ -532,14 +547,14 @@ __device__ __forceinline__ void phaseC19(const Params& P, int c, const ST* __res
   phaseC19_cell<ST>(P, c, fl, fB, X);
 }
 
-template <typename ST>
+template <typename ST, int VT = -1>
 __device__ __forceinline__ void phaseC7(const Params& P, int c, const ST* __restrict__ gA, ST* gB, const Aux& X) {
   const long long N = P.N;
   const Hint h = make_hint();
   float gl[7];
 #pragma unroll
   for (int i = 0; i < 7; ++i) gl[i] = PopStore<ST>::ld(gA + i * N + c, gbase(P, i), h);
-  phaseC7_cell<ST>(P, c, gl, gA, gB, X);
+  phaseC7_cell<ST, VT>(P, c, gl, gA, gB, X);
 }
 
 template <typename ST>

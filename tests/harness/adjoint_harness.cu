@@ -61,7 +61,7 @@ void a_collide7(const double* d, const int* k, const double* x, double* gs) {
   Params P = make(d, k);
   double T = 0;
   for (int i = 0; i < 7; ++i) T += x[i];
-  collide7(P, x, x[7], T, x[8], x[9], x[10], x[11], x[12], gs);
+  collide7(P, x, x[7], T, x[8], x[9], x[10], x[11], x[12], 0.0, gs);
 }
 void a_collide7_vjp(const double* d, const int* k, const double* x, const double* gsb, double* xb) {
   Params P = make(d, k);

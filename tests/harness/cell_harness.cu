@@ -14,7 +14,7 @@ static Params make(const double* d, const int* k) {
   P.lambda_l = (float)d[13]; P.lambda_v = (float)d[14]; P.rho_l = (float)d[15]; P.rho_v = (float)d[16];
   P.inv_drho = d[15] > d[16] ? (float)(1.0 / (d[15] - d[16])) : 0.f;
   P.lam_uniform = d[13] == d[14];
-  P.meq_printed = k[0]; P.eos_kind = k[1];
+  P.meq_printed = k[0]; P.eos_kind = k[1]; P.vartheta = k[2];
   return P;
 }
 
@@ -24,9 +24,9 @@ void h_collide19(const double* d, const int* k, const float* f, float rho, const
   collide19(P, f, rho, u[0], u[1], u[2], F[0], F[1], F[2], fs);
 }
 void h_collide7(const double* d, const int* k, const float* g, float rho, float T, const float* u, float divu,
-                float dpdT, float* gs) {
+                float dpdT, float d2T, float* gs) {
   Params P = make(d, k);
-  collide7(P, g, rho, T, u[0], u[1], u[2], divu, dpdT, gs);
+  collide7(P, g, rho, T, u[0], u[1], u[2], divu, dpdT, d2T, gs);
 }
 void h_zouhe(int face, float rho_b, const float* F, float* f) { zouhe(face, rho_b, F[0], F[1], F[2], f); }
 void h_eos(const double* d, const int* k, float rho, float T, float* out) {

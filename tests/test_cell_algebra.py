@@ -42,7 +42,7 @@ def _dk(p, o):
     kappa = 0.37464 + 1.54226 * p["omega"] - 0.26992 * p["omega"] ** 2
     d = np.array([p["a"], p["b"], p["R"], kappa, 1.0 / o.Tc(), p["G"], p["eos_c0"], p["s_e"], p["s_v"], p["s_q"],
                   p["s_pi"], p["cv"], p["wbar"], p["lambda_l"], p["lambda_v"], p["rho_l"], p["rho_v"]])
-    k = np.array([p["meq_printed"], p["eos_kind"]], dtype=np.int32)
+    k = np.array([p["meq_printed"], p["eos_kind"], p["vartheta"]], dtype=np.int32)
     return d, k
 
 
@@ -83,8 +83,9 @@ def setup_module(module):
     _C19T = tables()["c19"].T.astype(float)
 
 
-def test_collide7_matches_oracle(H):
-    p = W.base_params(2, 2, 2, lambda_l=0.4, lambda_v=0.2, rho_l=6.5, rho_v=0.38)
+@pytest.mark.parametrize("vartheta", [0, 1])
+def test_collide7_matches_oracle(H, vartheta):
+    p = W.base_params(2, 2, 2, lambda_l=0.4, lambda_v=0.2, rho_l=6.5, rho_v=0.38, vartheta=vartheta)
     o = Oracle(p)
     d, k = _dk(p, o)
     rng = np.random.default_rng(1)
@@ -95,12 +96,13 @@ def test_collide7_matches_oracle(H):
         T = g.sum()
         u = rng.uniform(-0.05, 0.05, 3).astype(np.float32).astype(np.float64)
         divu, dpdT = float(np.float32(rng.uniform(-1e-3, 1e-3))), float(np.float32(rng.uniform(0.1, 2)))
-        ref = o.collide7(g, rho, T, u, divu, dpdT)
+        d2T = float(np.float32(rng.uniform(-1e-3, 1e-3) * T))
+        ref = o.collide7(g, rho, T, u, divu, dpdT, d2T)
         ga, gp = _fp(g)
         ua, up = _fp(u)
         out = np.zeros(7, dtype=np.float32)
         H.h_collide7(*_args(d, k), gp, ct.c_float(rho), ct.c_float(T), up, ct.c_float(divu), ct.c_float(dpdT),
-                     out.ctypes.data_as(ct.POINTER(ct.c_float)))
+                     ct.c_float(d2T), out.ctypes.data_as(ct.POINTER(ct.c_float)))
         np.testing.assert_allclose(out, ref, rtol=2e-6)
 
 

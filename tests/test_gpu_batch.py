@@ -116,3 +116,13 @@ def test_batch_rejects_16bit_storage(thermo):
     with pytest.raises(lbm.LBMError):
         lbm.Batch([lat])
     lat.close()
+
+
+def test_batch_rejects_vartheta_one(thermo):
+    """The batched kernels carry no T history: a vartheta = 1 context is refused."""
+    p, rho0, T0 = _domains(thermo)[0]
+    lat = lbm.Lattice(dict(p, schedule=lbm.SCHED_PHASES, vartheta=1), rho0.reshape(-1).astype(np.float32),
+                      T0.reshape(-1).astype(np.float32))
+    with pytest.raises(lbm.LBMError):
+        lbm.Batch([lat])
+    lat.close()

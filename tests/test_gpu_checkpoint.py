@@ -82,3 +82,32 @@ def test_restore_rejects_foreign_images(thermo):
     assert empty.lbm_checkpoint(img) == lbm.ERR_STATE
     for x in (lat, other, bigger, empty):
         x.close()
+
+
+def test_restore_continues_bit_exact_with_the_T_history(thermo):
+    """vartheta = 1: the image carries the T history of the last two steps (8 B per cell),
+    so a restored run continues with the same correction terms."""
+    p, rho0, T0 = _droplet(thermo, schedule=lbm.SCHED_SLABS)
+    p.update(vartheta=1)
+    lat = lbm.Lattice(p, rho0, T0)
+    lat.lbm_step(7)
+    nb = lat.lbm_checkpoint_bytes()
+    assert nb == 256 + 26 * lat.N * 4 + 8 * lat.N
+    img = np.empty(nb, dtype=np.uint8)
+    assert lat.lbm_checkpoint(img) == lbm.OK
+    lat.lbm_step(5)
+    st, f1, g1 = lat.state()
+    lat.lbm_restore(img)
+    lat.lbm_step(5)
+    st2, f2, g2 = lat.state()
+    assert st == st2 == lbm.OK
+    assert np.array_equal(f1, f2) and np.array_equal(g1, g2)
+    # an image of the same lattice without the history is not accepted
+    q = dict(p, vartheta=0)
+    other = lbm.Lattice(q, rho0, T0)
+    img0 = np.empty(other.lbm_checkpoint_bytes(), dtype=np.uint8)
+    assert other.lbm_checkpoint(img0) == lbm.OK
+    with pytest.raises(lbm.LBMError):
+        lat.lbm_restore(np.concatenate([img0, np.zeros(8 * lat.N, dtype=np.uint8)]))
+    lat.close()
+    other.close()
