@@ -367,9 +367,9 @@ __global__ void k_adj_u(Params P, Aux X, AdjAux A, float* Jb) {
       float s = nb_kind(nb, -cx, -cy, -cz) == 0 ? A.Divb[c + nb_off(nb, -cx, -cy, -cz)] : 0.f;
       if (has_extra(em, cx, cy, cz)) s += extra_sources(P, q, cx, cy, cz, ec, [&](int x) { return A.Divb[x]; });
       const float k = 3.f * w19(i) * s;
-      ub[0] += cx * k;
-      ub[1] += cy * k;
-      ub[2] += cz * k;
+      if (cx) ub[0] += cx * k;
+      if (cy) ub[1] += cy * k;
+      if (cz) ub[2] += cz * k;
     }
     const int m = P.any_nonperiodic ? node_faces(P, q[0], q[1], q[2]) : 0;
     float j3[3] = {0.f, 0.f, 0.f};
@@ -406,9 +406,9 @@ __global__ void k_adj_psi(Params P, const float* g, Aux X, AdjAux A, float* Tbar
     for (int i = 1; i < 19; ++i) {
       const int cx = c19x(i), cy = c19y(i), cz = c19z(i);
       const float v = varpi19(i) * ld_aux(X.psi + c + nb_off_psi(nb, cx, cy, cz), h);
-      S[0] += cx * v;
-      S[1] += cy * v;
-      S[2] += cz * v;
+      if (cx) S[0] += cx * v;
+      if (cy) S[1] += cy * v;
+      if (cz) S[2] += cz * v;
     }
     float T = 0.f;
 #pragma unroll
@@ -419,7 +419,14 @@ __global__ void k_adj_psi(Params P, const float* g, Aux X, AdjAux A, float* Tbar
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
       const int cx = c19x(i), cy = c19y(i), cz = c19z(i);
-      auto term = [&](int x) { return X.psi[x] * (cx * A.Fb[x] + cy * A.Fb[N + x] + cz * A.Fb[2 * N + x]); };
+      // only the components the move has are loaded (0 * Fb is not folded away)
+      auto term = [&](int x) {
+        float s = 0.f;
+        if (cx) s += cx * A.Fb[x];
+        if (cy) s += cy * A.Fb[N + x];
+        if (cz) s += cz * A.Fb[2 * N + x];
+        return X.psi[x] * s;
+      };
       float t = nb_kind(nb, -cx, -cy, -cz) == 0 ? term(c + nb_off(nb, -cx, -cy, -cz)) : 0.f;
       if (has_extra(em, cx, cy, cz)) t += extra_sources(P, q, cx, cy, cz, ec, term);
       psib += varpi19(i) * t;
@@ -449,7 +456,13 @@ __global__ void k_adj_fold(Params P, AdjAux A, const float* Jb, const float* Tba
     const float rhob = A.Rb[c], Tb = Tbar[c];
     const float jx = Jb[c], jy = Jb[N + c], jz = Jb[2 * N + c];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) fb0[i * N + c] = fv[i] + rhob + c19x(i) * jx + c19y(i) * jy + c19z(i) * jz;
+    for (int i = 0; i < 19; ++i) {
+      float s = fv[i] + rhob;
+      if (c19x(i)) s += c19x(i) * jx;
+      if (c19y(i)) s += c19y(i) * jy;
+      if (c19z(i)) s += c19z(i) * jz;
+      fb0[i * N + c] = s;
+    }
 #pragma unroll
     for (int i = 0; i < 7; ++i) gb0[i * N + c] = gv[i] + Tb;
   }

@@ -326,16 +326,16 @@ __device__ __forceinline__ void force_at(const Params& P, int c, int x, int y, i
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
       const float v = varpi19(i) * ld_aux(psi + c + nb_off_psi(nb, c19x(i), c19y(i), c19z(i)), h);
-      sx += c19x(i) * v;
-      sy += c19y(i) * v;
-      sz += c19z(i) * v;
+      if (c19x(i)) sx += c19x(i) * v;  // zero components skipped (0 * v is not folded away)
+      if (c19y(i)) sy += c19y(i) * v;
+      if (c19z(i)) sz += c19z(i) * v;
     }
   } else {
     for (int i = 1; i < 19; ++i) {
       const float v = varpi19(i) * psi_ext(P, psi, x + c19x(i), y + c19y(i), z + c19z(i));
-      sx += c19x(i) * v;
-      sy += c19y(i) * v;
-      sz += c19z(i) * v;
+      if (c19x(i)) sx += c19x(i) * v;  // zero components skipped (0 * v is not folded away)
+      if (c19y(i)) sy += c19y(i) * v;
+      if (c19z(i)) sz += c19z(i) * v;
     }
   }
   const float k = -P.G * ld_aux(psi + c, h);
