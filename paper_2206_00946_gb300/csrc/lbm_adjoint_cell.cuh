@@ -171,6 +171,13 @@ LBM_HD void collide19_vjp(const Params& P, const R* f, bool ueq_from_f, const R*
 // The same product for the closed form of the rate-1 case (collide19_fast):
 // f* = f^eq(rho, u') + sum_k A_k col_k, u' = u + F/rho, A_k = (1 - s_k)(m_k - rho e_k(u))
 // for the six second-order moments k = 4..9 and their M-hat^-1 columns col_k.
+// acc += m k for an integer k known at compile time (a velocity component or a
+// product of them): skipped when k = 0, since m * 0 is not folded away.
+template <typename R>
+LBM_HD void add_k(R& acc, R m, int k) {
+  if (k) acc += m * R(k);
+}
+
 template <typename R>
 LBM_HD void collide19_fast_vjp(const Params& P, const R* f, bool ueq_from_f, const R* F, const R* b, R* fb,
                                R* Fb) {
@@ -178,9 +185,9 @@ LBM_HD void collide19_fast_vjp(const Params& P, const R* f, bool ueq_from_f, con
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     rho += f[i];
-    jx += R(c19x(i)) * f[i];
-    jy += R(c19y(i)) * f[i];
-    jz += R(c19z(i)) * f[i];
+    add_k(jx, f[i], c19x(i));
+    add_k(jy, f[i], c19y(i));
+    add_k(jz, f[i], c19z(i));
   }
   const R ir = rcp(rho);
   const R ux = ueq_from_f ? jx * ir : R(0), uy = ueq_from_f ? jy * ir : R(0), uz = ueq_from_f ? jz * ir : R(0);
@@ -190,18 +197,21 @@ LBM_HD void collide19_fast_vjp(const Params& P, const R* f, bool ueq_from_f, con
   R rhob = R(0), swb = R(0), s1x = R(0), s1y = R(0), s1z = R(0), s2x = R(0), s2y = R(0), s2z = R(0);
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
-    const R cx = R(c19x(i)), cy = R(c19y(i)), cz = R(c19z(i));
-    const R cu = cx * vx + cy * vy + cz * vz;
+    const int cx = c19x(i), cy = c19y(i), cz = c19z(i);
+    R cu = R(0);
+    add_k(cu, vx, cx);
+    add_k(cu, vy, cy);
+    add_k(cu, vz, cz);
     const R wi = i == 0 ? R(1) / R(3) : (i < 7 ? R(1) / R(18) : R(1) / R(36));  // as in collide19_fast
     const R wb = wi * b[i];
     rhob += wb * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * vv);
     swb += wb;
-    s1x += wb * cx;
-    s1y += wb * cy;
-    s1z += wb * cz;
-    s2x += wb * cu * cx;
-    s2y += wb * cu * cy;
-    s2z += wb * cu * cz;
+    add_k(s1x, wb, cx);
+    add_k(s1y, wb, cy);
+    add_k(s1z, wb, cz);
+    add_k(s2x, wb * cu, cx);
+    add_k(s2y, wb * cu, cy);
+    add_k(s2z, wb * cu, cz);
   }
   const R vbx = rho * (R(3) * s1x + R(9) * s2x - R(3) * vx * swb);
   const R vby = rho * (R(3) * s1y + R(9) * s2y - R(3) * vy * swb);
@@ -240,10 +250,18 @@ LBM_HD void collide19_fast_vjp(const Params& P, const R* f, bool ueq_from_f, con
   // m_k = rows 4..9 of M-hat applied to f
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
-    const R x = R(c19x(i)), y = R(c19y(i)), z = R(c19z(i));
-    const R xx = x * x, yy = y * y, zz = z * z;
-    fb[i] = rhob + x * jbx + y * jby + z * jbz + m4 * (xx + yy + zz) + m5 * (R(2) * xx - yy - zz) +
-            m6 * (yy - zz) + m7 * x * y + m8 * x * z + m9 * y * z;
+    const int x = c19x(i), y = c19y(i), z = c19z(i);
+    R v = rhob;
+    add_k(v, jbx, x);
+    add_k(v, jby, y);
+    add_k(v, jbz, z);
+    add_k(v, m4, x * x + y * y + z * z);
+    add_k(v, m5, 2 * x * x - y * y - z * z);
+    add_k(v, m6, y * y - z * z);
+    add_k(v, m7, x * y);
+    add_k(v, m8, x * z);
+    add_k(v, m9, y * z);
+    fb[i] = v;
   }
 }
 
