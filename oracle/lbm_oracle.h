@@ -78,7 +78,9 @@ int orc_step(const orc_params* P, const double* const* Tface, const double* f, c
 int orc_run(const orc_params* P, const double* const* Tface, double* f, double* g, int nsteps);
 /* vartheta = 1 (or 0): Th (2N) holds T at t-1 and t-2, and d^2T/dt^2 at t is the backward
  * second difference T(t) - 2 T(t-1) + T(t-2); Th_out (2N) receives T at t and t-1.
- * orc_step and orc_run take vartheta = 0 only. */
+ * orc_step and orc_run take vartheta = 0 only.  The sign, size and leading-order effect of
+ * S_i are pinned; the difference scheme is a reading (the paper names none): parity
+ * unpinned for the scheme itself. */
 int orc_step_hist(const orc_params* P, const double* const* Tface, const double* f, const double* g,
                   const double* Th, double* f_out, double* g_out, double* Th_out);
 int orc_run_hist(const orc_params* P, const double* const* Tface, double* f, double* g, double* Th, int nsteps);
