@@ -199,6 +199,15 @@ int lbm_set_face_T(lbm_ctx* ctx, int face, const float* T_face, int mem);
 /* Advances n >= 0 time steps; asynchronous on the context stream. */
 int lbm_step(lbm_ctx* ctx, int n);
 
+/* Failure detection test support (host-side injection; no GPU fault).  Makes the
+ * next lbm_step of a LBM_SCHED_FUSED context wait on plane-completion counters that
+ * nothing will advance (they are cleared while the step count is kept), so that its
+ * bounded device-side waits give up after about 2 s; the launch then aborts and
+ * lbm_sync returns LBM_ERR_TIMEOUT.  The context stays usable: lbm_set_state or
+ * lbm_restore clears the condition.  LBM_ERR_ARG for other schedules; LBM_ERR_STATE
+ * before the first step. */
+int lbm_inject_stall(lbm_ctx* ctx);
+
 /* Macroscopic fields of the current state: rho = sum f (Eq. 3), the real
  * velocity u = (sum c f + F/2) / rho (Eq. 5; 0 at wall nodes) and T = sum g.
  * Each output N floats (mem) or NULL to skip.  Synchronises the stream. */

@@ -1092,6 +1092,14 @@ int lbm_set_face_T(lbm_ctx* c, int face, const float* T_face, int mem) {
   return st;
 }
 
+int lbm_inject_stall(lbm_ctx* c) {
+  if (!c || c->hp.schedule != LBM_SCHED_FUSED || !c->plan.done_d) return LBM_ERR_ARG;
+  if (c->plan.epoch == 0) return LBM_ERR_STATE;  // the counters are at their start anyway
+  // the next launch waits for (epoch + 1) * tiles completions per plane; from zero it
+  // reaches one step's worth only
+  return cuda_status(cudaMemsetAsync(c->plan.done_d, 0, sizeof(unsigned) * 4 * c->P.nz, c->stream));
+}
+
 int lbm_step(lbm_ctx* c, int n) {
   if (!c || n < 0) return LBM_ERR_ARG;
   if (!c->has_state) return LBM_ERR_STATE;

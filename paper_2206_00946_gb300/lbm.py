@@ -46,7 +46,7 @@ EXPORTS = ["lbm_init", "lbm_set_state", "lbm_get_state", "lbm_set_face_T", "lbm_
            "lbm_maxwell", "lbm_launches_per_step", "lbm_profile", "lbm_profile_read", "lbm_reduce_static",
            "lbm_checkpoint_bytes", "lbm_checkpoint", "lbm_restore", "lbm_record", "lbm_adjoint_step",
            "lbm_adjoint_state", "lbm_batch_create", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_sync",
-           "lbm_batch_cells", "lbm_batch_destroy"]
+           "lbm_batch_cells", "lbm_batch_destroy", "lbm_inject_stall"]
 PROFILE_KINDS = ["phaseA", "phaseB", "phaseC", "phaseD", "fused", "phaseC7"]
 
 _lib = None
@@ -72,6 +72,7 @@ def load(path: str = LIB_PATH):
     L.lbm_get_state.argtypes = [vp, vp, vp, ct.c_int]
     L.lbm_set_face_T.argtypes = [vp, ct.c_int, vp, ct.c_int]
     L.lbm_step.argtypes = [vp, ct.c_int]
+    L.lbm_inject_stall.argtypes = [vp]
     L.lbm_macros.argtypes = [vp, vp, vp, vp, vp, vp, ct.c_int]
     L.lbm_reduce.argtypes = [vp, ct.POINTER(_D)]
     L.lbm_sync.argtypes = [vp]
@@ -246,6 +247,9 @@ class Lattice:
 
     def lbm_sync(self):
         return load().lbm_sync(self._ctx)
+
+    def lbm_inject_stall(self):
+        return load().lbm_inject_stall(self._ctx)
 
     def lbm_stream_map(self, map19=None, map7=None, node_class=None):
         return load().lbm_stream_map(self._ctx, _ptr(map19), _ptr(map7), _ptr(node_class))

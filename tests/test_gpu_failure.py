@@ -1,0 +1,67 @@
+"""Failure detection without a GPU fault.
+
+The persistent schedule's work items wait, with a bound of about 2 s, for the planes they
+read to be finished.  lbm_inject_stall clears the plane-completion counters while keeping
+the step count, so that the next step's waits cannot be satisfied: the waits give up, the
+launch aborts, and the host reads LBM_ERR_TIMEOUT.  The context stays usable.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2206_00946_gb300 import lbm
+from paper_2206_00946_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lbm.load()
+
+
+def _droplet(thermo, schedule):
+    p, rho0, T0 = W.droplet(thermo["Tc"], thermo["rho_v"], thermo["rho_l"], n=16, R=4.0, W=3.0, seed=7)
+    p.update(schedule=schedule)
+    return p, rho0.reshape(-1).astype(np.float32), T0.reshape(-1).astype(np.float32)
+
+
+def test_stalled_wait_times_out_and_the_context_recovers(thermo):
+    p, rho0, T0 = _droplet(thermo, lbm.SCHED_FUSED)
+    lat = lbm.Lattice(p, rho0, T0)
+    assert lat.lbm_inject_stall() == lbm.ERR_STATE  # before the first step
+    lat.lbm_step(2)
+    st, f0, g0 = lat.state()
+    assert st == lbm.OK
+    assert lat.lbm_inject_stall() == lbm.OK
+    t0 = time.perf_counter()
+    lat.lbm_step(1)
+    st = lat.lbm_sync()
+    dt = time.perf_counter() - t0
+    assert st == lbm.ERR_TIMEOUT
+    assert 1.0 < dt < 60.0, dt  # the bound is about 2 s
+    # the context stays usable: a state set again steps exactly like a fresh context
+    lat.lbm_set_state(f0, g0)
+    lat.lbm_step(3)
+    st, f1, g1 = lat.state()
+    assert st == lbm.OK
+    ref = lbm.Lattice(p)
+    ref.lbm_set_state(f0, g0)
+    ref.lbm_step(3)
+    st, f2, g2 = ref.state()
+    assert st == lbm.OK
+    assert np.array_equal(f1, f2) and np.array_equal(g1, g2)
+    lat.close()
+    ref.close()
+
+
+def test_stall_injection_needs_the_persistent_schedule(thermo):
+    p, rho0, T0 = _droplet(thermo, lbm.SCHED_SLABS)
+    lat = lbm.Lattice(p, rho0, T0)
+    lat.lbm_step(1)
+    assert lat.lbm_inject_stall() == lbm.ERR_ARG
+    lat.close()
