@@ -129,23 +129,53 @@ def _ptr(x):
     if isinstance(x, int):
         return x
     if isinstance(x, np.ndarray):
-        assert x.flags["C_CONTIGUOUS"]
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array is not C-contiguous")
         return x.ctypes.data
     if hasattr(x, "data_ptr"):
-        assert x.is_contiguous()
+        if not x.is_contiguous():
+            raise ValueError("tensor is not contiguous")
         return x.data_ptr()
     raise TypeError(type(x))
 
 
+def _is_device(x):
+    return bool(getattr(x, "is_cuda", False))
+
+
 def _mem_of(*xs):
-    for x in xs:
-        if x is None:
-            continue
-        if isinstance(x, np.ndarray):
-            return MEM_HOST
-        if hasattr(x, "is_cuda"):
-            return MEM_DEVICE if x.is_cuda else MEM_HOST
-    return MEM_DEVICE
+    """LBM_MEM_HOST or LBM_MEM_DEVICE for the buffers of one call (all alike)."""
+    kinds = {_is_device(x) for x in xs if x is not None and not isinstance(x, int)}
+    if len(kinds) > 1:
+        raise ValueError("the buffers of one call must be all host or all device memory")
+    return MEM_DEVICE if (not kinds or kinds.pop()) else MEM_HOST
+
+
+_DTYPES = {"f4": (np.float32, "float32"), "f8": (np.float64, "float64"), "i4": (np.int32, "int32"),
+           "u1": (np.uint8, "uint8")}
+
+
+def _arr(x, kind, count, what, device=None):
+    """Checks a buffer before the library reads or writes `count` elements of it: the C ABI
+    takes raw pointers, so a wrong type or a short buffer would be read or written past its
+    end.  device: True / False requires device / host memory; None accepts either."""
+    if x is None:
+        return
+    npdt, tname = _DTYPES[kind]
+    if isinstance(x, np.ndarray):
+        ok, contig, n = x.dtype == npdt, x.flags["C_CONTIGUOUS"], x.size
+    elif hasattr(x, "data_ptr"):
+        ok, contig, n = str(x.dtype) == "torch." + tname, x.is_contiguous(), x.numel()
+    else:
+        raise TypeError(f"{what}: a numpy array or a torch tensor is needed, not {type(x).__name__}")
+    if not ok:
+        raise TypeError(f"{what}: dtype {x.dtype}, {tname} needed")
+    if not contig:
+        raise ValueError(f"{what}: not contiguous")
+    if n < count:
+        raise ValueError(f"{what}: {n} elements, {count} needed")
+    if device is not None and _is_device(x) != device:
+        raise ValueError(f"{what}: {'device' if device else 'host'} memory needed")
 
 
 def _check(st, where):
@@ -171,6 +201,9 @@ def lbm_maxwell(params: dict, T: float):
 def lbm_reduce_static(f, g, n_cells, cv, rho_v, rho_l, out, stream=None):
     """Reductions of caller-owned device populations into a device array of 4 doubles, with no
     device allocation (see include/lbm.h); returns the status code."""
+    _arr(f, "f4", 19 * int(n_cells), "f", device=True)
+    _arr(g, "f4", 7 * int(n_cells), "g", device=True)
+    _arr(out, "f8", 4, "out", device=True)
     return load().lbm_reduce_static(_ptr(f), _ptr(g), int(n_cells), float(cv), float(rho_v), float(rho_l),
                                     _ptr(out), stream)
 
@@ -179,12 +212,14 @@ class Lattice:
     """Owns one lbm_ctx.  Methods mirror the C functions one to one."""
 
     def __init__(self, params: dict, rho0=None, T0=None, stream: int | None = None):
-        L = load()
+        self._ctx = ct.c_void_p()
         self.params = dict(params)
         self._p = make_params(self.params)
         self.N = self._p.nx * self._p.ny * self._p.nz
-        self._ctx = ct.c_void_p()
+        _arr(rho0, "f4", self.N, "rho0")
+        _arr(T0, "f4", self.N, "T0")
         mem = _mem_of(rho0, T0)
+        L = load()
         self._keep = (rho0, T0)
         st = L.lbm_init(ct.byref(self._ctx), ct.byref(self._p), _ptr(rho0), _ptr(T0), mem, stream)
         _check(st, "lbm_init")
@@ -200,10 +235,19 @@ class Lattice:
         except Exception:
             pass
 
+    def _face_len(self, face):
+        n = (self._p.nx, self._p.ny, self._p.nz)
+        a, b = [n[k] for k in range(3) if k != face // 2]
+        return a * b
+
     def lbm_set_state(self, f, g):
+        _arr(f, "f4", 19 * self.N, "f")
+        _arr(g, "f4", 7 * self.N, "g")
         _check(load().lbm_set_state(self._ctx, _ptr(f), _ptr(g), _mem_of(f, g)), "lbm_set_state")
 
     def lbm_get_state(self, f, g):
+        _arr(f, "f4", 19 * self.N, "f")
+        _arr(g, "f4", 7 * self.N, "g")
         st = load().lbm_get_state(self._ctx, _ptr(f), _ptr(g), _mem_of(f, g))
         return st
 
@@ -212,9 +256,11 @@ class Lattice:
 
     def lbm_checkpoint(self, dst):
         """Writes the state image into dst (uint8 numpy array or torch tensor of lbm_checkpoint_bytes())."""
+        _arr(dst, "u1", self.lbm_checkpoint_bytes(), "dst")
         return load().lbm_checkpoint(self._ctx, _ptr(dst), _mem_of(dst))
 
     def lbm_restore(self, src):
+        _arr(src, "u1", self.lbm_checkpoint_bytes(), "src")
         _check(load().lbm_restore(self._ctx, _ptr(src), _mem_of(src)), "lbm_restore")
 
     def lbm_record(self, n, K):
@@ -223,20 +269,32 @@ class Lattice:
 
     def lbm_adjoint_step(self, n, dL_drho=None, dL_dT=None, dL_dTface=None, dL_dT0=None):
         """Adjoint of the n recorded steps; device tensors (float32 seeds, float64 outputs)."""
+        nface = sum(self._face_len(f) for f in range(6) if self._p.face_kind[f] != 0)
+        _arr(dL_drho, "f4", self.N, "dL_drho", device=True)
+        _arr(dL_dT, "f4", self.N, "dL_dT", device=True)
+        _arr(dL_dTface, "f8", nface, "dL_dTface", device=True)
+        _arr(dL_dT0, "f8", self.N, "dL_dT0", device=True)
         _check(load().lbm_adjoint_step(self._ctx, int(n), _ptr(dL_drho), _ptr(dL_dT), _ptr(dL_dTface),
                                        _ptr(dL_dT0)), "lbm_adjoint_step")
 
     def lbm_adjoint_state(self, f_bar, g_bar):
+        _arr(f_bar, "f4", 19 * self.N, "f_bar")
+        _arr(g_bar, "f4", 7 * self.N, "g_bar")
         _check(load().lbm_adjoint_state(self._ctx, _ptr(f_bar), _ptr(g_bar), _mem_of(f_bar, g_bar)),
                "lbm_adjoint_state")
 
     def lbm_set_face_T(self, face, T_face):
+        if not 0 <= int(face) < 6:
+            raise ValueError(f"face {face}: 0..5 needed")
+        _arr(T_face, "f4", self._face_len(int(face)), "T_face")
         _check(load().lbm_set_face_T(self._ctx, int(face), _ptr(T_face), _mem_of(T_face)), "lbm_set_face_T")
 
     def lbm_step(self, n=1):
         _check(load().lbm_step(self._ctx, int(n)), "lbm_step")
 
     def lbm_macros(self, rho=None, ux=None, uy=None, uz=None, T=None):
+        for x, w in ((rho, "rho"), (ux, "ux"), (uy, "uy"), (uz, "uz"), (T, "T")):
+            _arr(x, "f4", self.N, w)
         return load().lbm_macros(self._ctx, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(uz), _ptr(T),
                                  _mem_of(rho, ux, uy, uz, T))
 
@@ -252,6 +310,9 @@ class Lattice:
         return load().lbm_inject_stall(self._ctx)
 
     def lbm_stream_map(self, map19=None, map7=None, node_class=None):
+        _arr(map19, "i4", 19 * self.N, "map19", device=False)
+        _arr(map7, "i4", 7 * self.N, "map7", device=False)
+        _arr(node_class, "u1", self.N, "node_class", device=False)
         return load().lbm_stream_map(self._ctx, _ptr(map19), _ptr(map7), _ptr(node_class))
 
     def lbm_launches_per_step(self):

@@ -51,5 +51,10 @@ def test_static_scratch_rejects_sizes_beyond_its_maximum():
         pytest.skip("no CUDA device")
     dummy = torch.zeros(32, dtype=torch.float32, device="cuda")
     out = torch.zeros(4, dtype=torch.float64, device="cuda")
-    st = lbm.lbm_reduce_static(dummy, dummy, 4096 * 8192 + 1, 5.0, 0.38, 6.5, out, None)
+    # the library's own check, before any device access (a raw call: the binding stops a
+    # buffer shorter than the cell count before calling the library)
+    st = lbm.load().lbm_reduce_static(dummy.data_ptr(), dummy.data_ptr(), 4096 * 8192 + 1, 5.0, 0.38, 6.5,
+                                      out.data_ptr(), None)
     assert st == lbm.ERR_ARG
+    with pytest.raises(ValueError):
+        lbm.lbm_reduce_static(dummy, dummy, 4096 * 8192 + 1, 5.0, 0.38, 6.5, out, None)
