@@ -258,6 +258,30 @@ def test_acentric_factor_recovered_from_vapor_pressure():
     assert abs(omega - 0.344) < 0.02
 
 
+def test_latent_heat_and_wall_temperature_printed_in_sec43():
+    """Sec. 4.3 prints h_lv = 0.5032 at T_s = 0.86 T_c (a = 3/49) and, from Ja = c_v (T_w - T_s) / h_lv
+    = 0.036 with c_v = 5, T_w = 0.8931 T_c.  h_lv is the specific internal-energy difference of the
+    coexisting phases: with e = c_v T + int_0^rho (p - T dp/dT) / r^2 dr the c_v T terms cancel and
+    e_v - e_l = int_{rho_v}^{rho_l} (T dp/dT - p) / r^2 dr.  This checks the EOS, its temperature
+    derivative (through kappa(omega)), the Maxwell densities and T_c against printed numbers."""
+    from scipy.integrate import quad
+
+    gold = json.load(open(os.path.join(GOLD, "paper_values.json")))
+    hs, eos = gold["heated_surface"], gold["pr_eos"]
+    o = _pr(eos["a"])
+    Tc = o.Tc()
+    Ts = 0.86 * Tc
+    rv, rl, _ = o.maxwell(Ts)
+    h_lv, err = quad(lambda r: (Ts * o.dpdT(r, Ts) - o.p_eos(r, Ts)) / r**2, rv, rl, limit=200, epsabs=1e-13)
+    assert err < 1e-10
+    assert abs(h_lv - hs["h_lv"]) < 5e-5  # printed to four decimals
+    # the enthalpy difference (Clausius-Clapeyron) is a different number: the printed value is not it
+    _, _, p_sat = o.maxwell(Ts)
+    assert abs(h_lv + p_sat * (1 / rv - 1 / rl) - hs["h_lv"]) > 0.05
+    Tw = Ts + hs["Ja"] * h_lv / hs["cv"]
+    assert abs(Tw / Tc - hs["Tw_over_Tc"]) < 5e-5
+
+
 # -------------------------------------------------------------- Zou-He -----
 
 def test_zouhe_top_face_matches_printed_formulas():
