@@ -9,7 +9,7 @@ job, and the fraction of the measured HBM copy bandwidth that the 208 bytes of
 algorithmic traffic per lattice update reach.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--storage f32|f16|bf16] [--schedule slabs|phases|fused]
+                    [--storage f32|f16|bf16|f16local] [--schedule slabs|phases|fused]
 
 The JSON line also carries the roofline of the dominant kernel (each kernel timed
 alone with CUDA events in the phase schedule, charged its own algorithmic bytes),
@@ -47,7 +47,7 @@ from paper_2206_00946_gb300 import workloads as W  # noqa: E402
 METRIC = "fused D3Q19+D3Q7 MLUPS"
 UNIT = "MLUPS"
 BYTES_PER_LU = 208  # f and g (19 + 7 FP32 populations) read once and written once per lattice update
-STORAGE = {"f32": (0, 4), "f16": (1, 2), "bf16": (2, 2)}  # lbm_storage code, bytes per stored population
+STORAGE = {"f32": (0, 4), "f16": (1, 2), "bf16": (2, 2), "f16local": (3, 2)}  # lbm_storage code, bytes per population
 
 
 def kernel_alg_bytes(kernel: str, esize: int):
@@ -523,7 +523,8 @@ def main():
         "config": {"workload": WORKLOAD if args.n == 128 else WORKLOAD.replace("128^3", f"{args.n}^3"),
                    "cells": N, "schedule": args.schedule, "parallelism": f"replicas x{world}",
                    "storage": {"f32": "f32", "f16": "f16 shifted by w_i rho_ref / w_i T_ref",
-                               "bf16": "bf16 shifted by w_i rho_ref / w_i T_ref"}[args.storage],
+                               "bf16": "bf16 shifted by w_i rho_ref / w_i T_ref",
+                               "f16local": "f16 shifted by w_i rho / w_i T of the cell before the step"}[args.storage],
                    "l2": f"inputs larger than L2: {2 * 26 * esize * N / 1e6:.0f} MB of double-buffered populations"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None, "traffic": traffic,

@@ -66,7 +66,14 @@ typedef enum {
 } lbm_status;
 
 typedef enum { LBM_FACE_PERIODIC = 0, LBM_FACE_WALL = 1, LBM_FACE_OPEN = 2 } lbm_face_kind;
-typedef enum { LBM_STORE_F32 = 0, LBM_STORE_F16_SHIFTED = 1, LBM_STORE_BF16_SHIFTED = 2 } lbm_storage;
+typedef enum {
+  LBM_STORE_F32 = 0,
+  LBM_STORE_F16_SHIFTED = 1,  /* IEEE half of f_i - w_i rho_ref, g_i - w_i T_ref (one global shift) */
+  LBM_STORE_BF16_SHIFTED = 2, /* bfloat16, the same shift */
+  LBM_STORE_F16_LOCAL = 3     /* IEEE half with per-cell references: rho_ref and T_ref of a stored
+                                 population are the density and temperature its cell had before the
+                                 step that wrote it (8 bytes per cell, twice, kept by the library) */
+} lbm_storage;
 typedef enum { LBM_MEM_DEVICE = 0, LBM_MEM_HOST = 1 } lbm_mem;
 typedef enum { LBM_SCHED_FUSED = 0, LBM_SCHED_PHASES = 1, LBM_SCHED_SLABS = 2 } lbm_schedule;
 
@@ -100,8 +107,8 @@ typedef struct lbm_params {
   int storage;                   /* lbm_storage: FP32 populations, or 16-bit IEEE half / bfloat16
                                     holding f_i - w_i rho_ref and g_i - w_i T_ref (all arithmetic in FP32;
                                     the FUSED schedule supports FP32 only) */
-  double store_rho_ref;          /* shift rho_ref of the 16-bit storage (e.g. rho_v) */
-  double store_T_ref;            /* shift T_ref of the 16-bit storage (e.g. the mean temperature) */
+  double store_rho_ref;          /* global shift rho_ref of the 16-bit storage (e.g. rho_v) */
+  double store_T_ref;            /* global shift T_ref of the 16-bit storage (e.g. the mean temperature) */
   int schedule;                  /* lbm_schedule: one persistent launch per step (FUSED), one launch
                                     per phase (PHASES), or per phase and z-slab on several streams,
                                     replayed from a CUDA graph (SLABS) */
@@ -122,7 +129,8 @@ int lbm_get_state(lbm_ctx* ctx, float* f, float* g, int mem);
 /* Checkpoint / restore of the time-stepping state (the populations in the
  * context's storage format), e.g. for recomputation between checkpoints.
  * The image is a 256-byte header (magic, lattice size, storage mode and
- * shifts) followed by f and g; lbm_checkpoint_bytes gives its size.
+ * shifts) followed by f and g (then the T history for vartheta = 1 and the
+ * per-cell references of LBM_STORE_F16_LOCAL); lbm_checkpoint_bytes gives its size.
  * lbm_checkpoint writes the image to dst (mem), synchronises the stream and
  * returns the error flags like lbm_get_state.  lbm_restore reads an image
  * written by a context with the same lattice size, storage mode and shifts

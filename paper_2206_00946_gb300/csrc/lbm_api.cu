@@ -26,37 +26,58 @@ constexpr int kBulkSmem = 2 * 26 * kBulkTile * 4 + 2 * 8;           // two stage
 #define LBM_PHASEC_MINBLOCKS 4
 #endif
 
+// ref: the per-cell references of buffer 0 (storage with per-cell references only):
+// the initial rho0 and T0 themselves
 template <typename T>
-__global__ void k_init(Params P, const float* __restrict__ rho0, const float* __restrict__ T0, T* f, T* g) {
+__global__ void k_init(Params P, const float* __restrict__ rho0, const float* __restrict__ T0, T* f, T* g,
+                       float2* ref) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x) {
     float fe[19];
-    feq19(rho0[c], 0.f, 0.f, 0.f, fe);
+    const float r = rho0[c], Tc = T0[c];
+    if (LocalRef<T>::on) ref[c] = make_float2(r, Tc);
+    feq19(r, 0.f, 0.f, 0.f, fe);
 #pragma unroll
-    for (int i = 0; i < 19; ++i) PopStore<T>::st(f + i * P.N + c, fe[i], fbase(P, i));
-    const float Tc = T0[c];
-    PopStore<T>::st(g + c, (1.f - P.wbar) * Tc, gbase(P, 0));
+    for (int i = 0; i < 19; ++i) PopStore<T>::st(f + i * P.N + c, fe[i], fbase_at<T>(P, i, r));
+    PopStore<T>::st(g + c, (1.f - P.wbar) * Tc, gbase_at<T>(P, 0, Tc));
 #pragma unroll
-    for (int i = 1; i < 7; ++i) PopStore<T>::st(g + i * P.N + c, P.wbar * (1.f / 6.f) * Tc, gbase(P, i));
+    for (int i = 1; i < 7; ++i) PopStore<T>::st(g + i * P.N + c, P.wbar * (1.f / 6.f) * Tc, gbase_at<T>(P, i, Tc));
+  }
+}
+
+// per-cell references of a state given in FP32: component `comp` (0: rho = sum f,
+// 1: T = sum g) of ref[c] from the q populations in src
+__global__ void k_ref_sum(Params P, const float* __restrict__ src, int q, float2* ref, int comp) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int i = 0; i < q; ++i) s += src[i * P.N + c];
+    if (comp == 0)
+      ref[c].x = s;
+    else
+      ref[c].y = s;
   }
 }
 
 // float populations (state exchanged with the caller) <-> storage, q directions
+// (ref: the per-cell references of the buffer, storage with per-cell references only)
 template <typename T>
-__global__ void k_store(Params P, const float* __restrict__ src, T* dst, int q, int is_g) {
-  const long long n = (long long)q * P.N;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(k / P.N);
-    PopStore<T>::st(dst + k, src[k], is_g ? gbase(P, i) : fbase(P, i));
-  }
+__device__ __forceinline__ float state_base(const Params& P, const float2* ref, long long k, int is_g) {
+  const int i = (int)(k / P.N);
+  const float2 r = LocalRef<T>::on ? ref[k - (long long)i * P.N] : make_float2(0.f, 0.f);
+  return is_g ? gbase_at<T>(P, i, r.y) : fbase_at<T>(P, i, r.x);
 }
 
 template <typename T>
-__global__ void k_load(Params P, const T* __restrict__ src, float* dst, int q, int is_g) {
+__global__ void k_store(Params P, const float* __restrict__ src, T* dst, int q, int is_g, const float2* ref) {
   const long long n = (long long)q * P.N;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(k / P.N);
-    dst[k] = PopStore<T>::ld_plain(src + k, is_g ? gbase(P, i) : fbase(P, i));
-  }
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    PopStore<T>::st(dst + k, src[k], state_base<T>(P, ref, k, is_g));
+}
+
+template <typename T>
+__global__ void k_load(Params P, const T* __restrict__ src, float* dst, int q, int is_g, const float2* ref) {
+  const long long n = (long long)q * P.N;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    dst[k] = PopStore<T>::ld_plain(src + k, state_base<T>(P, ref, k, is_g));
 }
 
 // Phase kernels over the cell range [c0, c1) (whole planes) with grid-stride loops.
@@ -97,11 +118,11 @@ __global__ void __launch_bounds__(256, 4) k_phaseC7(Params P, const T* __restric
 }
 
 template <typename T>
-void launch_c7(const lbm_ctx* c, int blocks, cudaStream_t st, const T* gA, T* gB, int c0, int c1) {
+void launch_c7(const lbm_ctx* c, const Aux& X, int blocks, cudaStream_t st, const T* gA, T* gB, int c0, int c1) {
   if (c->P.vartheta)
-    k_phaseC7<T, 1><<<blocks, kThreads, 0, st>>>(c->P, gA, gB, c->X, c0, c1);
+    k_phaseC7<T, 1><<<blocks, kThreads, 0, st>>>(c->P, gA, gB, X, c0, c1);
   else
-    k_phaseC7<T, 0><<<blocks, kThreads, 0, st>>>(c->P, gA, gB, c->X, c0, c1);
+    k_phaseC7<T, 0><<<blocks, kThreads, 0, st>>>(c->P, gA, gB, X, c0, c1);
 }
 
 // one thread per boundary candidate (boundary_candidate enumerates them)
@@ -130,14 +151,16 @@ __global__ void __launch_bounds__(256, 3) k_phaseD_planes(Params P, T* fB, T* gB
 
 // FP64 block reduction: mass, sum rho cv T, droplet volume, non-finite count.
 template <typename S>
-__global__ void k_reduce(Params P, const S* __restrict__ f, const S* __restrict__ g, double* partial) {
+__global__ void k_reduce(Params P, const S* __restrict__ f, const S* __restrict__ g, double* partial,
+                         const float2* ref) {
   double a[4] = {0, 0, 0, 0};
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x) {
+    const float2 r = LocalRef<S>::on ? ref[c] : make_float2(0.f, 0.f);
     float fl[19], gl[7];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) fl[i] = PopStore<S>::ld_plain(f + i * P.N + c, fbase(P, i));
+    for (int i = 0; i < 19; ++i) fl[i] = PopStore<S>::ld_plain(f + i * P.N + c, fbase_at<S>(P, i, r.x));
 #pragma unroll
-    for (int i = 0; i < 7; ++i) gl[i] = PopStore<S>::ld_plain(g + i * P.N + c, gbase(P, i));
+    for (int i = 0; i < 7; ++i) gl[i] = PopStore<S>::ld_plain(g + i * P.N + c, gbase_at<S>(P, i, r.y));
     float rho, jx, jy, jz;
     sum19(fl, rho, jx, jy, jz);
     const float T = sum7(gl);
@@ -201,11 +224,12 @@ __global__ void k_fill(float* p, long long n, float v) {
 }
 
 template <typename S>
-__global__ void k_sumT(Params P, const S* __restrict__ g, float* T) {
+__global__ void k_sumT(Params P, const S* __restrict__ g, float* T, const float2* ref) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)P.N; c += gridDim.x * blockDim.x) {
+    const float t = LocalRef<S>::on ? ref[c].y : 0.f;
     float gl[7];
 #pragma unroll
-    for (int i = 0; i < 7; ++i) gl[i] = PopStore<S>::ld_plain(g + i * P.N + c, gbase(P, i));
+    for (int i = 0; i < 7; ++i) gl[i] = PopStore<S>::ld_plain(g + i * P.N + c, gbase_at<S>(P, i, t));
     T[c] = sum7(gl);
   }
 }
@@ -229,7 +253,8 @@ int check_params(const lbm_params* p) {
   const long long N = (long long)p->nx * p->ny * p->nz;
   if (N > (1LL << 31) - 1) return LBM_ERR_ARG;
   if (p->vartheta != 0 && p->vartheta != 1) return LBM_ERR_ARG;
-  if (p->storage != LBM_STORE_F32 && p->storage != LBM_STORE_F16_SHIFTED && p->storage != LBM_STORE_BF16_SHIFTED)
+  if (p->storage != LBM_STORE_F32 && p->storage != LBM_STORE_F16_SHIFTED && p->storage != LBM_STORE_BF16_SHIFTED &&
+      p->storage != LBM_STORE_F16_LOCAL)
     return LBM_ERR_ARG;
   if (p->storage != LBM_STORE_F32 && p->schedule == LBM_SCHED_FUSED) return LBM_ERR_ARG;  // FP32 only
   if (p->schedule != LBM_SCHED_FUSED && p->schedule != LBM_SCHED_PHASES && p->schedule != LBM_SCHED_SLABS)
@@ -418,13 +443,26 @@ T* gbuf(lbm_ctx* c, int k) {
 #define LBM_WITH_STORAGE(c, FN, ...)                                                             \
   ((c)->hp.storage == LBM_STORE_F16_SHIFTED    ? FN<__half>(__VA_ARGS__)                          \
    : (c)->hp.storage == LBM_STORE_BF16_SHIFTED ? FN<__nv_bfloat16>(__VA_ARGS__)                   \
+   : (c)->hp.storage == LBM_STORE_F16_LOCAL    ? FN<lhalf>(__VA_ARGS__)                           \
                                                : FN<float>(__VA_ARGS__))
 
+// per-cell references of population buffer k (NULL without them)
+float2* ref_of(const lbm_ctx* c, int k) { return c->ref ? c->ref + (long long)k * c->N : nullptr; }
+
+// the scratch of a step that reads buffer a and writes buffer 1 - a
+Aux aux_for(const lbm_ctx* c, int a) {
+  Aux X = c->X;
+  X.ref_in = ref_of(c, a);
+  X.ref_out = ref_of(c, 1 - a);
+  return X;
+}
+
 // Phases A and B on the current state (macros of time t); returns launch status.
+// (with per-cell references phase A also writes those of the idle buffer: harmless)
 template <typename T>
 int run_macros_t(lbm_ctx* c, float* Tout) {
-  k_phaseA<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, c->cur), gbuf<T>(c, c->cur), c->X, Tout,
-                                                   c->err_d, 0, (int)c->N, 1);
+  k_phaseA<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, c->cur), gbuf<T>(c, c->cur), aux_for(c, c->cur),
+                                                   Tout, c->err_d, 0, (int)c->N, 1);
   k_phaseB<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->X, 0, (int)c->N);
   return cuda_status(cudaGetLastError());
 }
@@ -436,9 +474,10 @@ int run_macros(lbm_ctx* c, float* Tout) { return LBM_WITH_STORAGE(c, run_macros_
 template <typename T>
 int step_phases_t(lbm_ctx* c) {
   const int a = c->cur, b = 1 - c->cur;
+  const Aux X = aux_for(c, a);
   cudaEvent_t e = prof_begin(c);
   // j is stored only for the staged path, whose separate phase B reads it
-  k_phaseA<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, a), gbuf<T>(c, a), c->X, nullptr, c->err_d, 0,
+  k_phaseA<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, a), gbuf<T>(c, a), X, nullptr, c->err_d, 0,
                                                    (int)c->N, c->bulk_grid > 0 ? 1 : 0);
   prof_end(c, 0, e);
   if (c->bulk_grid > 0) {  // FP32 storage only: staged C19 + C7 after a separate phase B
@@ -451,16 +490,16 @@ int step_phases_t(lbm_ctx* c) {
     prof_end(c, 2, e);
   } else {
     e = prof_begin(c);
-    k_phaseBC19<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, a), fbuf<T>(c, b), c->X, 0, (int)c->N);
+    k_phaseBC19<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, a), fbuf<T>(c, b), X, 0, (int)c->N);
     prof_end(c, 2, e);
     // the D3Q7 phase needs the velocity of the neighbours: after the whole D3Q19 pass
     e = prof_begin(c);
-    launch_c7<T>(c, c->grid, c->stream, gbuf<T>(c, a), gbuf<T>(c, b), 0, (int)c->N);
+    launch_c7<T>(c, X, c->grid, c->stream, gbuf<T>(c, a), gbuf<T>(c, b), 0, (int)c->N);
     prof_end(c, 5, e);
   }
   if (c->P.bd_total > 0) {
     e = prof_begin(c);
-    k_phaseD<T><<<grid_for(c->P.bd_total), kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, b), gbuf<T>(c, b), c->X);
+    k_phaseD<T><<<grid_for(c->P.bd_total), kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, b), gbuf<T>(c, b), X);
     prof_end(c, 3, e);
   }
   c->cur = b;
@@ -612,6 +651,7 @@ template <typename T>
 int slab_enqueue_step_t(lbm_ctx* c, bool first) {
   SlabPlan& S = *c->slabs;
   const int a = c->cur, b = 1 - c->cur;
+  const Aux X = aux_for(c, a);
   const bool zper = c->P.face_kind[4] == FACE_PERIODIC;
   const int n = S.nslab, plane = c->P.nx * c->P.ny;
   std::vector<int> d;
@@ -630,14 +670,13 @@ int slab_enqueue_step_t(lbm_ctx* c, bool first) {
     const int blocks = std::min(grid_for((long long)(c1 - c0)), 152 * 8);
     switch (ph) {
       case SPH_A:
-        k_phaseA<T><<<blocks, kThreads, 0, st>>>(c->P, fbuf<T>(c, a), gbuf<T>(c, a), c->X, nullptr, c->err_d, c0, c1,
-                                                 0);
+        k_phaseA<T><<<blocks, kThreads, 0, st>>>(c->P, fbuf<T>(c, a), gbuf<T>(c, a), X, nullptr, c->err_d, c0, c1, 0);
         break;
       case SPH_C19:
-        k_phaseBC19<T><<<blocks, kThreads, 0, st>>>(c->P, fbuf<T>(c, a), fbuf<T>(c, b), c->X, c0, c1);
+        k_phaseBC19<T><<<blocks, kThreads, 0, st>>>(c->P, fbuf<T>(c, a), fbuf<T>(c, b), X, c0, c1);
         break;
       case SPH_C7:
-        launch_c7<T>(c, blocks, st, gbuf<T>(c, a), gbuf<T>(c, b), c0, c1);
+        launch_c7<T>(c, X, blocks, st, gbuf<T>(c, a), gbuf<T>(c, b), c0, c1);
         break;
       default: {
         int maxcnt = 0;
@@ -646,7 +685,7 @@ int slab_enqueue_step_t(lbm_ctx* c, bool first) {
           maxcnt = std::max(maxcnt, zb ? plane : c->P.bd_perim);
         }
         dim3 gd((unsigned)std::max(1, (maxcnt + kThreads - 1) / kThreads), (unsigned)(z1 - z0));
-        k_phaseD_planes<T><<<gd, kThreads, 0, st>>>(c->P, fbuf<T>(c, b), gbuf<T>(c, b), c->X, z0);
+        k_phaseD_planes<T><<<gd, kThreads, 0, st>>>(c->P, fbuf<T>(c, b), gbuf<T>(c, b), X, z0);
       }
     }
     cudaEventRecord(S.ev[code], st);
@@ -738,13 +777,16 @@ int convert_state_t(lbm_ctx* c, float* f, float* g, int mem, bool in) {
   float* user[2] = {f, g};
   const int q[2] = {19, 7};
   void* buf[2] = {c->f[c->cur], c->g[c->cur]};
+  float2* ref = ref_of(c, c->cur);
   for (int k = 0; k < 2 && st == LBM_OK; ++k) {
     if (!user[k]) continue;
     if (in) {
       st = copy_in(tmp, user[k], q[k] * N, mem, c->stream);
-      if (!st) k_store<T><<<blocks, kThreads, 0, c->stream>>>(c->P, tmp, static_cast<T*>(buf[k]), q[k], k);
+      // per-cell references of the state set: its own rho and T
+      if (!st && ref) k_ref_sum<<<c->grid, kThreads, 0, c->stream>>>(c->P, tmp, q[k], ref, k);
+      if (!st) k_store<T><<<blocks, kThreads, 0, c->stream>>>(c->P, tmp, static_cast<T*>(buf[k]), q[k], k, ref);
     } else {
-      k_load<T><<<blocks, kThreads, 0, c->stream>>>(c->P, static_cast<const T*>(buf[k]), tmp, q[k], k);
+      k_load<T><<<blocks, kThreads, 0, c->stream>>>(c->P, static_cast<const T*>(buf[k]), tmp, q[k], k, ref);
       st = copy_out(user[k], tmp, q[k] * N, mem, c->stream);
     }
     if (!st) st = cuda_status(cudaStreamSynchronize(c->stream));
@@ -765,12 +807,27 @@ namespace {
 // T(t-1) = T(t-2) = T = sum g of the current populations.
 template <typename T>
 int hist_reset_t(lbm_ctx* c) {
-  k_sumT<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, gbuf<T>(c, c->cur), c->X.T1);
+  k_sumT<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, gbuf<T>(c, c->cur), c->X.T1, ref_of(c, c->cur));
   if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
   return cuda_status(cudaMemcpyAsync(c->X.T2, c->X.T1, sizeof(float) * c->N, cudaMemcpyDeviceToDevice, c->stream));
 }
 
 int hist_reset(lbm_ctx* c) { return c->hist ? LBM_WITH_STORAGE(c, hist_reset_t, c) : LBM_OK; }
+
+// T = sum g of the current state into T (lbm_macros)
+template <typename S>
+int launch_sumT(lbm_ctx* c, float* T) {
+  k_sumT<S><<<c->grid, kThreads, 0, c->stream>>>(c->P, gbuf<S>(c, c->cur), T, ref_of(c, c->cur));
+  return LBM_OK;
+}
+
+// per-block FP64 partial sums of the current state (lbm_reduce)
+template <typename S>
+int launch_reduce(lbm_ctx* c) {
+  k_reduce<S><<<c->red_blocks, kThreads, 0, c->stream>>>(c->P, fbuf<S>(c, c->cur), gbuf<S>(c, c->cur), c->partial,
+                                                         ref_of(c, c->cur));
+  return LBM_OK;
+}
 
 }  // namespace
 
@@ -884,6 +941,7 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
   }
   ok = ok && cudaMalloc(&c->aux, sizeof(float) * 11 * N) == cudaSuccess;
   if (p->vartheta) ok = ok && cudaMalloc(&c->hist, sizeof(float) * 2 * N) == cudaSuccess;
+  if (p->storage == LBM_STORE_F16_LOCAL) ok = ok && cudaMalloc(&c->ref, sizeof(float2) * 2 * N) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
@@ -955,12 +1013,15 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
       t = (float*)T0;
     }
     if (p->storage == LBM_STORE_F16_SHIFTED)
-      k_init<__half><<<c->grid, kThreads, 0, c->stream>>>(c->P, r, t, fbuf<__half>(c, 0), gbuf<__half>(c, 0));
+      k_init<__half><<<c->grid, kThreads, 0, c->stream>>>(c->P, r, t, fbuf<__half>(c, 0), gbuf<__half>(c, 0), nullptr);
     else if (p->storage == LBM_STORE_BF16_SHIFTED)
       k_init<__nv_bfloat16><<<c->grid, kThreads, 0, c->stream>>>(c->P, r, t, fbuf<__nv_bfloat16>(c, 0),
-                                                                 gbuf<__nv_bfloat16>(c, 0));
+                                                                 gbuf<__nv_bfloat16>(c, 0), nullptr);
+    else if (p->storage == LBM_STORE_F16_LOCAL)
+      k_init<lhalf><<<c->grid, kThreads, 0, c->stream>>>(c->P, r, t, fbuf<lhalf>(c, 0), gbuf<lhalf>(c, 0),
+                                                         ref_of(c, 0));
     else
-      k_init<float><<<c->grid, kThreads, 0, c->stream>>>(c->P, r, t, fbuf<float>(c, 0), gbuf<float>(c, 0));
+      k_init<float><<<c->grid, kThreads, 0, c->stream>>>(c->P, r, t, fbuf<float>(c, 0), gbuf<float>(c, 0), nullptr);
     if (cudaGetLastError() != cudaSuccess || hist_reset(c) != LBM_OK) {
       lbm_destroy(c);
       return LBM_ERR_CUDA;
@@ -1005,7 +1066,8 @@ int lbm_get_state(lbm_ctx* c, float* f, float* g, int mem) {
 namespace {
 
 // Checkpoint image: this header, then f (19 N) and g (7 N) in the storage format,
-// then, for vartheta = 1, the T history (2 N floats).
+// then, for vartheta = 1, the T history (2 N floats), then, for FP16 storage with
+// per-cell references, those of the stored populations (2 N floats: rho, T per cell).
 struct CkptHeader {
   char magic[8];
   int32_t version, nx, ny, nz, storage, esize;
@@ -1036,7 +1098,7 @@ CkptHeader ckpt_header(const lbm_ctx* c) {
 long long lbm_checkpoint_bytes(const lbm_ctx* c) {
   if (!c) return 0;
   return (long long)sizeof(CkptHeader) + 26LL * c->N * (long long)c->esize +
-         (c->hist ? 2LL * c->N * (long long)sizeof(float) : 0LL);
+         (c->hist ? 2LL * c->N * (long long)sizeof(float) : 0LL) + (c->ref ? c->N * (long long)sizeof(float2) : 0LL);
 }
 
 int lbm_checkpoint(lbm_ctx* c, void* dst, int mem) {
@@ -1048,7 +1110,10 @@ int lbm_checkpoint(lbm_ctx* c, void* dst, int mem) {
   const size_t fb = 19ull * c->N * c->esize, gb = 7ull * c->N * c->esize;
   LBM_TRY(cudaMemcpyAsync(d + sizeof(h), c->f[c->cur], fb, kd, c->stream));
   LBM_TRY(cudaMemcpyAsync(d + sizeof(h) + fb, c->g[c->cur], gb, kd, c->stream));
-  if (c->hist) LBM_TRY(cudaMemcpyAsync(d + sizeof(h) + fb + gb, c->hist, 2ull * c->N * sizeof(float), kd, c->stream));
+  const size_t hb = c->hist ? 2ull * c->N * sizeof(float) : 0;
+  if (c->hist) LBM_TRY(cudaMemcpyAsync(d + sizeof(h) + fb + gb, c->hist, hb, kd, c->stream));
+  if (c->ref)
+    LBM_TRY(cudaMemcpyAsync(d + sizeof(h) + fb + gb + hb, ref_of(c, c->cur), c->N * sizeof(float2), kd, c->stream));
   if (mem == LBM_MEM_HOST) {
     std::memcpy(d, &h, sizeof(h));
   } else {
@@ -1076,7 +1141,10 @@ int lbm_restore(lbm_ctx* c, const void* src, int mem) {
   const size_t fb = 19ull * c->N * c->esize, gb = 7ull * c->N * c->esize;
   LBM_TRY(cudaMemcpyAsync(c->f[c->cur], s + sizeof(h), fb, kd, c->stream));
   LBM_TRY(cudaMemcpyAsync(c->g[c->cur], s + sizeof(h) + fb, gb, kd, c->stream));
-  if (c->hist) LBM_TRY(cudaMemcpyAsync(c->hist, s + sizeof(h) + fb + gb, 2ull * c->N * sizeof(float), kd, c->stream));
+  const size_t hb = c->hist ? 2ull * c->N * sizeof(float) : 0;
+  if (c->hist) LBM_TRY(cudaMemcpyAsync(c->hist, s + sizeof(h) + fb + gb, hb, kd, c->stream));
+  if (c->ref)
+    LBM_TRY(cudaMemcpyAsync(ref_of(c, c->cur), s + sizeof(h) + fb + gb + hb, c->N * sizeof(float2), kd, c->stream));
   if (mem == LBM_MEM_HOST) LBM_TRY(cudaStreamSynchronize(c->stream));
   if (fused_reset(&c->plan, c->P, c->stream)) return LBM_ERR_CUDA;
   LBM_TRY(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream));
@@ -1154,12 +1222,7 @@ int lbm_macros(lbm_ctx* c, float* rho, float* ux, float* uy, float* uz, float* T
   // T is summed into the ux slot of the scratch first when requested, then copied
   float* Tscratch = c->aux + 5 * c->N;  // Fx slot, rewritten by phase B below
   if (T) {
-    if (c->hp.storage == LBM_STORE_F16_SHIFTED)
-      k_sumT<__half><<<c->grid, kThreads, 0, c->stream>>>(c->P, gbuf<__half>(c, c->cur), Tscratch);
-    else if (c->hp.storage == LBM_STORE_BF16_SHIFTED)
-      k_sumT<__nv_bfloat16><<<c->grid, kThreads, 0, c->stream>>>(c->P, gbuf<__nv_bfloat16>(c, c->cur), Tscratch);
-    else
-      k_sumT<float><<<c->grid, kThreads, 0, c->stream>>>(c->P, gbuf<float>(c, c->cur), Tscratch);
+    LBM_WITH_STORAGE(c, launch_sumT, c, Tscratch);
     int st = copy_out(T, Tscratch, c->N, mem, c->stream);
     if (st) return st;
   }
@@ -1176,15 +1239,7 @@ int lbm_macros(lbm_ctx* c, float* rho, float* ux, float* uy, float* uz, float* T
 int lbm_reduce(lbm_ctx* c, double out[4]) {
   if (!c || !out) return LBM_ERR_ARG;
   if (!c->has_state) return LBM_ERR_STATE;
-  if (c->hp.storage == LBM_STORE_F16_SHIFTED)
-    k_reduce<__half><<<c->red_blocks, kThreads, 0, c->stream>>>(c->P, fbuf<__half>(c, c->cur), gbuf<__half>(c, c->cur),
-                                                                c->partial);
-  else if (c->hp.storage == LBM_STORE_BF16_SHIFTED)
-    k_reduce<__nv_bfloat16><<<c->red_blocks, kThreads, 0, c->stream>>>(
-        c->P, fbuf<__nv_bfloat16>(c, c->cur), gbuf<__nv_bfloat16>(c, c->cur), c->partial);
-  else
-    k_reduce<float><<<c->red_blocks, kThreads, 0, c->stream>>>(c->P, fbuf<float>(c, c->cur), gbuf<float>(c, c->cur),
-                                                               c->partial);
+  LBM_WITH_STORAGE(c, launch_reduce, c);
   k_reduce_final<<<1, 32, 0, c->stream>>>(c->partial, c->red_blocks, c->red_out);
   LBM_TRY(cudaGetLastError());
   LBM_TRY(cudaMemcpyAsync(c->red_h, c->red_out, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream));
@@ -1244,6 +1299,7 @@ void lbm_destroy(lbm_ctx* c) {
   }
   cudaFree(c->aux);
   cudaFree(c->hist);
+  cudaFree(c->ref);
   if (c->side) cudaStreamSynchronize(c->side);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);

@@ -57,6 +57,7 @@ struct lbm_ctx {
   int cur;
   float* aux;
   float* hist;  // vartheta = 1: T at the two previous steps (2N floats, X.T1 and X.T2)
+  float2* ref;  // FP16 storage with per-cell references: those of population buffer k at ref + k N
   Aux X;
   float* tface[6];
   long long tface_n[6];

@@ -24,6 +24,10 @@ struct Aux {
   float *Fx, *Fy, *Fz, *ux, *uy, *uz;  // phase B
   float *gstar, *divu;  // optional (NULL): the D3Q7 phase also stores g* (7N) and div u
   float *T1, *T2;       // vartheta = 1: T at the two previous steps, kept by the D3Q7 phase
+  // FP16 storage with per-cell references: (rho_ref, T_ref) of every cell for the
+  // populations read this step (ref_in) and for those written (ref_out); NULL otherwise
+  const float2* ref_in;
+  float2* ref_out;
 };
 
 // L2 residency: population loads stream through once per kernel (evict-first),
@@ -71,7 +75,25 @@ __device__ __forceinline__ void st_aux(float* a, float v, const Hint& h) {
 
 // Population storage.  FP32 stores f_i itself; the shifted 16-bit forms store
 // f_i - w_i rho_ref and g_i - w_i T_ref in IEEE half or bfloat16, and every
-// arithmetic operation stays in FP32: decode = base + (float)stored.
+// arithmetic operation stays in FP32: decode = base + (float)stored.  With one
+// global shift (__half, __nv_bfloat16) rho_ref and T_ref are parameters; with
+// per-cell references (lhalf) they are the density and temperature that the
+// destination cell had before the step that wrote the population: the pushes
+// know them (phase A has stored them), and a later load reads the cell's own.
+struct lhalf {
+  __half v;
+};
+static_assert(sizeof(lhalf) == 2, "lhalf is stored as one IEEE half");
+
+template <typename ST>
+struct LocalRef {
+  static constexpr bool on = false;
+};
+template <>
+struct LocalRef<lhalf> {
+  static constexpr bool on = true;
+};
+
 template <typename ST>
 struct PopStore;
 
@@ -103,6 +125,18 @@ struct PopStore<__half> {
 };
 
 template <>
+struct PopStore<lhalf> {
+  __device__ __forceinline__ static float ld(const lhalf* a, float base, const Hint& h) {
+    return base + __half2float(__ushort_as_half(ld_u16_stream(a, h)));
+  }
+  __device__ __forceinline__ static float ld_plain(const lhalf* a, float base) { return base + __half2float(a->v); }
+  __device__ __forceinline__ static void st(lhalf* a, float v, float base) { a->v = __float2half_rn(v - base); }
+  __device__ __forceinline__ static float round(float v, float base) {
+    return base + __half2float(__float2half_rn(v - base));
+  }
+};
+
+template <>
 struct PopStore<__nv_bfloat16> {
   __device__ __forceinline__ static float ld(const __nv_bfloat16* a, float base, const Hint& h) {
     return base + __bfloat162float(__ushort_as_bfloat16(ld_u16_stream(a, h)));
@@ -118,10 +152,30 @@ struct PopStore<__nv_bfloat16> {
   }
 };
 
-// shift bases of direction i
+// shift bases of direction i (one global shift)
 __device__ __forceinline__ float fbase(const Params& P, int i) { return w19(i) * P.rho_ref; }
 __device__ __forceinline__ float gbase(const Params& P, int i) {
   return (i == 0 ? 1.f - P.wbar : P.wbar * (1.f / 6.f)) * P.T_ref;
+}
+// shift bases for storage type ST at a cell whose references are r (density) and
+// t (temperature); the global shift ignores them
+template <typename ST>
+__device__ __forceinline__ float fbase_at(const Params& P, int i, float r) {
+  return LocalRef<ST>::on ? w19(i) * r : fbase(P, i);
+}
+template <typename ST>
+__device__ __forceinline__ float gbase_at(const Params& P, int i, float t) {
+  return LocalRef<ST>::on ? (i == 0 ? 1.f - P.wbar : P.wbar * (1.f / 6.f)) * t : gbase(P, i);
+}
+// the references of the populations read (in) or written (out) at cell c, (0, 0)
+// when the storage has none
+template <typename ST>
+__device__ __forceinline__ float2 ref_in_at(const Aux& X, long long c) {
+  return LocalRef<ST>::on ? X.ref_in[c] : make_float2(0.f, 0.f);
+}
+template <typename ST>
+__device__ __forceinline__ float2 ref_out_at(const Aux& X, long long c) {
+  return LocalRef<ST>::on ? X.ref_out[c] : make_float2(0.f, 0.f);
 }
 
 __device__ __forceinline__ void sum19(const float* f, float& rho, float& jx, float& jy, float& jz) {
@@ -249,9 +303,11 @@ __device__ __forceinline__ void boundary_rules(const Params& P, int c, int x, in
     q[fc >> 1] += (fc & 1) ? -1 : 1;
   }
   const int cf = cell_of(P, q[0], q[1], q[2]);
+  // references of the new state (written this step) at the inward neighbour and here
+  const float2 rf = ref_out_at<ST>(X, cf), rc = ref_out_at<ST>(X, c);
   float gf[7];
 #pragma unroll
-  for (int i = 0; i < 7; ++i) gf[i] = PopStore<ST>::ld_plain(g + i * N + cf, gbase(P, i));
+  for (int i = 0; i < 7; ++i) gf[i] = PopStore<ST>::ld_plain(g + i * N + cf, gbase_at<ST>(P, i, rf.y));
   const float Fx = X.Fx[c], Fy = X.Fy[c], Fz = X.Fz[c];
   if (nopen) {
     // one open face: Zou-He (writes only the unknowns); edges and corners of open
@@ -263,8 +319,8 @@ __device__ __forceinline__ void boundary_rules(const Params& P, int c, int x, in
     for (int i = 1; i < 19; ++i)
       if ((unk >> i) & 1u) {
         const float v = nnp == 1 ? fl[i] : w19(i) * rbm;
-        PopStore<ST>::st(f + i * N + c, v, fbase(P, i));
-        fl[i] = PopStore<ST>::round(v, fbase(P, i));
+        PopStore<ST>::st(f + i * N + c, v, fbase_at<ST>(P, i, rc.x));
+        fl[i] = PopStore<ST>::round(v, fbase_at<ST>(P, i, rc.x));
       }
   }
   Tb /= (float)nnp;
@@ -274,8 +330,8 @@ __device__ __forceinline__ void boundary_rules(const Params& P, int c, int x, in
   for (int i = 0; i < 7; ++i) {
     const float w = i == 0 ? w0 : w1;
     const float v = w * Tb + gf[i] - w * Tf;
-    PopStore<ST>::st(g + i * N + c, v, gbase(P, i));
-    gl[i] = PopStore<ST>::round(v, gbase(P, i));
+    PopStore<ST>::st(g + i * N + c, v, gbase_at<ST>(P, i, rc.y));
+    gl[i] = PopStore<ST>::round(v, gbase_at<ST>(P, i, rc.y));
   }
 }
 
@@ -284,14 +340,17 @@ template <typename ST>
 __device__ __forceinline__ void phaseA(const Params& P, int c, const ST* __restrict__ f, const ST* __restrict__ g,
                                        const Aux& X, float* __restrict__ Tout, int& err, bool write_j = true) {
   const Hint h = make_hint();
+  const float2 rin = ref_in_at<ST>(X, c);
   float fl[19], gl[7];
 #pragma unroll
-  for (int i = 0; i < 19; ++i) fl[i] = PopStore<ST>::ld(f + i * P.N + c, fbase(P, i), h);
+  for (int i = 0; i < 19; ++i) fl[i] = PopStore<ST>::ld(f + i * P.N + c, fbase_at<ST>(P, i, rin.x), h);
 #pragma unroll
-  for (int i = 0; i < 7; ++i) gl[i] = PopStore<ST>::ld(g + i * P.N + c, gbase(P, i), h);
+  for (int i = 0; i < 7; ++i) gl[i] = PopStore<ST>::ld(g + i * P.N + c, gbase_at<ST>(P, i, rin.y), h);
   float rho, jx, jy, jz;
   sum19(fl, rho, jx, jy, jz);
   const float T = sum7(gl);
+  // the references of the populations this step writes: this state's rho and T
+  if (LocalRef<ST>::on) X.ref_out[c] = make_float2(rho, T);
   if (!isfinite(rho) || !isfinite(T) || !isfinite(jx + jy + jz)) err |= ERRF_NONFINITE;
   float p, dpdT, psi;
   eos_pr(P, rho, T, p, dpdT);
@@ -395,10 +454,15 @@ __device__ __forceinline__ void phaseC19_cell(const Params& P, int c, const floa
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     const int k = nb_kind(nb, c19x(i), c19y(i), c19z(i));
-    if (k == 0)
-      PopStore<ST>::st(fB + i * N + (c + nb_off(nb, c19x(i), c19y(i), c19z(i))), fs[i], fbase(P, i));
-    else if (k & FACE_WALL)
-      PopStore<ST>::st(fB + opp19(i) * N + c, fs[i], fbase(P, opp19(i)));  // modified bounce-back
+    if (k == 0) {
+      const int d = c + nb_off(nb, c19x(i), c19y(i), c19z(i));
+      // per-cell references: the destination's rho of this step (phase A stored it)
+      const float r = LocalRef<ST>::on ? ld_aux(X.rho + d, h) : 0.f;
+      PopStore<ST>::st(fB + i * N + d, fs[i], fbase_at<ST>(P, i, r));
+    } else if (k & FACE_WALL) {
+      const float r = LocalRef<ST>::on ? ld_aux(X.rho + c, h) : 0.f;
+      PopStore<ST>::st(fB + opp19(i) * N + c, fs[i], fbase_at<ST>(P, opp19(i), r));  // modified bounce-back
+    }
     // else: leaves through an open face
   }
 }
@@ -419,9 +483,10 @@ __device__ __forceinline__ void phaseBC19(const Params& P, int c, const ST* __re
   st_aux(X.Fx + c, Fx, h);
   st_aux(X.Fy + c, Fy, h);
   st_aux(X.Fz + c, Fz, h);
+  const float rin = ref_in_at<ST>(X, c).x;
   float fl[19];
 #pragma unroll
-  for (int i = 0; i < 19; ++i) fl[i] = PopStore<ST>::ld(fA + i * N + c, fbase(P, i), h);
+  for (int i = 0; i < 19; ++i) fl[i] = PopStore<ST>::ld(fA + i * N + c, fbase_at<ST>(P, i, rin), h);
   float rho, jx, jy, jz;
   sum19(fl, rho, jx, jy, jz);
   const int m = P.any_nonperiodic ? node_faces(P, x, y, z) : 0;
@@ -446,10 +511,15 @@ __device__ __forceinline__ void phaseBC19(const Params& P, int c, const ST* __re
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     const int k = nb_kind(nb, c19x(i), c19y(i), c19z(i));
-    if (k == 0)
-      PopStore<ST>::st(fB + i * N + (c + nb_off(nb, c19x(i), c19y(i), c19z(i))), fs[i], fbase(P, i));
-    else if (k & FACE_WALL)
-      PopStore<ST>::st(fB + opp19(i) * N + c, fs[i], fbase(P, opp19(i)));  // modified bounce-back
+    if (k == 0) {
+      const int d = c + nb_off(nb, c19x(i), c19y(i), c19z(i));
+      // per-cell references: the destination's rho of this step (phase A stored it)
+      const float r = LocalRef<ST>::on ? ld_aux(X.rho + d, h) : 0.f;
+      PopStore<ST>::st(fB + i * N + d, fs[i], fbase_at<ST>(P, i, r));
+    } else if (k & FACE_WALL) {
+      const float r = LocalRef<ST>::on ? ld_aux(X.rho + c, h) : 0.f;
+      PopStore<ST>::st(fB + opp19(i) * N + c, fs[i], fbase_at<ST>(P, opp19(i), r));  // modified bounce-back
+    }
   }
 }
 
@@ -488,16 +558,26 @@ __device__ __forceinline__ void phaseC7_cell(const Params& P, int c, const float
   // the destinations' g_i and rho of the relaxed streaming, loaded first so that
   // their latency overlaps the stencil and the collision (a move beyond a
   // non-periodic face reads the cell itself and stores nothing)
-  float gold[7], ry[7];
+  // (per-cell references: g_i(y) decodes with y's reference of the state read and is
+  // encoded with y's reference of this step, (rho, T)(y) as phase A stored them)
+  float gold[7], ry[7], ty[7];
   int yc[7];
 #pragma unroll
   for (int i = 1; i < 7; ++i) {
     const bool ok = nb_kind(nb, c7x(i), c7y(i), c7z(i)) == 0;
     yc[i] = c + (ok ? nb_off(nb, c7x(i), c7y(i), c7z(i)) : 0);
-    gold[i] = PopStore<ST>::ld(gA + i * N + yc[i], gbase(P, i), h);
-    ry[i] = ok ? ld_aux(X.rho + yc[i], h) : 0.f;
+    gold[i] = PopStore<ST>::ld(gA + i * N + yc[i], gbase_at<ST>(P, i, ref_in_at<ST>(X, yc[i]).y), h);
+    if (LocalRef<ST>::on) {
+      const float2 ro = X.ref_out[yc[i]];
+      ry[i] = ok ? ro.x : 0.f;
+      ty[i] = ro.y;
+    } else {
+      ry[i] = ok ? ld_aux(X.rho + yc[i], h) : 0.f;
+      ty[i] = 0.f;
+    }
   }
-  const float rho = ld_aux(X.rho + c, h);
+  const float2 rc = ref_out_at<ST>(X, c);
+  const float rho = LocalRef<ST>::on ? rc.x : ld_aux(X.rho + c, h);
   const float T = sum7(gl);
   // vartheta = 1: d^2T/dt^2 as the backward difference T - 2 T(t-1) + T(t-2); the cell's
   // history moves on by one step after the populations are stored
@@ -518,11 +598,11 @@ __device__ __forceinline__ void phaseC7_cell(const Params& P, int c, const float
     for (int i = 0; i < 7; ++i) X.gstar[i * N + c] = gs[i];
   }
   // relaxed streaming: g_i(y) += (g*_i(y - c_i) - g_i(y)) / (rho(y) c_v)
-  PopStore<ST>::st(gB + c, gl[0] + (gs[0] - gl[0]) * rcp(rho * P.cv), gbase(P, 0));
+  PopStore<ST>::st(gB + c, gl[0] + (gs[0] - gl[0]) * rcp(rho * P.cv), gbase_at<ST>(P, 0, rc.y));
 #pragma unroll
   for (int i = 1; i < 7; ++i) {
     if (nb_kind(nb, c7x(i), c7y(i), c7z(i))) continue;
-    PopStore<ST>::st(gB + i * N + yc[i], gold[i] + (gs[i] - gold[i]) * rcp(ry[i] * P.cv), gbase(P, i));
+    PopStore<ST>::st(gB + i * N + yc[i], gold[i] + (gs[i] - gold[i]) * rcp(ry[i] * P.cv), gbase_at<ST>(P, i, ty[i]));
   }
   if (vt) {
     X.T2[c] = T1;
@@ -541,9 +621,10 @@ template <typename ST>
 __device__ __forceinline__ void phaseC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB, const Aux& X) {
   const long long N = P.N;
   const Hint h = make_hint();
+  const float rin = ref_in_at<ST>(X, c).x;
   float fl[19];
 #pragma unroll
-  for (int i = 0; i < 19; ++i) fl[i] = PopStore<ST>::ld(fA + i * N + c, fbase(P, i), h);
+  for (int i = 0; i < 19; ++i) fl[i] = PopStore<ST>::ld(fA + i * N + c, fbase_at<ST>(P, i, rin), h);
   phaseC19_cell<ST>(P, c, fl, fB, X);
 }
 
@@ -551,9 +632,10 @@ template <typename ST, int VT = -1>
 __device__ __forceinline__ void phaseC7(const Params& P, int c, const ST* __restrict__ gA, ST* gB, const Aux& X) {
   const long long N = P.N;
   const Hint h = make_hint();
+  const float tin = ref_in_at<ST>(X, c).y;
   float gl[7];
 #pragma unroll
-  for (int i = 0; i < 7; ++i) gl[i] = PopStore<ST>::ld(gA + i * N + c, gbase(P, i), h);
+  for (int i = 0; i < 7; ++i) gl[i] = PopStore<ST>::ld(gA + i * N + c, gbase_at<ST>(P, i, tin), h);
   phaseC7_cell<ST, VT>(P, c, gl, gA, gB, X);
 }
 
@@ -572,8 +654,10 @@ __device__ __forceinline__ void phaseD(const Params& P, int c, int x, int y, int
   float fl[19], gl[7];
   // only the open-face rule reads f, and only its known populations
   const unsigned skip = on_open(P, m) ? unknown19(P, x, y, z) : 0x7ffffu;
+  const float rout = ref_out_at<ST>(X, c).x;  // the state written this step
 #pragma unroll
-  for (int i = 0; i < 19; ++i) fl[i] = ((skip >> i) & 1u) ? 0.f : PopStore<ST>::ld_plain(fB + i * N + c, fbase(P, i));
+  for (int i = 0; i < 19; ++i)
+    fl[i] = ((skip >> i) & 1u) ? 0.f : PopStore<ST>::ld_plain(fB + i * N + c, fbase_at<ST>(P, i, rout));
   boundary_rules<ST>(P, c, x, y, z, m, fl, gl, fB, gB, X);
 }
 

@@ -19,7 +19,7 @@ LIB_PATH = os.environ.get("LBM_LIB") or os.path.join(_HERE, "_lib", "liblbm.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_PSI_DOMAIN, ERR_TIMEOUT, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 FACE_PERIODIC, FACE_WALL, FACE_OPEN = 0, 1, 2
-STORE_F32, STORE_F16_SHIFTED, STORE_BF16_SHIFTED = 0, 1, 2
+STORE_F32, STORE_F16_SHIFTED, STORE_BF16_SHIFTED, STORE_F16_LOCAL = 0, 1, 2, 3
 MEM_DEVICE, MEM_HOST = 0, 1
 SCHED_FUSED, SCHED_PHASES, SCHED_SLABS = 0, 1, 2
 

@@ -28,7 +28,8 @@ def _droplet(thermo, n=16, storage=0, schedule=lbm.SCHED_PHASES):
     return p, rho0.reshape(-1).astype(np.float32), T0.reshape(-1).astype(np.float32)
 
 
-@pytest.mark.parametrize("storage", [lbm.STORE_F32, lbm.STORE_F16_SHIFTED, lbm.STORE_BF16_SHIFTED])
+@pytest.mark.parametrize("storage", [lbm.STORE_F32, lbm.STORE_F16_SHIFTED, lbm.STORE_BF16_SHIFTED,
+                                     lbm.STORE_F16_LOCAL])
 @pytest.mark.parametrize("where", ["host", "device"])
 def test_restore_continues_bit_exact(storage, where, thermo):
     import torch
@@ -37,7 +38,8 @@ def test_restore_continues_bit_exact(storage, where, thermo):
     lat = lbm.Lattice(p, rho0, T0)
     lat.lbm_step(7)
     nb = lat.lbm_checkpoint_bytes()
-    assert nb == 256 + 26 * lat.N * (4 if storage == lbm.STORE_F32 else 2)
+    refs = 8 * lat.N if storage == lbm.STORE_F16_LOCAL else 0  # per-cell rho_ref, T_ref
+    assert nb == 256 + 26 * lat.N * (4 if storage == lbm.STORE_F32 else 2) + refs
     img = np.empty(nb, dtype=np.uint8) if where == "host" else torch.empty(nb, dtype=torch.uint8, device="cuda")
     assert lat.lbm_checkpoint(img) == lbm.OK
     lat.lbm_step(5)
