@@ -422,11 +422,18 @@ def test_16bit_storage_set_get_roundtrip(storage, thermo):
     d = f.astype(np.float64) - fref
     assert np.all(np.abs(fq - f) <= 1.02 * k * np.abs(d) + 6e-8 + 1e-7 * np.abs(f))
     lat2 = lbm.Lattice(p)
-    lat2.lbm_set_state(fq, gq)  # a stored state comes back up to the FP32 rounding of the shift
+    lat2.lbm_set_state(fq, gq)
     st, fq2, gq2 = lat2.state()
     lat2.close()
-    assert np.all(np.abs(fq2 - fq) <= 2e-7 * np.abs(fq) + 6e-8)
-    assert np.all(np.abs(gq2 - gq) <= 2e-7 * np.abs(gq) + 6e-8)
+    if storage == lbm.STORE_F16_LOCAL:
+        # the references are now the rho and T of the stored state, which differ slightly
+        # from those of f and g: the deviations are rounded once more
+        fr2, gr2 = _local_refs(fq, gq)
+        assert np.all(np.abs(fq2 - fq) <= 1.02 * k * np.abs(fq - fr2) + 2e-7 * np.abs(fq) + 6e-8)
+        assert np.all(np.abs(gq2 - gq) <= 1.02 * k * np.abs(gq - gr2) + 2e-7 * np.abs(gq) + 6e-8)
+    else:  # a stored state comes back up to the FP32 rounding of the shift
+        assert np.all(np.abs(fq2 - fq) <= 2e-7 * np.abs(fq) + 6e-8)
+        assert np.all(np.abs(gq2 - gq) <= 2e-7 * np.abs(gq) + 6e-8)
 
 
 _STORE_1000 = {}
