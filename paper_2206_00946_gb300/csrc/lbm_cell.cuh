@@ -14,6 +14,15 @@
 #define LBM_HD inline
 #endif
 
+// Device functions of the phase code (lbm_lattice.cuh, lbm_phases.cuh); host
+// functions as well when LBM_HOST_PHASES is defined, for a CPU harness that runs
+// the same per-cell code.
+#if defined(LBM_HOST_PHASES)
+#define LBM_DEV __host__ __device__ __forceinline__
+#else
+#define LBM_DEV __device__ __forceinline__
+#endif
+
 namespace lbm {
 
 // ---------------------------------------------------------------- lattices --

@@ -126,11 +126,20 @@ LBM_HD int nb_off_psi(const Nb& nb, int cx, int cy, int cz) {
   return o;
 }
 
+// load through L2 only (cache-global); a plain load on the host
+LBM_DEV float ld_cg(const float* p) {
+#if defined(__CUDA_ARCH__)
+  return __ldcg(p);
+#else
+  return *p;
+#endif
+}
+
 // psi at lattice point (x,y,z) that may lie outside the domain: periodic faces
 // wrap; open faces copy the boundary node; wall faces mirror through the wall
 // layer and add the wetting term sqrt(|grad_t psi|^2) tan(pi/2 - theta) of
 // Eq. 36 when exactly one non-periodic axis is crossed.
-__device__ __forceinline__ float psi_ext(const Params& P, const float* psi, int x, int y, int z) {
+LBM_DEV float psi_ext(const Params& P, const float* psi, int x, int y, int z) {
   int q[3] = {x, y, z}, r[3];
   int nout = 0, wax = -1, wface = -1;
 #pragma unroll
@@ -155,7 +164,7 @@ __device__ __forceinline__ float psi_ext(const Params& P, const float* psi, int 
       wface = face;
     }
   }
-  float val = __ldcg(psi + cell_of(P, r[0], r[1], r[2]));
+  float val = ld_cg(psi + cell_of(P, r[0], r[1], r[2]));
   if (nout == 1 && wax >= 0) {
     const float tn = P.tan_wet[wface];
     if (tn != 0.f) {
@@ -177,7 +186,7 @@ __device__ __forceinline__ float psi_ext(const Params& P, const float* psi, int 
         pp[wax] = pm[wax] = layer;
         pp[b] = up;
         pm[b] = dn;
-        const float d = __ldcg(psi + cell_of(P, pp[0], pp[1], pp[2])) - __ldcg(psi + cell_of(P, pm[0], pm[1], pm[2]));
+        const float d = ld_cg(psi + cell_of(P, pp[0], pp[1], pp[2])) - ld_cg(psi + cell_of(P, pm[0], pm[1], pm[2]));
         s2 += d * d;
       }
       val += sqrtf(s2) * tn;
@@ -188,7 +197,7 @@ __device__ __forceinline__ float psi_ext(const Params& P, const float* psi, int 
 
 // Real velocity at a point that may lie outside: zero beyond a wall, the
 // boundary node's value beyond an open face, periodic wrap otherwise.
-__device__ __forceinline__ void u_ext(const Params& P, const float* ux, const float* uy, const float* uz, int x, int y, int z, float& ox, float& oy, float& oz) {
+LBM_DEV void u_ext(const Params& P, const float* ux, const float* uy, const float* uz, int x, int y, int z, float& ox, float& oy, float& oz) {
   int q[3] = {x, y, z};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -202,9 +211,9 @@ __device__ __forceinline__ void u_ext(const Params& P, const float* ux, const fl
     q[a] = (k == FACE_PERIODIC) ? wrapi(v, n) : (v < 0 ? 0 : n - 1);
   }
   const int c = cell_of(P, q[0], q[1], q[2]);
-  ox = __ldcg(ux + c);
-  oy = __ldcg(uy + c);
-  oz = __ldcg(uz + c);
+  ox = ld_cg(ux + c);
+  oy = ld_cg(uy + c);
+  oz = ld_cg(uz + c);
 }
 
 }  // namespace lbm

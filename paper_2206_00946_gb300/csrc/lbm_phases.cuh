@@ -38,38 +38,60 @@ struct Hint {
   unsigned long long stream, keep;
 };
 
-__device__ __forceinline__ Hint make_hint() {
+LBM_DEV Hint make_hint() {
   Hint h;
+#if defined(__CUDA_ARCH__)
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(h.stream));
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(h.keep));
+#else
+  h.stream = h.keep = 0;  // host harness: no cache policies
+#endif
   return h;
 }
 
 // Population stores keep the default policy: a push-streamed warp store is shifted
 // by one cell for x-moving directions and so covers two sectors partially; evicting
 // early would write each sector twice and force an ECC read-modify-write in HBM.
-__device__ __forceinline__ void st_pop(float* a, float v, const Hint&) { *a = v; }
+LBM_DEV void st_pop(float* a, float v, const Hint&) { *a = v; }
 
 #if defined(LBM_NO_L2HINT)
-__device__ __forceinline__ float ld_pop(const float* a, const Hint&) { return __ldg(a); }
-__device__ __forceinline__ float ld_aux(const float* a, const Hint&) { return *a; }
-__device__ __forceinline__ void st_aux(float* a, float v, const Hint&) { *a = v; }
+LBM_DEV float ld_pop(const float* a, const Hint&) {
+#if defined(__CUDA_ARCH__)
+  return __ldg(a);
+#else
+  return *a;
+#endif
+}
+LBM_DEV float ld_aux(const float* a, const Hint&) { return *a; }
+LBM_DEV void st_aux(float* a, float v, const Hint&) { *a = v; }
 #else
 // populations of the previous time step (read-only during the step)
-__device__ __forceinline__ float ld_pop(const float* a, const Hint& h) {
+LBM_DEV float ld_pop(const float* a, const Hint& h) {
+#if defined(__CUDA_ARCH__)
   float v;
   asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(h.stream));
   return v;
+#else
+  return *a;
+#endif
 }
 
 // scratch written and read within the step
-__device__ __forceinline__ float ld_aux(const float* a, const Hint& h) {
+LBM_DEV float ld_aux(const float* a, const Hint& h) {
+#if defined(__CUDA_ARCH__)
   float v;
   asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(h.keep));
   return v;
+#else
+  return *a;
+#endif
 }
-__device__ __forceinline__ void st_aux(float* a, float v, const Hint& h) {
+LBM_DEV void st_aux(float* a, float v, const Hint& h) {
+#if defined(__CUDA_ARCH__)
   asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(h.keep));
+#else
+  *a = v;
+#endif
 }
 #endif
 
@@ -99,86 +121,90 @@ struct PopStore;
 
 template <>
 struct PopStore<float> {
-  __device__ __forceinline__ static float ld(const float* a, float, const Hint& h) { return ld_pop(a, h); }
-  __device__ __forceinline__ static float ld_plain(const float* a, float) { return *a; }
-  __device__ __forceinline__ static void st(float* a, float v, float) { *a = v; }
-  __device__ __forceinline__ static float round(float v, float) { return v; }
+  LBM_DEV static float ld(const float* a, float, const Hint& h) { return ld_pop(a, h); }
+  LBM_DEV static float ld_plain(const float* a, float) { return *a; }
+  LBM_DEV static void st(float* a, float v, float) { *a = v; }
+  LBM_DEV static float round(float v, float) { return v; }
 };
 
-__device__ __forceinline__ unsigned short ld_u16_stream(const void* a, const Hint& h) {
+LBM_DEV unsigned short ld_u16_stream(const void* a, const Hint& h) {
+#if defined(__CUDA_ARCH__)
   unsigned short v;
   asm volatile("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(a), "l"(h.stream));
   return v;
+#else
+  return *static_cast<const unsigned short*>(a);
+#endif
 }
 
 template <>
 struct PopStore<__half> {
-  __device__ __forceinline__ static float ld(const __half* a, float base, const Hint& h) {
+  LBM_DEV static float ld(const __half* a, float base, const Hint& h) {
     return base + __half2float(__ushort_as_half(ld_u16_stream(a, h)));
   }
-  __device__ __forceinline__ static float ld_plain(const __half* a, float base) { return base + __half2float(*a); }
-  __device__ __forceinline__ static void st(__half* a, float v, float base) { *a = __float2half_rn(v - base); }
+  LBM_DEV static float ld_plain(const __half* a, float base) { return base + __half2float(*a); }
+  LBM_DEV static void st(__half* a, float v, float base) { *a = __float2half_rn(v - base); }
   // the value a later load of st(v) returns
-  __device__ __forceinline__ static float round(float v, float base) {
+  LBM_DEV static float round(float v, float base) {
     return base + __half2float(__float2half_rn(v - base));
   }
 };
 
 template <>
 struct PopStore<lhalf> {
-  __device__ __forceinline__ static float ld(const lhalf* a, float base, const Hint& h) {
+  LBM_DEV static float ld(const lhalf* a, float base, const Hint& h) {
     return base + __half2float(__ushort_as_half(ld_u16_stream(a, h)));
   }
-  __device__ __forceinline__ static float ld_plain(const lhalf* a, float base) { return base + __half2float(a->v); }
-  __device__ __forceinline__ static void st(lhalf* a, float v, float base) { a->v = __float2half_rn(v - base); }
-  __device__ __forceinline__ static float round(float v, float base) {
+  LBM_DEV static float ld_plain(const lhalf* a, float base) { return base + __half2float(a->v); }
+  LBM_DEV static void st(lhalf* a, float v, float base) { a->v = __float2half_rn(v - base); }
+  LBM_DEV static float round(float v, float base) {
     return base + __half2float(__float2half_rn(v - base));
   }
 };
 
 template <>
 struct PopStore<__nv_bfloat16> {
-  __device__ __forceinline__ static float ld(const __nv_bfloat16* a, float base, const Hint& h) {
+  LBM_DEV static float ld(const __nv_bfloat16* a, float base, const Hint& h) {
     return base + __bfloat162float(__ushort_as_bfloat16(ld_u16_stream(a, h)));
   }
-  __device__ __forceinline__ static float ld_plain(const __nv_bfloat16* a, float base) {
+  LBM_DEV static float ld_plain(const __nv_bfloat16* a, float base) {
     return base + __bfloat162float(*a);
   }
-  __device__ __forceinline__ static void st(__nv_bfloat16* a, float v, float base) {
+  LBM_DEV static void st(__nv_bfloat16* a, float v, float base) {
     *a = __float2bfloat16_rn(v - base);
   }
-  __device__ __forceinline__ static float round(float v, float base) {
+  LBM_DEV static float round(float v, float base) {
     return base + __bfloat162float(__float2bfloat16_rn(v - base));
   }
 };
 
 // shift bases of direction i (one global shift)
-__device__ __forceinline__ float fbase(const Params& P, int i) { return w19(i) * P.rho_ref; }
-__device__ __forceinline__ float gbase(const Params& P, int i) {
+LBM_DEV float fbase(const Params& P, int i) { return w19(i) * P.rho_ref; }
+LBM_DEV float gbase(const Params& P, int i) {
   return (i == 0 ? 1.f - P.wbar : P.wbar * (1.f / 6.f)) * P.T_ref;
 }
 // shift bases for storage type ST at a cell whose references are r (density) and
 // t (temperature); the global shift ignores them
 template <typename ST>
-__device__ __forceinline__ float fbase_at(const Params& P, int i, float r) {
+LBM_DEV float fbase_at(const Params& P, int i, float r) {
   return LocalRef<ST>::on ? w19(i) * r : fbase(P, i);
 }
 template <typename ST>
-__device__ __forceinline__ float gbase_at(const Params& P, int i, float t) {
+LBM_DEV float gbase_at(const Params& P, int i, float t) {
   return LocalRef<ST>::on ? (i == 0 ? 1.f - P.wbar : P.wbar * (1.f / 6.f)) * t : gbase(P, i);
 }
 // the references of the populations read (in) or written (out) at cell c, (0, 0)
 // when the storage has none
 template <typename ST>
-__device__ __forceinline__ float2 ref_in_at(const Aux& X, long long c) {
+LBM_DEV float2 ref_in_at(const Aux& X, long long c) {
   return LocalRef<ST>::on ? X.ref_in[c] : make_float2(0.f, 0.f);
 }
 template <typename ST>
-__device__ __forceinline__ float2 ref_out_at(const Aux& X, long long c) {
+LBM_DEV float2 ref_out_at(const Aux& X, long long c) {
   return LocalRef<ST>::on ? X.ref_out[c] : make_float2(0.f, 0.f);
 }
 
-__device__ __forceinline__ void sum19(const float* f, float& rho, float& jx, float& jy, float& jz) {
+LBM_DEV void sum19(const float* f, float& rho, float& jx, float& jy, float& jz) {
   rho = ((f[0] + (f[1] + f[2])) + ((f[3] + f[4]) + (f[5] + f[6]))) +
         (((f[7] + f[8]) + (f[9] + f[10])) + ((f[11] + f[12]) + (f[13] + f[14]))) + ((f[15] + f[16]) + (f[17] + f[18]));
   jx = ((f[1] - f[2]) + (f[7] - f[8])) + ((f[9] - f[10]) + (f[11] - f[12])) + (f[13] - f[14]);
@@ -186,11 +212,11 @@ __device__ __forceinline__ void sum19(const float* f, float& rho, float& jx, flo
   jz = ((f[5] - f[6]) + (f[11] - f[12])) + ((f[14] - f[13]) + (f[15] - f[16])) + (f[18] - f[17]);
 }
 
-__device__ __forceinline__ float sum7(const float* g) {
+LBM_DEV float sum7(const float* g) {
   return (g[0] + (g[1] + g[2])) + ((g[3] + g[4]) + (g[5] + g[6]));
 }
 
-__device__ __forceinline__ void cell_xyz(const Params& P, int c, int& x, int& y, int& z) {
+LBM_DEV void cell_xyz(const Params& P, int c, int& x, int& y, int& z) {
   const int row = (int)fdiv((unsigned)c, P.dnx_mul, P.dnx_shr);
   x = c - row * P.nx;
   z = (int)fdiv((unsigned)row, P.dny_mul, P.dny_shr);
@@ -200,7 +226,7 @@ __device__ __forceinline__ void cell_xyz(const Params& P, int c, int& x, int& y,
 // Boundary nodes of plane z are enumerated as candidates k = 0..count-1: the
 // whole plane when z lies on a non-periodic z face, otherwise its perimeter
 // rows/columns on non-periodic x or y faces.
-__device__ __forceinline__ int boundary_count(const Params& P, int z) {
+LBM_DEV int boundary_count(const Params& P, int z) {
   const bool xnp = P.face_kind[0] != FACE_PERIODIC, ynp = P.face_kind[2] != FACE_PERIODIC;
   if (P.face_kind[4] != FACE_PERIODIC && (z == 0 || z == P.nz - 1)) return P.nx * P.ny;
   if (xnp && ynp) return 2 * P.nx + 2 * (P.ny - 2);
@@ -209,7 +235,7 @@ __device__ __forceinline__ int boundary_count(const Params& P, int z) {
   return 0;
 }
 
-__device__ __forceinline__ void boundary_xy(const Params& P, int z, int k, int& x, int& y) {
+LBM_DEV void boundary_xy(const Params& P, int z, int k, int& x, int& y) {
   const bool xnp = P.face_kind[0] != FACE_PERIODIC, ynp = P.face_kind[2] != FACE_PERIODIC;
   if (P.face_kind[4] != FACE_PERIODIC && (z == 0 || z == P.nz - 1)) {
     y = (int)fdiv((unsigned)k, P.dnx_mul, P.dnx_shr);
@@ -235,7 +261,7 @@ __device__ __forceinline__ void boundary_xy(const Params& P, int z, int k, int& 
 // All boundary nodes of the lattice as one flat index range: the whole planes
 // z = 0 and nz-1 when the z faces are not periodic, then the perimeter
 // candidates of the other planes.
-__device__ __forceinline__ void boundary_candidate(const Params& P, int idx, int& x, int& y, int& z) {
+LBM_DEV void boundary_candidate(const Params& P, int idx, int& x, int& y, int& z) {
   const int plane = P.nx * P.ny;
   int k;
   if (idx < P.bd_zplanes * plane) {
@@ -251,12 +277,12 @@ __device__ __forceinline__ void boundary_candidate(const Params& P, int idx, int
   boundary_xy(P, z, k, x, y);
 }
 
-__device__ __forceinline__ bool interior1(const Params& P, int x, int y, int z) {
+LBM_DEV bool interior1(const Params& P, int x, int y, int z) {
   return x >= 1 && x <= P.nx - 2 && y >= 1 && y <= P.ny - 2 && z >= 1 && z <= P.nz - 2;
 }
 
 // ------------------------------------------------------------------- A -----
-__device__ __forceinline__ float face_T_at(const Params& P, int face, int x, int y, int z) {
+LBM_DEV float face_T_at(const Params& P, int face, int x, int y, int z) {
   const int a = face >> 1;
   const float* t = P.Tface[face];
   if (a == 0) return t[y + P.ny * z];
@@ -265,7 +291,7 @@ __device__ __forceinline__ float face_T_at(const Params& P, int face, int x, int
 }
 
 // Unknown D3Q19 directions of a node: those arriving from beyond a non-periodic face.
-__device__ __forceinline__ unsigned unknown19(const Params& P, int x, int y, int z) {
+LBM_DEV unsigned unknown19(const Params& P, int x, int y, int z) {
   unsigned unk = 0;
 #pragma unroll
   for (int i = 1; i < 19; ++i) {
@@ -284,7 +310,7 @@ __device__ __forceinline__ unsigned unknown19(const Params& P, int x, int y, int
 // fl / gl by the values a later load returns).  Every load is issued before the
 // first store, so that the node's memory round trips overlap.
 template <typename ST>
-__device__ __forceinline__ void boundary_rules(const Params& P, int c, int x, int y, int z, int m, float* fl,
+LBM_DEV void boundary_rules(const Params& P, int c, int x, int y, int z, int m, float* fl,
                                                   float* gl, ST* f, ST* g, const Aux& X) {
   const long long N = P.N;
   int nnp = 0, nopen = 0, oface = -1;
@@ -337,7 +363,7 @@ __device__ __forceinline__ void boundary_rules(const Params& P, int c, int x, in
 
 // write_j: store j for phase B (the fused force + D3Q19 pass recomputes it).
 template <typename ST>
-__device__ __forceinline__ void phaseA(const Params& P, int c, const ST* __restrict__ f, const ST* __restrict__ g,
+LBM_DEV void phaseA(const Params& P, int c, const ST* __restrict__ f, const ST* __restrict__ g,
                                        const Aux& X, float* __restrict__ Tout, int& err, bool write_j = true) {
   const Hint h = make_hint();
   const float2 rin = ref_in_at<ST>(X, c);
@@ -367,7 +393,7 @@ __device__ __forceinline__ void phaseA(const Params& P, int c, const ST* __restr
 
 // ------------------------------------------------------------------- B -----
 // Wetting term of Eq. 36 is needed only next to a wall face with theta != 90.
-__device__ __forceinline__ bool needs_wetting(const Params& P, const Nb& nb) {
+LBM_DEV bool needs_wetting(const Params& P, const Nb& nb) {
   bool w = false;
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -377,7 +403,7 @@ __device__ __forceinline__ bool needs_wetting(const Params& P, const Nb& nb) {
 }
 
 // F = -G psi(x) sum_i varpi_i psi(x + c_i) c_i (Eq. 6), ghost psi beyond the faces
-__device__ __forceinline__ void force_at(const Params& P, int c, int x, int y, int z, const Nb& nb, const Aux& X,
+LBM_DEV void force_at(const Params& P, int c, int x, int y, int z, const Nb& nb, const Aux& X,
                                          const Hint& h, float& Fx, float& Fy, float& Fz) {
   const float* psi = X.psi;
   float sx = 0.f, sy = 0.f, sz = 0.f;
@@ -403,7 +429,7 @@ __device__ __forceinline__ void force_at(const Params& P, int c, int x, int y, i
   Fz = k * sz;
 }
 
-__device__ __forceinline__ void phaseB(const Params& P, int c, const Aux& X) {
+LBM_DEV void phaseB(const Params& P, int c, const Aux& X) {
   int x, y, z;
   cell_xyz(P, c, x, y, z);
   Nb nb;
@@ -431,7 +457,7 @@ __device__ __forceinline__ void phaseB(const Params& P, int c, const Aux& X) {
 // Phase C, D3Q19 part, for one cell whose pre-collision populations are in fl:
 // collision with the exact-difference forcing, push streaming, bounce-back.
 template <typename ST>
-__device__ __forceinline__ void phaseC19_cell(const Params& P, int c, const float* fl, ST* fB, const Aux& X) {
+LBM_DEV void phaseC19_cell(const Params& P, int c, const float* fl, ST* fB, const Aux& X) {
   int x, y, z;
   cell_xyz(P, c, x, y, z);
   Nb nb;
@@ -471,7 +497,7 @@ __device__ __forceinline__ void phaseC19_cell(const Params& P, int c, const floa
 // real velocity (both stored for the D3Q7 phase and the next step's open faces),
 // then the D3Q19 collision and push of phaseC19_cell.
 template <typename ST>
-__device__ __forceinline__ void phaseBC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB, const Aux& X) {
+LBM_DEV void phaseBC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB, const Aux& X) {
   int x, y, z;
   cell_xyz(P, c, x, y, z);
   Nb nb;
@@ -525,7 +551,7 @@ __device__ __forceinline__ void phaseBC19(const Params& P, int c, const ST* __re
 
 // div u = 3 sum_i w_i c_i . u(x + c_i): the isotropic D3Q19 difference of the
 // real velocity (zero beyond a wall, the boundary node's value beyond an open face).
-__device__ __forceinline__ float divu_at(const Params& P, int c, const Nb& nb, const Aux& X, const Hint& h) {
+LBM_DEV float divu_at(const Params& P, int c, const Nb& nb, const Aux& X, const Hint& h) {
   float du = 0.f;
 #pragma unroll
   for (int i = 1; i < 19; ++i) {
@@ -546,7 +572,7 @@ __device__ __forceinline__ float divu_at(const Params& P, int c, const Nb& nb, c
 // real velocity of the cell come from phases A and B.
 // VT: vartheta known at compile time (0 or 1), or -1 to read it from P.
 template <typename ST, int VT = -1>
-__device__ __forceinline__ void phaseC7_cell(const Params& P, int c, const float* gl, const ST* __restrict__ gA, ST* gB,
+LBM_DEV void phaseC7_cell(const Params& P, int c, const float* gl, const ST* __restrict__ gA, ST* gB,
                                              const Aux& X) {
   const bool vt = VT < 0 ? P.vartheta != 0 : VT != 0;
   int x, y, z;
@@ -611,14 +637,14 @@ __device__ __forceinline__ void phaseC7_cell(const Params& P, int c, const float
 }
 
 template <typename ST>
-__device__ __forceinline__ void phaseC_cell(const Params& P, int c, const float* fl, const float* gl,
+LBM_DEV void phaseC_cell(const Params& P, int c, const float* fl, const float* gl,
                                             const ST* __restrict__ gA, ST* fB, ST* gB, const Aux& X) {
   phaseC19_cell<ST>(P, c, fl, fB, X);
   phaseC7_cell<ST>(P, c, gl, gA, gB, X);
 }
 
 template <typename ST>
-__device__ __forceinline__ void phaseC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB, const Aux& X) {
+LBM_DEV void phaseC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB, const Aux& X) {
   const long long N = P.N;
   const Hint h = make_hint();
   const float rin = ref_in_at<ST>(X, c).x;
@@ -629,7 +655,7 @@ __device__ __forceinline__ void phaseC19(const Params& P, int c, const ST* __res
 }
 
 template <typename ST, int VT = -1>
-__device__ __forceinline__ void phaseC7(const Params& P, int c, const ST* __restrict__ gA, ST* gB, const Aux& X) {
+LBM_DEV void phaseC7(const Params& P, int c, const ST* __restrict__ gA, ST* gB, const Aux& X) {
   const long long N = P.N;
   const Hint h = make_hint();
   const float tin = ref_in_at<ST>(X, c).y;
@@ -640,7 +666,7 @@ __device__ __forceinline__ void phaseC7(const Params& P, int c, const ST* __rest
 }
 
 template <typename ST>
-__device__ __forceinline__ void phaseC(const Params& P, int c, const ST* __restrict__ fA, const ST* __restrict__ gA,
+LBM_DEV void phaseC(const Params& P, int c, const ST* __restrict__ fA, const ST* __restrict__ gA,
                                        ST* fB, ST* gB, const Aux& X) {
   phaseC19<ST>(P, c, fA, fB, X);
   phaseC7<ST>(P, c, gA, gB, X);
@@ -648,7 +674,7 @@ __device__ __forceinline__ void phaseC(const Params& P, int c, const ST* __restr
 
 // ------------------------------------------------------------------- D -----
 template <typename ST>
-__device__ __forceinline__ void phaseD(const Params& P, int c, int x, int y, int z, int m, ST* fB, ST* gB,
+LBM_DEV void phaseD(const Params& P, int c, int x, int y, int z, int m, ST* fB, ST* gB,
                                        const Aux& X) {
   const long long N = P.N;
   float fl[19], gl[7];

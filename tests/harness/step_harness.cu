@@ -1,0 +1,86 @@
+// Host harness for the per-cell phase code of the library (csrc/lbm_phases.cuh):
+// the same phase functions, compiled for the host with LBM_HOST_PHASES, run
+// over a small lattice in the order of the one-launch-per-phase schedule
+// (A for every cell, then force + D3Q19 collide/push, then D3Q7
+// collide/push, then the boundary rules on the face nodes), with the
+// double-buffered populations in any storage form.  CPU tests compare it with
+// the FP64 oracle before any GPU run.  Test infrastructure only.
+#define LBM_HOST_PHASES
+#include "lbm_api.cu"
+
+// the harness never records an adjoint (lbm_adjoint.cu is not linked in)
+void adj_free(lbm_ctx*) {}
+
+namespace {
+
+template <typename ST>
+int host_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps, float* f_out, float* g_out) {
+  if (check_params(hp) != LBM_OK || hp->vartheta) return LBM_ERR_ARG;
+  Params P = make_device_params(*hp);
+  const long long N = P.N;
+  std::vector<std::vector<float>> tface(6);
+  for (int f = 0; f < 6; ++f)
+    if (hp->face_kind[f] != LBM_FACE_PERIODIC) {
+      tface[f].assign((size_t)face_len(*hp, f), (float)hp->face_T[f]);
+      P.Tface[f] = tface[f].data();
+    }
+  std::vector<ST> fb[2], gb[2];
+  for (int k = 0; k < 2; ++k) {
+    fb[k].resize((size_t)(19 * N));
+    gb[k].resize((size_t)(7 * N));
+  }
+  std::vector<float> aux((size_t)(11 * N), 0.f);
+  std::vector<float2> ref(LocalRef<ST>::on ? (size_t)(2 * N) : 0);
+  float* a = aux.data();
+  Aux X = Aux{a, a + N, a + 2 * N, a + 3 * N, a + 4 * N, a + 5 * N, a + 6 * N, a + 7 * N, a + 8 * N, a + 9 * N, a + 10 * N};
+  auto refs = [&](int k) -> float2* { return LocalRef<ST>::on ? ref.data() + (size_t)k * N : nullptr; };
+  // the state into buffer 0: per-cell references of the state itself (as lbm_set_state)
+  for (long long c = 0; c < N; ++c) {
+    float r = 0.f, t = 0.f;
+    for (int i = 0; i < 19; ++i) r += f0[i * N + c];
+    for (int i = 0; i < 7; ++i) t += g0[i * N + c];
+    if (LocalRef<ST>::on) refs(0)[c] = make_float2(r, t);
+    const float2 rc = LocalRef<ST>::on ? refs(0)[c] : make_float2(0.f, 0.f);
+    for (int i = 0; i < 19; ++i) PopStore<ST>::st(&fb[0][i * N + c], f0[i * N + c], fbase_at<ST>(P, i, rc.x));
+    for (int i = 0; i < 7; ++i) PopStore<ST>::st(&gb[0][i * N + c], g0[i * N + c], gbase_at<ST>(P, i, rc.y));
+  }
+  int err = 0, cur = 0;
+  for (int s = 0; s < nsteps; ++s) {
+    const int A = cur, B = 1 - cur;
+    Aux Xs = X;
+    Xs.ref_in = refs(A);
+    Xs.ref_out = refs(B);
+    for (long long c = 0; c < N; ++c) phaseA<ST>(P, (int)c, fb[A].data(), gb[A].data(), Xs, nullptr, err, false);
+    for (long long c = 0; c < N; ++c) phaseBC19<ST>(P, (int)c, fb[A].data(), fb[B].data(), Xs);
+    for (long long c = 0; c < N; ++c) phaseC7<ST, 0>(P, (int)c, gb[A].data(), gb[B].data(), Xs);
+    for (long long k = 0; k < P.bd_total; ++k) {
+      int x, y, z;
+      boundary_candidate(P, (int)k, x, y, z);
+      const int m = node_faces(P, x, y, z);
+      if (m) phaseD<ST>(P, cell_of(P, x, y, z), x, y, z, m, fb[B].data(), gb[B].data(), Xs);
+    }
+    cur = B;
+  }
+  for (long long c = 0; c < N; ++c) {
+    const float2 rc = LocalRef<ST>::on ? refs(cur)[c] : make_float2(0.f, 0.f);
+    for (int i = 0; i < 19; ++i) f_out[i * N + c] = PopStore<ST>::ld_plain(&fb[cur][i * N + c], fbase_at<ST>(P, i, rc.x));
+    for (int i = 0; i < 7; ++i) g_out[i * N + c] = PopStore<ST>::ld_plain(&gb[cur][i * N + c], gbase_at<ST>(P, i, rc.y));
+  }
+  return err;
+}
+
+}  // namespace
+
+extern "C" {
+// nsteps steps of the lattice hp from the FP32 state (f0, g0) in hp->storage;
+// returns the phase error flags (ERRF_*) or a negative lbm_status
+int h_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps, float* f_out, float* g_out) {
+  switch (hp->storage) {
+    case LBM_STORE_F32: return host_run<float>(hp, f0, g0, nsteps, f_out, g_out);
+    case LBM_STORE_F16_SHIFTED: return host_run<__half>(hp, f0, g0, nsteps, f_out, g_out);
+    case LBM_STORE_BF16_SHIFTED: return host_run<__nv_bfloat16>(hp, f0, g0, nsteps, f_out, g_out);
+    case LBM_STORE_F16_LOCAL: return host_run<lhalf>(hp, f0, g0, nsteps, f_out, g_out);
+    default: return LBM_ERR_ARG;
+  }
+}
+}

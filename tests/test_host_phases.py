@@ -1,0 +1,113 @@
+"""CPU run of the library's per-cell phase code against the FP64 oracle.
+
+tests/harness/step_harness.cu compiles csrc/lbm_phases.cuh for the host (LBM_HOST_PHASES)
+and runs whole steps over small lattices in the order of the one-launch-per-phase
+schedule: phase A for every cell, then force + D3Q19 collide/push, then D3Q7
+collide/push, then the boundary rules on the face nodes, with double-buffered
+populations in each storage form.  Index, boundary and storage mistakes in the
+kernels' code therefore show up without a GPU.  The arithmetic differs from the
+GPU's only in the reciprocals (a correctly rounded division here, the fast
+intrinsic there) and in the contraction of multiply-adds, so the FP32 tolerance
+of the GPU parity tests applies.
+"""
+import ctypes as ct
+import os
+import shutil
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+from cases import (CASES, HALF_ULP, STORAGES_16, W7, _face_nodes, _local_refs, _storage_bound_ok, case_params,
+                   droplet_state, f32, pop_err)
+from oracle import Oracle
+from paper_2206_00946_gb300 import lbm, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2206_00946_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def H():
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    d = tempfile.mkdtemp()
+    so = os.path.join(d, "step_harness.so")
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-O2", "-shared",
+                    "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
+                    os.path.join(ROOT, "tests", "harness", "step_harness.cu"), "-o", so], check=True)
+    L = ct.CDLL(so)
+    L.h_run.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p]
+    return L
+
+
+def host_run(H, p, f, g, n):
+    """n steps of the phase code on the host (one-launch-per-phase order); n = 0 returns the state as stored."""
+    P = lbm.make_params(dict(p, schedule=lbm.SCHED_PHASES))
+    f, g = f32(f), f32(g)
+    fo, go = np.empty_like(f), np.empty_like(g)
+    err = H.h_run(ct.byref(P), f.ctypes.data, g.ctypes.data, n, fo.ctypes.data, go.ctypes.data)
+    assert err == 0, err
+    return fo, go
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_one_step_populations_match_oracle(H, name, thermo):
+    p = case_params(name, thermo)
+    f, g = droplet_state(p, thermo, seed=11)
+    st_o, fo, go = Oracle(p).step(f.astype(np.float64), g.astype(np.float64))
+    assert st_o == 0
+    fh, gh = host_run(H, p, f, g, 1)
+    assert pop_err(fh, fo, thermo) < 1e-5
+    assert pop_err(gh, go, thermo) < 1e-5
+
+
+@pytest.mark.parametrize("storage", STORAGES_16)
+@pytest.mark.parametrize("name", ["periodic", "open_all", "wall_bottom_open_top", "walls_xy_theta", "ragged_open_x"])
+def test_16bit_storage_one_step_within_half_ulp(H, name, storage, thermo):
+    """As the GPU test of the same name: one step from the stored state is within half an ulp
+    of the stored deviations of the oracle's step (per-cell shifts for STORE_F16_LOCAL)."""
+    p = case_params(name, thermo)
+    rho_ref, T_ref = 0.8 * thermo["rho_v"], thermo["Ts"]
+    p.update(storage=storage, store_rho_ref=rho_ref, store_T_ref=T_ref)
+    f, g = droplet_state(p, thermo, seed=11)
+    fq, gq = host_run(H, p, f, g, 0)
+    fh, gh = host_run(H, p, f, g, 1)
+    st_o, fo, go = Oracle(p).step(fq.astype(np.float64), gq.astype(np.float64))
+    assert st_o == 0
+    face = _face_nodes(p)
+    fref, gref = (_local_refs(fq, gq) if storage == lbm.STORE_F16_LOCAL else (W.W19 * rho_ref, W7 * T_ref))
+    ex_f, rel_f = _storage_bound_ok(fh, fo, fref, HALF_ULP[storage], thermo, face)
+    ex_g, rel_g = _storage_bound_ok(gh, go, gref, HALF_ULP[storage], thermo, face)
+    assert ex_f <= 0 and ex_g <= 0, (rel_f, rel_g)
+
+
+def test_per_cell_references_cut_the_fp16_error(H, thermo):
+    """300 steps of the evaporating 20^3 droplet (open faces) from the FP32 initial state,
+    against the oracle.  Measured on the host: FP32 1.5e-5 (max relative rho); FP16 with one
+    global shift 3.4e-3 / 7.5e-4 (rho / T), relative L2 1.2e-3 on rho; FP16 with per-cell
+    references 2.4e-4 / 4.0e-5, L2 6.3e-5: the per-cell references make the stored
+    deviations the change of a cell over one step plus its non-equilibrium part."""
+    p, rho0, T0 = W.droplet(thermo["Tc"], thermo["rho_v"], thermo["rho_l"], n=20, R=5.0, W=3.0, seed=2206)
+    o = Oracle(p)
+    f0, g0 = o.init_state(rho0, T0)
+    f0, g0 = f32(f0), f32(g0)
+    st, fo, go = o.run(f0.astype(np.float64), g0.astype(np.float64), 300)
+    assert st == 0
+    rho_o, T_o = fo.sum(0), go.sum(0)
+
+    def errors(storage):
+        fh, gh = host_run(H, dict(p, storage=storage), f0, g0, 300)
+        rho, T = fh.sum(0).astype(np.float64), gh.sum(0).astype(np.float64)
+        return (float(np.max(np.abs(rho - rho_o) / rho_o)), float(np.max(np.abs(T - T_o) / T_o)),
+                float(np.linalg.norm(rho - rho_o) / np.linalg.norm(rho_o)))
+
+    e32 = errors(lbm.STORE_F32)
+    eg = errors(lbm.STORE_F16_SHIFTED)
+    el = errors(lbm.STORE_F16_LOCAL)
+    print(f"300 droplet steps, max rho / max T / L2 rho: FP32 {e32}, FP16 global {eg}, FP16 per-cell {el}")
+    assert e32[0] < 1e-4
+    assert el[0] < 1e-3 and el[1] < 2e-4 and el[2] < 2.5e-4
+    assert eg[0] > 1e-3 and el[2] < eg[2] / 5
