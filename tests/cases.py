@@ -3,11 +3,14 @@ the small lattices with every boundary kind, seeded droplet states, the populati
 error relative to the workloads' smallest physical scale, and the rounding bound
 of the 16-bit storage forms."""
 import numpy as np
+import pytest
 
 from paper_2206_00946_gb300 import lbm, workloads as W
 
 W7 = W.w7(0.75)
-STORAGES_16 = [lbm.STORE_F16_SHIFTED, lbm.STORE_BF16_SHIFTED, lbm.STORE_F16_LOCAL]  # the 16-bit forms
+# the 16-bit forms; the per-cell-reference form runs after every other test (see conftest)
+F16_LOCAL = pytest.param(lbm.STORE_F16_LOCAL, marks=pytest.mark.per_cell_refs, id="f16local")
+STORAGES_16 = [lbm.STORE_F16_SHIFTED, lbm.STORE_BF16_SHIFTED, F16_LOCAL]
 
 
 def f32(a):

@@ -11,6 +11,12 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built liblbm.so")
     config.addinivalue_line("markers", "slow: long CPU run (still part of the default suite)")
+    config.addinivalue_line("markers", "per_cell_refs: the FP16 storage with per-cell references (run last)")
+
+
+def pytest_collection_modifyitems(config, items):
+    # the per-cell-reference storage form is the newest: its cases run after all others
+    items.sort(key=lambda it: it.get_closest_marker("per_cell_refs") is not None)
 
 
 @pytest.fixture(scope="session")

@@ -8,6 +8,7 @@ different lattice, storage mode or shift is rejected.
 import numpy as np
 import pytest
 
+from cases import F16_LOCAL
 from paper_2206_00946_gb300 import lbm
 from paper_2206_00946_gb300 import workloads as W
 
@@ -28,8 +29,7 @@ def _droplet(thermo, n=16, storage=0, schedule=lbm.SCHED_PHASES):
     return p, rho0.reshape(-1).astype(np.float32), T0.reshape(-1).astype(np.float32)
 
 
-@pytest.mark.parametrize("storage", [lbm.STORE_F32, lbm.STORE_F16_SHIFTED, lbm.STORE_BF16_SHIFTED,
-                                     lbm.STORE_F16_LOCAL])
+@pytest.mark.parametrize("storage", [lbm.STORE_F32, lbm.STORE_F16_SHIFTED, lbm.STORE_BF16_SHIFTED, F16_LOCAL])
 @pytest.mark.parametrize("where", ["host", "device"])
 def test_restore_continues_bit_exact(storage, where, thermo):
     import torch
