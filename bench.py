@@ -17,9 +17,11 @@ the end-to-end rate through host buffers, the FP64 CPU oracle on a bounded sampl
 (cpu_baseline), the adjoint/forward cost on a 64^3 droplet over 2000 steps with
 checkpoints every 100 (adjoint), 48 uneven droplet domains stepped as one batch
 (batched), and the 512^3 heated-plate pool with 64 droplets in FP16-shifted
-storage (large), and the step time with the correction term of Eq. 16
-(vartheta = 1) against without (vartheta); --no-adjoint / --no-batched /
---no-large / --no-vartheta / --no-cpu-baseline skip those.
+storage (large), the step time with the correction term of Eq. 16
+(vartheta = 1) against without (vartheta), and the rate in each population
+storage form (storage_forms: FP32, FP16 with one global shift, FP16 with
+per-cell references); --no-adjoint / --no-batched / --no-large /
+--no-vartheta / --no-storage / --no-cpu-baseline skip those.
 
 N > 1 (torchrun, one rank per GPU) runs N independent replicas of the domain
 (weak scaling, no collective on the data path).  --impl reference times the
@@ -321,6 +323,35 @@ def vartheta_cost(lbm, p, rho0, T0, stream, steps=2000, warmup=50):
             "paper_cpu_ratio": 55983.6 / 54461.5, "steps": steps}
 
 
+def storage_cost(lbm, p, rho0, T0, stream, steps=2000, warmup=50):
+    """MLUPS of the workload in each population storage form (slab schedule): FP32, FP16 with
+    one global shift, and FP16 with per-cell references.  A form whose run reports an error
+    status is recorded with that status instead of a rate."""
+    import torch
+    rho_d = torch.tensor(rho0.reshape(-1), dtype=torch.float32, device="cuda")
+    T_d = torch.tensor(T0.reshape(-1), dtype=torch.float32, device="cuda")
+    N = p["nx"] * p["ny"] * p["nz"]
+    out = {"steps": steps}
+    for name in ("f32", "f16", "f16local"):
+        lat = lbm.Lattice(dict(p, storage=STORAGE[name][0], schedule=lbm.SCHED_SLABS), rho_d, T_d,
+                          stream=stream.cuda_stream)
+        lat.lbm_step(warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lat.lbm_step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = lat.lbm_sync()
+        lat.close()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"mlups": N / (ms * 1e-3) / 1e6, "ms_per_step": ms} if st == lbm.OK else \
+            {"status": lbm.lbm_status_string(st)}
+    if "mlups" in out["f32"] and "mlups" in out["f16local"]:
+        out["f16local_over_f32"] = out["f16local"]["mlups"] / out["f32"]["mlups"]
+    return out
+
+
 def thermo_product():
     """T_c and the coexistence densities from the library's host helpers (not the oracle)."""
     from paper_2206_00946_gb300 import lbm
@@ -393,6 +424,7 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the 512^3 FP16 pool measurement")
     ap.add_argument("--adjoint-side", type=int, default=64, help="cube side of the adjoint workload (64)")
     ap.add_argument("--no-vartheta", action="store_true", help="skip the vartheta = 1 cost measurement")
+    ap.add_argument("--no-storage", action="store_true", help="skip the storage-form comparison")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = dist_env()
@@ -497,6 +529,9 @@ def main():
     vartheta = None
     if args.storage == "f32" and not args.no_vartheta:
         vartheta = vartheta_cost(lbm, p, rho0, T0, stream)
+    storage_forms = None
+    if args.storage == "f32" and not args.no_storage:
+        storage_forms = storage_cost(lbm, p, rho0, T0, stream)
 
     if rank != 0:
         if dist:
@@ -542,6 +577,7 @@ def main():
         "batched": batched,
         "large": large,
         "vartheta": vartheta,
+        "storage_forms": storage_forms,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * N / args.steps,
                 "d2h_bytes_per_step": 5 * 4 * N / args.steps},
         "gpu_launches": launches * args.steps,

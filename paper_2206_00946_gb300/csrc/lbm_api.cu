@@ -83,7 +83,7 @@ __global__ void k_load(Params P, const T* __restrict__ src, float* dst, int q, i
 // Phase kernels over the cell range [c0, c1) (whole planes) with grid-stride loops.
 // write_j: store j for phase B (only lbm_macros runs phase B on its own).
 template <typename T>
-__global__ void k_phaseA(Params P, const T* __restrict__ f, const T* __restrict__ g, Aux X, float* Tout, int* err,
+__global__ void k_phaseA(Params P, const T* __restrict__ f, const T* __restrict__ g, AuxFor<T> X, float* Tout, int* err,
                          int c0, int c1, int write_j) {
   int e = 0;
   for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x)
@@ -97,7 +97,7 @@ __global__ void k_phaseB(Params P, Aux X, int c0, int c1) {
 
 template <typename T>
 __global__ void __launch_bounds__(256, LBM_PHASEC_MINBLOCKS) k_phaseC19(Params P, const T* __restrict__ fA, T* fB,
-                                                                        Aux X, int c0, int c1) {
+                                                                        AuxFor<T> X, int c0, int c1) {
   for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x)
     phaseC19(P, c, fA, fB, X);
 }
@@ -105,20 +105,21 @@ __global__ void __launch_bounds__(256, LBM_PHASEC_MINBLOCKS) k_phaseC19(Params P
 // force, velocity and the D3Q19 collision + push in one pass (phases B and C19)
 template <typename T>
 __global__ void __launch_bounds__(256, LBM_PHASEC_MINBLOCKS) k_phaseBC19(Params P, const T* __restrict__ fA, T* fB,
-                                                                         Aux X, int c0, int c1) {
+                                                                         AuxFor<T> X, int c0, int c1) {
   for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x)
     phaseBC19(P, c, fA, fB, X);
 }
 
 // VT: vartheta of the context (a separate instantiation each, launched by launch_c7)
 template <typename T, int VT>
-__global__ void __launch_bounds__(256, 4) k_phaseC7(Params P, const T* __restrict__ gA, T* gB, Aux X, int c0, int c1) {
+__global__ void __launch_bounds__(256, 4) k_phaseC7(Params P, const T* __restrict__ gA, T* gB, AuxFor<T> X, int c0,
+                                                    int c1) {
   for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x)
     phaseC7<T, VT>(P, c, gA, gB, X);
 }
 
 template <typename T>
-void launch_c7(const lbm_ctx* c, const Aux& X, int blocks, cudaStream_t st, const T* gA, T* gB, int c0, int c1) {
+void launch_c7(const lbm_ctx* c, const AuxFor<T>& X, int blocks, cudaStream_t st, const T* gA, T* gB, int c0, int c1) {
   if (c->P.vartheta)
     k_phaseC7<T, 1><<<blocks, kThreads, 0, st>>>(c->P, gA, gB, X, c0, c1);
   else
@@ -127,7 +128,7 @@ void launch_c7(const lbm_ctx* c, const Aux& X, int blocks, cudaStream_t st, cons
 
 // one thread per boundary candidate (boundary_candidate enumerates them)
 template <typename T>
-__global__ void __launch_bounds__(256, 3) k_phaseD(Params P, T* fB, T* gB, Aux X) {
+__global__ void __launch_bounds__(256, 3) k_phaseD(Params P, T* fB, T* gB, AuxFor<T> X) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < (int)P.bd_total; k += gridDim.x * blockDim.x) {
     int x, y, z;
     boundary_candidate(P, k, x, y, z);
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(256, 3) k_phaseD(Params P, T* fB, T* gB, Aux X
 
 // boundary nodes of planes z0 + blockIdx.y
 template <typename T>
-__global__ void __launch_bounds__(256, 3) k_phaseD_planes(Params P, T* fB, T* gB, Aux X, int z0) {
+__global__ void __launch_bounds__(256, 3) k_phaseD_planes(Params P, T* fB, T* gB, AuxFor<T> X, int z0) {
   const int z = z0 + blockIdx.y;
   const int cnt = boundary_count(P, z);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
@@ -450,10 +451,14 @@ T* gbuf(lbm_ctx* c, int k) {
 float2* ref_of(const lbm_ctx* c, int k) { return c->ref ? c->ref + (long long)k * c->N : nullptr; }
 
 // the scratch of a step that reads buffer a and writes buffer 1 - a
-Aux aux_for(const lbm_ctx* c, int a) {
-  Aux X = c->X;
-  X.ref_in = ref_of(c, a);
-  X.ref_out = ref_of(c, 1 - a);
+template <typename T>
+AuxFor<T> aux_for(const lbm_ctx* c, int a) {
+  AuxFor<T> X;
+  static_cast<Aux&>(X) = c->X;
+  if constexpr (LocalRef<T>::on) {
+    X.ref_in = ref_of(c, a);
+    X.ref_out = ref_of(c, 1 - a);
+  }
   return X;
 }
 
@@ -461,7 +466,7 @@ Aux aux_for(const lbm_ctx* c, int a) {
 // (with per-cell references phase A also writes those of the idle buffer: harmless)
 template <typename T>
 int run_macros_t(lbm_ctx* c, float* Tout) {
-  k_phaseA<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, c->cur), gbuf<T>(c, c->cur), aux_for(c, c->cur),
+  k_phaseA<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, c->cur), gbuf<T>(c, c->cur), aux_for<T>(c, c->cur),
                                                    Tout, c->err_d, 0, (int)c->N, 1);
   k_phaseB<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->X, 0, (int)c->N);
   return cuda_status(cudaGetLastError());
@@ -474,7 +479,7 @@ int run_macros(lbm_ctx* c, float* Tout) { return LBM_WITH_STORAGE(c, run_macros_
 template <typename T>
 int step_phases_t(lbm_ctx* c) {
   const int a = c->cur, b = 1 - c->cur;
-  const Aux X = aux_for(c, a);
+  const AuxFor<T> X = aux_for<T>(c, a);
   cudaEvent_t e = prof_begin(c);
   // j is stored only for the staged path, whose separate phase B reads it
   k_phaseA<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, a), gbuf<T>(c, a), X, nullptr, c->err_d, 0,
@@ -651,7 +656,7 @@ template <typename T>
 int slab_enqueue_step_t(lbm_ctx* c, bool first) {
   SlabPlan& S = *c->slabs;
   const int a = c->cur, b = 1 - c->cur;
-  const Aux X = aux_for(c, a);
+  const AuxFor<T> X = aux_for<T>(c, a);
   const bool zper = c->P.face_kind[4] == FACE_PERIODIC;
   const int n = S.nslab, plane = c->P.nx * c->P.ny;
   std::vector<int> d;

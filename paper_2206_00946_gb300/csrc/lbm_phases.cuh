@@ -15,6 +15,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "lbm_lattice.cuh"
 
 namespace lbm {
@@ -24,8 +26,12 @@ struct Aux {
   float *Fx, *Fy, *Fz, *ux, *uy, *uz;  // phase B
   float *gstar, *divu;  // optional (NULL): the D3Q7 phase also stores g* (7N) and div u
   float *T1, *T2;       // vartheta = 1: T at the two previous steps, kept by the D3Q7 phase
-  // FP16 storage with per-cell references: (rho_ref, T_ref) of every cell for the
-  // populations read this step (ref_in) and for those written (ref_out); NULL otherwise
+};
+
+// The scratch of the FP16 storage with per-cell references: (rho_ref, T_ref) of every
+// cell for the populations read this step (ref_in) and for those written (ref_out).
+// Only that storage form's kernels take it, so the others keep the plain Aux.
+struct AuxRef : Aux {
   const float2* ref_in;
   float2* ref_out;
 };
@@ -117,6 +123,9 @@ struct LocalRef<lhalf> {
 };
 
 template <typename ST>
+using AuxFor = typename std::conditional<LocalRef<ST>::on, AuxRef, Aux>::type;
+
+template <typename ST>
 struct PopStore;
 
 template <>
@@ -196,12 +205,18 @@ LBM_DEV float gbase_at(const Params& P, int i, float t) {
 // the references of the populations read (in) or written (out) at cell c, (0, 0)
 // when the storage has none
 template <typename ST>
-LBM_DEV float2 ref_in_at(const Aux& X, long long c) {
-  return LocalRef<ST>::on ? X.ref_in[c] : make_float2(0.f, 0.f);
+LBM_DEV float2 ref_in_at(const AuxFor<ST>& X, long long c) {
+  if constexpr (LocalRef<ST>::on)
+    return X.ref_in[c];
+  else
+    return make_float2(0.f, 0.f);
 }
 template <typename ST>
-LBM_DEV float2 ref_out_at(const Aux& X, long long c) {
-  return LocalRef<ST>::on ? X.ref_out[c] : make_float2(0.f, 0.f);
+LBM_DEV float2 ref_out_at(const AuxFor<ST>& X, long long c) {
+  if constexpr (LocalRef<ST>::on)
+    return X.ref_out[c];
+  else
+    return make_float2(0.f, 0.f);
 }
 
 LBM_DEV void sum19(const float* f, float& rho, float& jx, float& jy, float& jz) {
@@ -311,7 +326,7 @@ LBM_DEV unsigned unknown19(const Params& P, int x, int y, int z) {
 // first store, so that the node's memory round trips overlap.
 template <typename ST>
 LBM_DEV void boundary_rules(const Params& P, int c, int x, int y, int z, int m, float* fl,
-                                                  float* gl, ST* f, ST* g, const Aux& X) {
+                                                  float* gl, ST* f, ST* g, const AuxFor<ST>& X) {
   const long long N = P.N;
   int nnp = 0, nopen = 0, oface = -1;
   float rb = 0.f, Tb = 0.f;
@@ -364,7 +379,7 @@ LBM_DEV void boundary_rules(const Params& P, int c, int x, int y, int z, int m, 
 // write_j: store j for phase B (the fused force + D3Q19 pass recomputes it).
 template <typename ST>
 LBM_DEV void phaseA(const Params& P, int c, const ST* __restrict__ f, const ST* __restrict__ g,
-                                       const Aux& X, float* __restrict__ Tout, int& err, bool write_j = true) {
+                                       const AuxFor<ST>& X, float* __restrict__ Tout, int& err, bool write_j = true) {
   const Hint h = make_hint();
   const float2 rin = ref_in_at<ST>(X, c);
   float fl[19], gl[7];
@@ -376,7 +391,7 @@ LBM_DEV void phaseA(const Params& P, int c, const ST* __restrict__ f, const ST* 
   sum19(fl, rho, jx, jy, jz);
   const float T = sum7(gl);
   // the references of the populations this step writes: this state's rho and T
-  if (LocalRef<ST>::on) X.ref_out[c] = make_float2(rho, T);
+  if constexpr (LocalRef<ST>::on) X.ref_out[c] = make_float2(rho, T);
   if (!isfinite(rho) || !isfinite(T) || !isfinite(jx + jy + jz)) err |= ERRF_NONFINITE;
   float p, dpdT, psi;
   eos_pr(P, rho, T, p, dpdT);
@@ -457,7 +472,7 @@ LBM_DEV void phaseB(const Params& P, int c, const Aux& X) {
 // Phase C, D3Q19 part, for one cell whose pre-collision populations are in fl:
 // collision with the exact-difference forcing, push streaming, bounce-back.
 template <typename ST>
-LBM_DEV void phaseC19_cell(const Params& P, int c, const float* fl, ST* fB, const Aux& X) {
+LBM_DEV void phaseC19_cell(const Params& P, int c, const float* fl, ST* fB, const AuxFor<ST>& X) {
   int x, y, z;
   cell_xyz(P, c, x, y, z);
   Nb nb;
@@ -497,7 +512,7 @@ LBM_DEV void phaseC19_cell(const Params& P, int c, const float* fl, ST* fB, cons
 // real velocity (both stored for the D3Q7 phase and the next step's open faces),
 // then the D3Q19 collision and push of phaseC19_cell.
 template <typename ST>
-LBM_DEV void phaseBC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB, const Aux& X) {
+LBM_DEV void phaseBC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB, const AuxFor<ST>& X) {
   int x, y, z;
   cell_xyz(P, c, x, y, z);
   Nb nb;
@@ -573,7 +588,7 @@ LBM_DEV float divu_at(const Params& P, int c, const Nb& nb, const Aux& X, const 
 // VT: vartheta known at compile time (0 or 1), or -1 to read it from P.
 template <typename ST, int VT = -1>
 LBM_DEV void phaseC7_cell(const Params& P, int c, const float* gl, const ST* __restrict__ gA, ST* gB,
-                                             const Aux& X) {
+                                             const AuxFor<ST>& X) {
   const bool vt = VT < 0 ? P.vartheta != 0 : VT != 0;
   int x, y, z;
   cell_xyz(P, c, x, y, z);
@@ -593,7 +608,7 @@ LBM_DEV void phaseC7_cell(const Params& P, int c, const float* gl, const ST* __r
     const bool ok = nb_kind(nb, c7x(i), c7y(i), c7z(i)) == 0;
     yc[i] = c + (ok ? nb_off(nb, c7x(i), c7y(i), c7z(i)) : 0);
     gold[i] = PopStore<ST>::ld(gA + i * N + yc[i], gbase_at<ST>(P, i, ref_in_at<ST>(X, yc[i]).y), h);
-    if (LocalRef<ST>::on) {
+    if constexpr (LocalRef<ST>::on) {
       const float2 ro = X.ref_out[yc[i]];
       ry[i] = ok ? ro.x : 0.f;
       ty[i] = ro.y;
@@ -638,13 +653,13 @@ LBM_DEV void phaseC7_cell(const Params& P, int c, const float* gl, const ST* __r
 
 template <typename ST>
 LBM_DEV void phaseC_cell(const Params& P, int c, const float* fl, const float* gl,
-                                            const ST* __restrict__ gA, ST* fB, ST* gB, const Aux& X) {
+                                            const ST* __restrict__ gA, ST* fB, ST* gB, const AuxFor<ST>& X) {
   phaseC19_cell<ST>(P, c, fl, fB, X);
   phaseC7_cell<ST>(P, c, gl, gA, gB, X);
 }
 
 template <typename ST>
-LBM_DEV void phaseC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB, const Aux& X) {
+LBM_DEV void phaseC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB, const AuxFor<ST>& X) {
   const long long N = P.N;
   const Hint h = make_hint();
   const float rin = ref_in_at<ST>(X, c).x;
@@ -655,7 +670,7 @@ LBM_DEV void phaseC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB,
 }
 
 template <typename ST, int VT = -1>
-LBM_DEV void phaseC7(const Params& P, int c, const ST* __restrict__ gA, ST* gB, const Aux& X) {
+LBM_DEV void phaseC7(const Params& P, int c, const ST* __restrict__ gA, ST* gB, const AuxFor<ST>& X) {
   const long long N = P.N;
   const Hint h = make_hint();
   const float tin = ref_in_at<ST>(X, c).y;
@@ -667,7 +682,7 @@ LBM_DEV void phaseC7(const Params& P, int c, const ST* __restrict__ gA, ST* gB, 
 
 template <typename ST>
 LBM_DEV void phaseC(const Params& P, int c, const ST* __restrict__ fA, const ST* __restrict__ gA,
-                                       ST* fB, ST* gB, const Aux& X) {
+                                       ST* fB, ST* gB, const AuxFor<ST>& X) {
   phaseC19<ST>(P, c, fA, fB, X);
   phaseC7<ST>(P, c, gA, gB, X);
 }
@@ -675,7 +690,7 @@ LBM_DEV void phaseC(const Params& P, int c, const ST* __restrict__ fA, const ST*
 // ------------------------------------------------------------------- D -----
 template <typename ST>
 LBM_DEV void phaseD(const Params& P, int c, int x, int y, int z, int m, ST* fB, ST* gB,
-                                       const Aux& X) {
+                                       const AuxFor<ST>& X) {
   const long long N = P.N;
   float fl[19], gl[7];
   // only the open-face rule reads f, and only its known populations

@@ -32,7 +32,8 @@ int host_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps,
   std::vector<float> aux((size_t)(11 * N), 0.f);
   std::vector<float2> ref(LocalRef<ST>::on ? (size_t)(2 * N) : 0);
   float* a = aux.data();
-  Aux X = Aux{a, a + N, a + 2 * N, a + 3 * N, a + 4 * N, a + 5 * N, a + 6 * N, a + 7 * N, a + 8 * N, a + 9 * N, a + 10 * N};
+  const Aux X = Aux{a, a + N, a + 2 * N, a + 3 * N, a + 4 * N, a + 5 * N, a + 6 * N, a + 7 * N, a + 8 * N, a + 9 * N,
+                    a + 10 * N};
   auto refs = [&](int k) -> float2* { return LocalRef<ST>::on ? ref.data() + (size_t)k * N : nullptr; };
   // the state into buffer 0: per-cell references of the state itself (as lbm_set_state)
   for (long long c = 0; c < N; ++c) {
@@ -47,9 +48,12 @@ int host_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps,
   int err = 0, cur = 0;
   for (int s = 0; s < nsteps; ++s) {
     const int A = cur, B = 1 - cur;
-    Aux Xs = X;
-    Xs.ref_in = refs(A);
-    Xs.ref_out = refs(B);
+    AuxFor<ST> Xs;
+    static_cast<Aux&>(Xs) = X;
+    if constexpr (LocalRef<ST>::on) {
+      Xs.ref_in = refs(A);
+      Xs.ref_out = refs(B);
+    }
     for (long long c = 0; c < N; ++c) phaseA<ST>(P, (int)c, fb[A].data(), gb[A].data(), Xs, nullptr, err, false);
     for (long long c = 0; c < N; ++c) phaseBC19<ST>(P, (int)c, fb[A].data(), fb[B].data(), Xs);
     for (long long c = 0; c < N; ++c) phaseC7<ST, 0>(P, (int)c, gb[A].data(), gb[B].data(), Xs);
