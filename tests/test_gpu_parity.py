@@ -391,7 +391,10 @@ def test_16bit_storage_slab_1000_steps_error_vs_oracle(storage, thermo):
     if storage == lbm.STORE_F16_SHIFTED:
         assert e_rho < 1.5e-2 and e_T < 5e-3, (e_rho, e_T)
     elif storage == lbm.STORE_F16_LOCAL:
-        assert e_rho < 4e-3 and e_T < 2e-4 and l2_rho < 1e-3 and l2_T < 1e-4, (e_rho, e_T, l2_rho, l2_T)
+        # a margin of 3-7x over the host run: this slab amplifies rounding differences (the host and
+        # GPU runs of the global shift differ by 3x); the global shift measured 6.4e-3 / 2.2e-3 and
+        # 1.7e-3 / 9.5e-4 (L2) on the GPU
+        assert e_rho < 8e-3 and e_T < 3e-4 and l2_rho < 1e-3 and l2_T < 1e-4, (e_rho, e_T, l2_rho, l2_T)
     else:
         assert np.all(np.isfinite(fg)) and np.all(np.isfinite(gg)) and e_T < 0.1, (e_rho, e_T)
 
@@ -421,7 +424,8 @@ def test_16bit_storage_droplet_1000_steps_error_vs_oracle(storage, thermo):
     if storage == lbm.STORE_F16_SHIFTED:
         assert e_T < 2e-2 and l2_T < 4e-3, (e_T, l2_T)  # measured 9.4e-3 and 1.9e-3
     elif storage == lbm.STORE_F16_LOCAL:  # the kernels on the host: 3.7e-3 / 2.8e-4, L2 1.3e-3 / 5.4e-5
-        assert e_rho < 8e-3 and e_T < 6e-4 and l2_rho < 3e-3 and l2_T < 1.2e-4, (e_rho, e_T, l2_rho, l2_T)
+        # (margin as for the slab; the global shift: 0.12 / 9.4e-3, L2 4.7e-2 / 1.9e-3 on the GPU)
+        assert e_rho < 2e-2 and e_T < 2e-3 and l2_rho < 5e-3 and l2_T < 3e-4, (e_rho, e_T, l2_rho, l2_T)
 
 
 # The collision takes a closed form when s_q = s_pi = 1 and m^eq = M-hat f^eq (the
