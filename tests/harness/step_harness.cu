@@ -15,7 +15,7 @@ namespace {
 
 template <typename ST>
 int host_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps, float* f_out, float* g_out) {
-  if (check_params(hp) != LBM_OK || hp->vartheta) return LBM_ERR_ARG;
+  if (check_params(hp) != LBM_OK) return LBM_ERR_ARG;
   Params P = make_device_params(*hp);
   const long long N = P.N;
   std::vector<std::vector<float>> tface(6);
@@ -31,9 +31,14 @@ int host_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps,
   }
   std::vector<float> aux((size_t)(11 * N), 0.f);
   std::vector<float2> ref(LocalRef<ST>::on ? (size_t)(2 * N) : 0);
+  std::vector<float> hist(hp->vartheta ? (size_t)(2 * N) : 0);  // T(t-1), T(t-2) for vartheta = 1
   float* a = aux.data();
-  const Aux X = Aux{a, a + N, a + 2 * N, a + 3 * N, a + 4 * N, a + 5 * N, a + 6 * N, a + 7 * N, a + 8 * N, a + 9 * N,
+  Aux X = Aux{a, a + N, a + 2 * N, a + 3 * N, a + 4 * N, a + 5 * N, a + 6 * N, a + 7 * N, a + 8 * N, a + 9 * N,
                     a + 10 * N};
+  if (hp->vartheta) {
+    X.T1 = hist.data();
+    X.T2 = hist.data() + N;
+  }
   auto refs = [&](int k) -> float2* { return LocalRef<ST>::on ? ref.data() + (size_t)k * N : nullptr; };
   // the state into buffer 0: per-cell references of the state itself (as lbm_set_state)
   for (long long c = 0; c < N; ++c) {
@@ -45,6 +50,14 @@ int host_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps,
     for (int i = 0; i < 19; ++i) PopStore<ST>::st(&fb[0][i * N + c], f0[i * N + c], fbase_at<ST>(P, i, rc.x));
     for (int i = 0; i < 7; ++i) PopStore<ST>::st(&gb[0][i * N + c], g0[i * N + c], gbase_at<ST>(P, i, rc.y));
   }
+  // vartheta = 1: the state is taken to be at rest before, T(t-1) = T(t-2) = sum g as stored
+  if (hp->vartheta)
+    for (long long c = 0; c < N; ++c) {
+      const float t = LocalRef<ST>::on ? refs(0)[c].y : 0.f;
+      float gl[7];
+      for (int i = 0; i < 7; ++i) gl[i] = PopStore<ST>::ld_plain(&gb[0][i * N + c], gbase_at<ST>(P, i, t));
+      X.T1[c] = X.T2[c] = sum7(gl);
+    }
   int err = 0, cur = 0;
   for (int s = 0; s < nsteps; ++s) {
     const int A = cur, B = 1 - cur;
@@ -56,7 +69,12 @@ int host_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps,
     }
     for (long long c = 0; c < N; ++c) phaseA<ST>(P, (int)c, fb[A].data(), gb[A].data(), Xs, nullptr, err, false);
     for (long long c = 0; c < N; ++c) phaseBC19<ST>(P, (int)c, fb[A].data(), fb[B].data(), Xs);
-    for (long long c = 0; c < N; ++c) phaseC7<ST, 0>(P, (int)c, gb[A].data(), gb[B].data(), Xs);
+    for (long long c = 0; c < N; ++c) {
+      if (hp->vartheta)
+        phaseC7<ST, 1>(P, (int)c, gb[A].data(), gb[B].data(), Xs);
+      else
+        phaseC7<ST, 0>(P, (int)c, gb[A].data(), gb[B].data(), Xs);
+    }
     for (long long k = 0; k < P.bd_total; ++k) {
       int x, y, z;
       boundary_candidate(P, (int)k, x, y, z);

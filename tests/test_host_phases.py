@@ -84,6 +84,34 @@ def test_16bit_storage_one_step_within_half_ulp(H, name, storage, thermo):
     assert ex_f <= 0 and ex_g <= 0, (rel_f, rel_g)
 
 
+@pytest.mark.parametrize("storage", [lbm.STORE_F32, lbm.STORE_F16_LOCAL])
+@pytest.mark.parametrize("name", ["walls_z", "open_all", "wall_bottom_open_top", "periodic"])
+def test_vartheta_one_steps_match_oracle(H, name, storage, thermo):
+    """The D3Q7 phase with the correction of Eq. 16 (vartheta = 1): three steps of a vapour
+    density bump with a 1 % temperature wave, the state taken to be at rest before, against
+    the oracle given the same history.  FP32 within the one-step tolerance; FP16 with
+    per-cell references within its storage rounding over three steps, with the bounds of
+    the GPU test of the 16-bit forms (next to the open faces the stored deviations of f
+    reach about 10 % of f, so 2^-11 of that per step: measured 1.3e-4 on f)."""
+    p = dict(case_params(name, thermo), vartheta=1, storage=storage)
+    x, y, z = W.grid(p["nx"], p["ny"], p["nz"])
+    r2 = (x - 0.45 * p["nx"]) ** 2 + (y - 0.55 * p["ny"]) ** 2 + (z - 0.5 * p["nz"]) ** 2
+    rho0 = W.perturb(thermo["rho_v"] * (1.0 + 0.03 * np.exp(-r2 / 4.0)), 1e-3, seed=12)
+    T0 = thermo["Ts"] * (1 + 0.01 * np.sin(0.7 * x + 0.5 * y + 0.3 * z))
+    o = Oracle(p)
+    f, g = o.init_state(rho0, T0)
+    f, g = f32(f), f32(g)
+    fq, gq = host_run(H, p, f, g, 0)
+    st_o, fo, go, _ = o.run_hist(fq.astype(np.float64), gq.astype(np.float64), o.history(gq.astype(np.float64)), 3)
+    assert st_o == 0
+    _, f0, g0 = Oracle(dict(p, vartheta=0)).run(fq.astype(np.float64), gq.astype(np.float64), 3)
+    assert pop_err(g0, go, thermo) > 1e-4  # the correction matters at this tolerance
+    fh, gh = host_run(H, p, f, g, 3)
+    tf, tg = (1e-5, 1e-5) if storage == lbm.STORE_F32 else (5e-4, 1e-4)
+    ef, eg = pop_err(fh, fo, thermo), pop_err(gh, go, thermo)
+    assert ef < tf and eg < tg, (ef, eg)
+
+
 def test_per_cell_references_cut_the_fp16_error(H, thermo):
     """300 steps of the evaporating 20^3 droplet (open faces) from the FP32 initial state,
     against the oracle.  Measured on the host: FP32 1.5e-5 (max relative rho); FP16 with one
