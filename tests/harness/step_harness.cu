@@ -13,8 +13,11 @@ void adj_free(lbm_ctx*) {}
 
 namespace {
 
+// tface[f] (may be NULL, as may any entry): a per-node Dirichlet temperature of face f, as
+// lbm_set_face_T takes it; NULL entries use face_T[f]
 template <typename ST>
-int host_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps, float* f_out, float* g_out) {
+int host_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps, float* f_out, float* g_out,
+             const float* const* tface_in) {
   if (check_params(hp) != LBM_OK) return LBM_ERR_ARG;
   Params P = make_device_params(*hp);
   const long long N = P.N;
@@ -22,6 +25,8 @@ int host_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps,
   for (int f = 0; f < 6; ++f)
     if (hp->face_kind[f] != LBM_FACE_PERIODIC) {
       tface[f].assign((size_t)face_len(*hp, f), (float)hp->face_T[f]);
+      if (tface_in && tface_in[f])
+        for (size_t k = 0; k < tface[f].size(); ++k) tface[f][k] = tface_in[f][k];
       P.Tface[f] = tface[f].data();
     }
   std::vector<ST> fb[2], gb[2];
@@ -94,14 +99,16 @@ int host_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps,
 }  // namespace
 
 extern "C" {
-// nsteps steps of the lattice hp from the FP32 state (f0, g0) in hp->storage;
+// nsteps steps of the lattice hp from the FP32 state (f0, g0) in hp->storage, with the
+// per-node face temperatures tface (NULL: the constant face_T);
 // returns the phase error flags (ERRF_*) or a negative lbm_status
-int h_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps, float* f_out, float* g_out) {
+int h_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps, float* f_out, float* g_out,
+          const float* const* tface) {
   switch (hp->storage) {
-    case LBM_STORE_F32: return host_run<float>(hp, f0, g0, nsteps, f_out, g_out);
-    case LBM_STORE_F16_SHIFTED: return host_run<__half>(hp, f0, g0, nsteps, f_out, g_out);
-    case LBM_STORE_BF16_SHIFTED: return host_run<__nv_bfloat16>(hp, f0, g0, nsteps, f_out, g_out);
-    case LBM_STORE_F16_LOCAL: return host_run<lhalf>(hp, f0, g0, nsteps, f_out, g_out);
+    case LBM_STORE_F32: return host_run<float>(hp, f0, g0, nsteps, f_out, g_out, tface);
+    case LBM_STORE_F16_SHIFTED: return host_run<__half>(hp, f0, g0, nsteps, f_out, g_out, tface);
+    case LBM_STORE_BF16_SHIFTED: return host_run<__nv_bfloat16>(hp, f0, g0, nsteps, f_out, g_out, tface);
+    case LBM_STORE_F16_LOCAL: return host_run<lhalf>(hp, f0, g0, nsteps, f_out, g_out, tface);
     default: return LBM_ERR_ARG;
   }
 }

@@ -39,16 +39,19 @@ def H():
                     "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
                     os.path.join(ROOT, "tests", "harness", "step_harness.cu"), "-o", so], check=True)
     L = ct.CDLL(so)
-    L.h_run.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p]
+    L.h_run.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p]
     return L
 
 
-def host_run(H, p, f, g, n):
-    """n steps of the phase code on the host (one-launch-per-phase order); n = 0 returns the state as stored."""
+def host_run(H, p, f, g, n, tface=None):
+    """n steps of the phase code on the host (one-launch-per-phase order); n = 0 returns the state as
+    stored.  tface: {face: per-node temperatures} as lbm_set_face_T takes them."""
     P = lbm.make_params(dict(p, schedule=lbm.SCHED_PHASES))
     f, g = f32(f), f32(g)
     fo, go = np.empty_like(f), np.empty_like(g)
-    err = H.h_run(ct.byref(P), f.ctypes.data, g.ctypes.data, n, fo.ctypes.data, go.ctypes.data)
+    keep = {k: f32(v).reshape(-1) for k, v in (tface or {}).items()}
+    tf = (ct.c_void_p * 6)(*[keep[k].ctypes.data if k in keep else None for k in range(6)])
+    err = H.h_run(ct.byref(P), f.ctypes.data, g.ctypes.data, n, fo.ctypes.data, go.ctypes.data, tf)
     assert err == 0, err
     return fo, go
 
@@ -57,6 +60,32 @@ def host_run(H, p, f, g, n):
 def test_one_step_populations_match_oracle(H, name, thermo):
     p = case_params(name, thermo)
     f, g = droplet_state(p, thermo, seed=11)
+    st_o, fo, go = Oracle(p).step(f.astype(np.float64), g.astype(np.float64))
+    assert st_o == 0
+    fh, gh = host_run(H, p, f, g, 1)
+    assert pop_err(fh, fo, thermo) < 1e-5
+    assert pop_err(gh, go, thermo) < 1e-5
+
+
+def test_per_node_face_temperature_field(H, thermo):
+    """A per-node temperature on the bottom wall (as lbm_set_face_T gives it) against the
+    oracle given the same field."""
+    p = case_params("wall_bottom_open_top", thermo)
+    f, g = droplet_state(p, thermo, seed=13)
+    tz = thermo["Ts"] * (1.05 + 0.01 * W.uniform(3, p["nx"] * p["ny"]).reshape(p["ny"], p["nx"]))
+    o = Oracle(p)
+    o.set_face_T([None, None, None, None, f32(tz).astype(np.float64), None])
+    _, fo, go = o.step(f.astype(np.float64), g.astype(np.float64))
+    fh, gh = host_run(H, p, f, g, 1, tface={4: tz})
+    assert pop_err(gh, go, thermo) < 1e-5 and pop_err(fh, fo, thermo) < 1e-5
+
+
+# the general moment-space collision (rates other than s_q = s_pi = 1, or the printed m^eq rows)
+@pytest.mark.parametrize("rates", [dict(s_q=1.1, s_pi=0.9), dict(meq_printed=1), dict(s_q=0.7, s_pi=1.3, s_e=0.9)])
+@pytest.mark.parametrize("name", ["open_all", "walls_z", "periodic"])
+def test_one_step_general_collision_matches_oracle(H, name, rates, thermo):
+    p = dict(case_params(name, thermo), **rates)
+    f, g = droplet_state(p, thermo, seed=13)
     st_o, fo, go = Oracle(p).step(f.astype(np.float64), g.astype(np.float64))
     assert st_o == 0
     fh, gh = host_run(H, p, f, g, 1)
