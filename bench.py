@@ -333,20 +333,26 @@ def storage_cost(lbm, p, rho0, T0, stream, steps=2000, warmup=50):
     N = p["nx"] * p["ny"] * p["nz"]
     out = {"steps": steps}
     for name in ("f32", "f16", "f16local"):
-        lat = lbm.Lattice(dict(p, storage=STORAGE[name][0], schedule=lbm.SCHED_SLABS), rho_d, T_d,
-                          stream=stream.cuda_stream)
-        lat.lbm_step(warmup)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        lat.lbm_step(steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        st = lat.lbm_sync()
-        lat.close()
-        ms = e0.elapsed_time(e1) / steps
-        out[name] = {"mlups": N / (ms * 1e-3) / 1e6, "ms_per_step": ms} if st == lbm.OK else \
-            {"status": lbm.lbm_status_string(st)}
+        lat = None
+        try:
+            lat = lbm.Lattice(dict(p, storage=STORAGE[name][0], schedule=lbm.SCHED_SLABS), rho_d, T_d,
+                              stream=stream.cuda_stream)
+            lat.lbm_step(warmup)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            lat.lbm_step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st = lat.lbm_sync()
+            ms = e0.elapsed_time(e1) / steps
+            out[name] = {"mlups": N / (ms * 1e-3) / 1e6, "ms_per_step": ms} if st == lbm.OK else \
+                {"status": lbm.lbm_status_string(st)}
+        except Exception as exc:  # a form that fails is reported in its entry, not fatal to the line
+            out[name] = {"status": f"{type(exc).__name__}: {exc}"}
+        finally:
+            if lat is not None:
+                lat.close()
     if "mlups" in out["f32"] and "mlups" in out["f16local"]:
         out["f16local_over_f32"] = out["f16local"]["mlups"] / out["f32"]["mlups"]
     return out
