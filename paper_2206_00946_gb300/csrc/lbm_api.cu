@@ -589,21 +589,21 @@ void slab_plan_destroy(SlabPlan* S) {
   delete S;
 }
 
-int slab_plan_create(lbm_ctx* c) {
-  SlabPlan* S = new (std::nothrow) SlabPlan();
-  if (!S) return LBM_ERR_ARG;
-  const int nz = c->P.nz, plane = c->P.nx * c->P.ny;
-  int sp = env_int("LBM_SLAB_PLANES", 0);
-  if (sp <= 0) sp = std::max(3, (262144 + plane - 1) / plane);  // about 256 Ki cells per slab kernel
+// The host part of a slab plan: slabs of about sp planes (at least 3), which of them
+// hold face nodes, and the stage order (a topological order of the within-step
+// dependencies along the diagonal wavefront slab + lag(phase)).  Returns false if no
+// order exists (not reachable: the dependency graph is acyclic).
+bool slab_plan_layout(const Params& P, int sp, SlabPlan* S) {
+  const int nz = P.nz;
   sp = std::max(3, std::min(sp, nz));
   S->nslab = std::max(1, nz / sp);
+  S->zb.clear();
   for (int s = 0; s <= S->nslab; ++s) S->zb.push_back((int)((long long)nz * s / S->nslab));
   S->has_d.assign(S->nslab, 0);
   for (int s = 0; s < S->nslab; ++s)
     for (int z = S->zb[s]; z < S->zb[s + 1]; ++z)
-      if (plane_has_boundary(c->P, z)) S->has_d[s] = 1;
-  const bool zper = c->P.face_kind[4] == FACE_PERIODIC;
-  // topological order along the diagonal wavefront slab + lag(phase)
+      if (plane_has_boundary(P, z)) S->has_d[s] = 1;
+  const bool zper = P.face_kind[4] == FACE_PERIODIC;
   const int lag[SPH_N] = {0, 1, 2, 3};
   const int n = S->nslab;
   std::vector<char> placed(SPH_N * n, 0), exists(SPH_N * n, 1);
@@ -611,6 +611,7 @@ int slab_plan_create(lbm_ctx* c) {
   int total = 0;
   for (int k = 0; k < SPH_N * n; ++k) total += exists[k];
   std::vector<int> d;
+  S->order.clear();
   while ((int)S->order.size() < total) {
     int best = -1, bestkey = 1 << 30;
     for (int ph = SPH_N - 1; ph >= 0; --ph)
@@ -627,13 +628,24 @@ int slab_plan_create(lbm_ctx* c) {
           best = id;
         }
       }
-    if (best < 0) {
-      slab_plan_destroy(S);
-      return LBM_ERR_ARG;  // not reachable: the dependency graph is acyclic
-    }
+    if (best < 0) return false;
     placed[best] = 1;
     S->order.push_back(best);
   }
+  return true;
+}
+
+int slab_plan_create(lbm_ctx* c) {
+  SlabPlan* S = new (std::nothrow) SlabPlan();
+  if (!S) return LBM_ERR_ARG;
+  const int plane = c->P.nx * c->P.ny;
+  int sp = env_int("LBM_SLAB_PLANES", 0);
+  if (sp <= 0) sp = std::max(3, (262144 + plane - 1) / plane);  // about 256 Ki cells per slab kernel
+  if (!slab_plan_layout(c->P, sp, S)) {
+    slab_plan_destroy(S);
+    return LBM_ERR_ARG;
+  }
+  const int n = S->nslab;
   S->nstreams = std::max(1, std::min(kMaxSlabStreams, env_int("LBM_SLAB_STREAMS", 8)));
   bool ok = cudaEventCreateWithFlags(&S->fork, cudaEventDisableTiming) == cudaSuccess;
   for (int i = 0; i < S->nstreams && ok; ++i) {
@@ -642,7 +654,8 @@ int slab_plan_create(lbm_ctx* c) {
   }
   S->ev.assign(SPH_N * n, nullptr);
   for (int k = 0; k < SPH_N * n && ok; ++k)
-    if (exists[k]) ok = cudaEventCreateWithFlags(&S->ev[k], cudaEventDisableTiming) == cudaSuccess;
+    if (k / n != SPH_D || S->has_d[k % n])  // the stages that exist
+      ok = cudaEventCreateWithFlags(&S->ev[k], cudaEventDisableTiming) == cudaSuccess;
   S->graph_steps = std::max(0, env_int("LBM_GRAPH_STEPS", 8));
   if (S->graph_steps & 1) S->graph_steps += 1;  // even: the buffers return to their parity
   c->slabs = S;

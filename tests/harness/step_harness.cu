@@ -113,3 +113,37 @@ int h_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps, fl
   }
 }
 }
+
+extern "C" {
+// The slab plan of lattice hp with slabs of about sp planes (the host part of the
+// pipelined schedule): *nslab slabs with plane bounds zb[0..nslab], the stage order
+// (stage code = phase * nslab + slab; phases A, BC19, C7, D = 0..3), for every stage
+// code the stages of the same step it waits for (deps_within, 8 per code, -1 padded),
+// and for every slab the stages of the previous step its phase A waits for
+// (deps_prev, 8 per slab, -1 padded).  max_slab bounds the arrays: zb holds max_slab + 1,
+// order and deps_within 4 * max_slab (x 8), deps_prev max_slab x 8.  Returns 0 or -1.
+int h_slab_plan(const lbm_params* hp, int sp, int max_slab, int* nslab, int* zb, int* order, int* norder,
+                int* deps_within, int* deps_prev) {
+  if (check_params(hp) != LBM_OK) return -1;
+  const Params P = make_device_params(*hp);
+  SlabPlan S;
+  if (!slab_plan_layout(P, sp, &S) || S.nslab > max_slab) return -1;
+  const bool zper = P.face_kind[4] == FACE_PERIODIC;
+  *nslab = S.nslab;
+  for (int s = 0; s <= S.nslab; ++s) zb[s] = S.zb[s];
+  *norder = (int)S.order.size();
+  for (size_t k = 0; k < S.order.size(); ++k) order[k] = S.order[k];
+  std::vector<int> d;
+  for (int code = 0; code < SPH_N * S.nslab; ++code) {
+    slab_deps_within(S, zper, code / S.nslab, code % S.nslab, d);
+    if (d.size() > 8) return -1;
+    for (int k = 0; k < 8; ++k) deps_within[code * 8 + k] = k < (int)d.size() ? d[k] : -1;
+  }
+  for (int s = 0; s < S.nslab; ++s) {
+    slab_deps_prev(S, zper, s, d);
+    if (d.size() > 8) return -1;
+    for (int k = 0; k < 8; ++k) deps_prev[s * 8 + k] = k < (int)d.size() ? d[k] : -1;
+  }
+  return 0;
+}
+}

@@ -197,3 +197,109 @@ def test_per_cell_references_meet_1e3_on_the_slab(H, thermo):
     print(f"1000 slab steps, relative L2 rho / T: FP16 per-cell {el}, FP16 global {eg}")
     assert el[0] < 1e-3 and el[1] < 1e-4
     assert eg[0] > 1e-3
+
+
+# ------------------------------------------------------- slab pipeline order --
+# The slab schedule runs every phase per z-slab on several streams; a stage waits
+# for other stages only through the dependency lists of the plan (and through the
+# order of its own stream).  This replays two consecutive steps of the plan the
+# library builds and checks, against the planes each phase kernel reads and writes,
+# that every pair of conflicting stages is ordered.
+
+A_, BC19_, C7_, D_ = 0, 1, 2, 3
+N_STREAMS = 8  # the default number of slab streams; slab s runs on stream s % 8
+
+
+def slab_plan(H, p, sp, max_slab=64):
+    P = lbm.make_params(dict(p, schedule=lbm.SCHED_SLABS))
+    nslab, norder = ct.c_int(), ct.c_int()
+    zb = np.zeros(max_slab + 1, np.int32)
+    order = np.zeros(4 * max_slab, np.int32)
+    dw = np.zeros(4 * max_slab * 8, np.int32)
+    dp = np.zeros(max_slab * 8, np.int32)
+    H.h_slab_plan.argtypes = [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                              ct.c_void_p, ct.c_void_p]
+    assert H.h_slab_plan(ct.byref(P), sp, max_slab, ct.byref(nslab), zb.ctypes.data, order.ctypes.data,
+                         ct.byref(norder), dw.ctypes.data, dp.ctypes.data) == 0
+    n = nslab.value
+    within = {c: [q for q in dw[c * 8:(c + 1) * 8] if q >= 0] for c in range(4 * n)}
+    prev = {s: [q for q in dp[s * 8:(s + 1) * 8] if q >= 0] for s in range(n)}
+    return n, list(zb[:n + 1]), list(order[:norder.value]), within, prev
+
+
+def stage_access(ph, s, t, zb, nz, zper):
+    """(resource, mode, planes) of stage (phase ph, slab s) in step t: what its kernel reads ('r')
+    and writes ('w').  'p' marks the writes of the streaming pushes: every (direction,
+    destination) has exactly one source cell, so two pushes never write the same element.
+    Buffers by absolute index: step t reads populations a = t % 2 and writes b."""
+    a, b = t % 2, 1 - t % 2
+    own = set(range(zb[s], zb[s + 1]))
+    halo = set(own)
+    for z in (zb[s] - 1, zb[s + 1]):
+        if 0 <= z < nz:
+            halo.add(z)
+        elif zper:
+            halo.add(z % nz)
+    if ph == A_:
+        return [(f"f{a}", "r", own), (f"g{a}", "r", own), (f"ref{a}", "r", own),
+                ("rho", "w", own), ("psi", "w", own), (f"ref{b}", "w", own)]
+    if ph == BC19_:  # force from the psi stencil; collide; push (with the destinations' rho)
+        return [("psi", "r", halo), ("rho", "r", halo), (f"f{a}", "r", own), (f"ref{a}", "r", own),
+                ("F", "w", own), ("u", "w", own), (f"f{b}", "p", halo)]
+    if ph == C7_:  # div u stencil; destinations' old g, rho and references; relaxed push
+        return [("u", "r", halo), ("rho", "r", halo), (f"ref{a}", "r", halo), (f"ref{b}", "r", halo),
+                (f"g{a}", "r", halo), ("T12", "r", own), ("T12", "w", own), (f"g{b}", "p", halo)]
+    return [(f"f{b}", "r", own), (f"g{b}", "r", own), ("F", "r", own), (f"ref{b}", "r", own),
+            (f"f{b}", "w", own), (f"g{b}", "w", own)]
+
+
+def unordered_conflicts(n, zb, order, within, prev, nz, zper):
+    seq = [(t, code) for t in (0, 1) for code in order]
+    pos = {st: i for i, st in enumerate(seq)}
+    preds = {st: set() for st in seq}
+    for t, code in seq:
+        for q in within[code]:
+            preds[(t, code)].add((t, q))
+        if t == 1 and code // n == A_:
+            for q in prev[code % n]:
+                preds[(t, code)].add((0, q))
+    last_on_stream = {}
+    for st in seq:  # the order of each stream
+        k = (st[1] % n) % N_STREAMS
+        if k in last_on_stream:
+            preds[st].add(last_on_stream[k])
+        last_on_stream[k] = st
+    before = {}
+    for st in seq:  # every stage that is ordered before st
+        acc = set()
+        for q in preds[st]:
+            assert pos[q] < pos[st]
+            acc.add(q)
+            acc |= before[q]
+        before[st] = acc
+    acc = {st: stage_access(st[1] // n, st[1] % n, st[0], zb, nz, zper) for st in seq}
+    bad = []
+    for i, x in enumerate(seq):
+        for y in seq[i + 1:]:
+            if x in before[y]:
+                continue
+            for rx, mx, px in acc[x]:
+                for ry, my, py in acc[y]:
+                    if rx == ry and {mx, my} != {"r"} and {mx, my} != {"p"} and px & py:
+                        bad.append((x, y, rx))
+    return bad
+
+
+@pytest.mark.parametrize("faces_z", [0, 1, 2])
+@pytest.mark.parametrize("nz,sp", [(9, 3), (12, 3), (13, 4), (40, 5), (6, 3), (3, 3), (64, 3)])
+def test_slab_pipeline_orders_every_conflict(H, faces_z, nz, sp, thermo):
+    """Periodic, wall and open z faces; one to twenty-one slabs (with periodic z, one or two
+    slabs make a slab its own neighbour)."""
+    kinds = {0: [0, 0, 0, 0, 0, 0], 1: [0, 0, 0, 0, 1, 1], 2: [2, 2, 0, 0, 2, 2]}[faces_z]
+    p = W.base_params(5, 4, nz, rho_l=thermo["rho_l"], rho_v=thermo["rho_v"], face_kind=kinds,
+                      face_T=[thermo["Ts"]] * 6, face_rho=[thermo["rho_v"]] * 6)
+    n, zb, order, within, prev = slab_plan(H, p, sp)
+    assert len(set(order)) == len(order) and all(0 <= c < 4 * n for c in order)
+    assert {c for c in order if c // n != D_} == {c for c in range(3 * n)}  # every A, BC19, C7 stage once
+    bad = unordered_conflicts(n, zb, order, within, prev, nz, faces_z == 0)
+    assert not bad, bad[:5]
