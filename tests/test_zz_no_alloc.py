@@ -3,8 +3,10 @@
 Some callers cannot call cudaMalloc when they want these diagnostics (their
 device memory is all handed out by their own pool, or they are a plug-in that
 only receives device pointers); lbm_reduce_static serves them from a fixed
-scratch array inside the library.  This file is collected last so that a run
-stopping at its first failure has already run every other test.
+scratch array inside the library.  This file is collected after every other
+test file, so that a run stopping at its first failure has already run the rest
+of the suite; only the cases of the FP16 storage with per-cell references, which
+the suite's configuration moves to the very end, run after it.
 """
 import numpy as np
 import pytest
