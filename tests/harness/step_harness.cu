@@ -147,3 +147,31 @@ int h_slab_plan(const lbm_params* hp, int sp, int max_slab, int* nslab, int* zb,
   return 0;
 }
 }
+
+extern "C" {
+// The persistent schedule's stage order for lattice hp with the given gap (stage code =
+// phase << 24 | plane, phases A, B, C, D = 0..3) into order (capacity cap); *n receives
+// the count.  deps (8 per stage code, -1 padded, indexed phase * nz + plane) lists the
+// stage codes each stage waits for.  Returns 0 or -1.
+int h_fused_plan(const lbm_params* hp, int gap, int cap, int* order, int* n, int* deps) {
+  if (check_params(hp) != LBM_OK) return -1;
+  const Params P = make_device_params(*hp);
+  const std::vector<int> o = fused_order(P, gap);
+  if ((int)o.size() > cap) return -1;
+  *n = (int)o.size();
+  for (size_t k = 0; k < o.size(); ++k) order[k] = o[k];
+  for (int ph = 0; ph < 4; ++ph)
+    for (int z = 0; z < P.nz; ++z) {
+      int* d = deps + (ph * P.nz + z) * 8;
+      int m = 0;
+      const int r = dep_radius(ph);
+      for (int k = -r; r > 0 && k <= r; ++k) {
+        bool valid;
+        const int q = dep_plane(P, z, k, valid);
+        if (valid && m < 8) d[m++] = ((ph - 1) << 24) | q;
+      }
+      for (; m < 8; ++m) d[m] = -1;
+    }
+  return 0;
+}
+}

@@ -303,3 +303,88 @@ def test_slab_pipeline_orders_every_conflict(H, faces_z, nz, sp, thermo):
     assert {c for c in order if c // n != D_} == {c for c in range(3 * n)}  # every A, BC19, C7 stage once
     bad = unordered_conflicts(n, zb, order, within, prev, nz, faces_z == 0)
     assert not bad, bad[:5]
+
+
+# ------------------------------------------------- persistent schedule order --
+def fused_access(ph, z, nz, zper, faces_z):
+    """(resource, mode, planes) of the persistent schedule's stage (phase ph, plane z); phase C
+    is the D3Q19 and the D3Q7 collide/push of the plane.  'p': streaming pushes (disjoint).
+    Phase D rewrites face nodes ('@bnd') and reads g at their inward neighbours x_b - sum n,
+    which lie strictly inside along every face normal of x_b and so are never face nodes
+    ('@inw'); the two parts do not overlap."""
+    def planes(k):
+        out = set()
+        for d in range(-k, k + 1):
+            q = z + d
+            if 0 <= q < nz:
+                out.add(q)
+            elif zper:
+                out.add(q % nz)
+        return out
+    own, n1 = {z}, planes(1)
+    if ph == 0:
+        return [("f", "r", own), ("g", "r", own), ("rho", "w", own), ("psi", "w", own), ("j", "w", own)]
+    if ph == 1:
+        return [("psi", "r", n1), ("rho", "r", own), ("j", "r", own), ("F", "w", own), ("u", "w", own)]
+    if ph == 2:
+        return [("f", "r", own), ("F", "r", own), ("fB", "p", n1), ("g", "r", n1), ("rho", "r", n1),
+                ("u", "r", n1), ("gB", "p", n1)]
+    inward = n1 if faces_z else own  # a z-face node's inward neighbour is on the next plane
+    return [("fB@bnd", "r", own), ("gB@inw", "r", inward), ("F", "r", own), ("fB@bnd", "w", own),
+            ("gB@bnd", "w", own)]
+
+
+def _same(rx, ry):
+    """Resources overlap: the same buffer, and the same part unless one is the whole buffer."""
+    bx, _, px = rx.partition("@")
+    by, _, py = ry.partition("@")
+    return bx == by and (px == py or not px or not py)
+
+
+@pytest.mark.parametrize("gap", [0, 3, 9])
+@pytest.mark.parametrize("faces", [(0, 0), (0, 1), (2, 2), (1, 0)])
+@pytest.mark.parametrize("nz", [3, 4, 7, 16])
+def test_fused_plan_is_dispensable_and_orders_every_conflict(H, faces, nz, gap, thermo):
+    """Every stage of the persistent kernel's order waits only for stages dispensed before it
+    (so the earliest unfinished item can always run: no deadlock), and the dependency radii
+    order every pair of conflicting stages of one step.  faces: (x/y kind, z kind)."""
+    fxy, fz = faces
+    kinds = [fxy, fxy, fxy, fxy, fz, fz]
+    p = W.base_params(5, 4, nz, rho_l=thermo["rho_l"], rho_v=thermo["rho_v"], face_kind=kinds,
+                      face_T=[thermo["Ts"]] * 6, face_rho=[thermo["rho_v"]] * 6)
+    if fxy == 1 and fz == 2:
+        pytest.skip("a wall face may not share an edge with an open face")
+    P = lbm.make_params(dict(p, schedule=lbm.SCHED_FUSED))
+    cap = 4 * nz
+    order = np.zeros(cap, np.int32)
+    deps = np.zeros(cap * 8, np.int32)
+    n = ct.c_int()
+    H.h_fused_plan.argtypes = [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p]
+    assert H.h_fused_plan(ct.byref(P), gap, cap, order.ctypes.data, ct.byref(n), deps.ctypes.data) == 0
+    seq = [int(c) for c in order[:n.value]]
+    assert len(set(seq)) == len(seq)
+    pos = {c: i for i, c in enumerate(seq)}
+    for ph in range(3):  # phases A, B, C of every plane; D where the plane holds face nodes
+        assert all((ph << 24 | z) in pos for z in range(nz))
+    wait = {c: [int(q) for q in deps[((c >> 24) * nz + (c & 0xffffff)) * 8:][:8] if q >= 0] for c in seq}
+    for c in seq:
+        for q in wait[c]:
+            assert q in pos and pos[q] < pos[c], (c, q)
+    before = {}
+    for c in seq:
+        acc = set()
+        for q in wait[c]:
+            acc |= {q} | before[q]
+        before[c] = acc
+    zper = fz == 0
+    access = {c: fused_access(c >> 24, c & 0xffffff, nz, zper, fz != 0) for c in seq}
+    bad = []
+    for i, x in enumerate(seq):
+        for y in seq[i + 1:]:
+            if x in before[y] or y in before[x]:
+                continue
+            for rx, mx, px in access[x]:
+                for ry, my, py in access[y]:
+                    if _same(rx, ry) and {mx, my} != {"r"} and {mx, my} != {"p"} and px & py:
+                        bad.append((hex(x), hex(y), rx))
+    assert not bad, bad[:5]
