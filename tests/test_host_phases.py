@@ -9,6 +9,10 @@ kernels' code therefore show up without a GPU.  The arithmetic differs from the
 GPU's only in the reciprocals (a correctly rounded division here, the fast
 intrinsic there) and in the contraction of multiply-adds, so the FP32 tolerance
 of the GPU parity tests applies.
+
+The same harness exposes the host part of the two pipelined schedules (the slab
+plan and the persistent kernel's stage order), whose ordering of conflicting
+stages is checked at the end of this file.
 """
 import ctypes as ct
 import os
