@@ -4,7 +4,9 @@
 // (A for every cell, then force + D3Q19 collide/push, then D3Q7
 // collide/push, then the boundary rules on the face nodes), with the
 // double-buffered populations in any storage form.  CPU tests compare it with
-// the FP64 oracle before any GPU run.  Test infrastructure only.
+// the FP64 oracle before any GPU run.  It also exposes the host part of the slab
+// pipeline and of the persistent kernel (their stage orders and dependency lists)
+// for the CPU checks of their ordering.  Test infrastructure only.
 #define LBM_HOST_PHASES
 #include "lbm_api.cu"
 
