@@ -48,6 +48,9 @@ def test_params_struct_matches_header():
     dict(face_kind=[0, 0, 0, 0, 2, 2], face_rho=[0] * 6),
     dict(wbar=1.5),
     dict(storage=7),
+    dict(storage=4),
+    dict(storage=3, schedule=0),          # 16-bit storage in the persistent schedule (FP32 only)
+    dict(storage=1, schedule=0),
     dict(nz=2, face_kind=[0, 0, 0, 0, 1, 1]),
 ])
 def test_invalid_parameters_rejected_before_any_device_work(bad):

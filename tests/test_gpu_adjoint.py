@@ -14,6 +14,7 @@ not divide the step count).
 import numpy as np
 import pytest
 
+from cases import F16_LOCAL
 from oracle import Oracle
 from oracle.torch_step import TorchStep
 from paper_2206_00946_gb300 import lbm
@@ -161,9 +162,10 @@ def test_record_leaves_the_same_state_as_stepping(schedule, thermo):
     b.close()
 
 
-def test_record_rejects_16bit_storage(thermo):
+@pytest.mark.parametrize("storage", [lbm.STORE_F16_SHIFTED, F16_LOCAL])
+def test_record_rejects_16bit_storage(storage, thermo):
     p, rho0, T0, face, Tb, wT = _case("open", thermo)
-    lat = lbm.Lattice(dict(p, storage=lbm.STORE_F16_SHIFTED, schedule=lbm.SCHED_PHASES),
+    lat = lbm.Lattice(dict(p, storage=storage, schedule=lbm.SCHED_PHASES),
                       rho0.astype(np.float32), T0.astype(np.float32))
     with pytest.raises(lbm.LBMError) as e:
         lat.lbm_record(4, 2)

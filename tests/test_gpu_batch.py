@@ -10,6 +10,7 @@ states unchanged; errors of one domain surface through lbm_batch_sync.
 import numpy as np
 import pytest
 
+from cases import F16_LOCAL
 from paper_2206_00946_gb300 import lbm
 from paper_2206_00946_gb300 import workloads as W
 
@@ -109,9 +110,10 @@ def test_batch_reports_a_domain_error(thermo):
         lat.close()
 
 
-def test_batch_rejects_16bit_storage(thermo):
+@pytest.mark.parametrize("storage", [lbm.STORE_F16_SHIFTED, F16_LOCAL])
+def test_batch_rejects_16bit_storage(storage, thermo):
     p, rho0, T0 = _domains(thermo)[0]
-    lat = lbm.Lattice(dict(p, schedule=lbm.SCHED_PHASES, storage=lbm.STORE_F16_SHIFTED),
+    lat = lbm.Lattice(dict(p, schedule=lbm.SCHED_PHASES, storage=storage),
                       rho0.reshape(-1).astype(np.float32), T0.reshape(-1).astype(np.float32))
     with pytest.raises(lbm.LBMError):
         lbm.Batch([lat])
