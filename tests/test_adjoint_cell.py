@@ -6,32 +6,22 @@ random cotangents b and directions v, <b, J v> from central differences of
 the forward must equal <VJP(b), v>.
 """
 import ctypes as ct
-import os
-import shutil
-import subprocess
-import tempfile
 
 import numpy as np
 import pytest
 
+import harness_build
 from oracle import Oracle
 from paper_2206_00946_gb300 import workloads as W
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-CSRC = os.path.join(ROOT, "paper_2206_00946_gb300", "csrc")
 DP = ct.POINTER(ct.c_double)
 
 
 @pytest.fixture(scope="module")
 def H():
-    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
-    if not os.path.exists(nvcc):
+    if not harness_build.nvcc():
         pytest.skip("nvcc not available")
-    d = tempfile.mkdtemp()
-    so = os.path.join(d, "adjoint_harness.so")
-    subprocess.run([nvcc, "-std=c++17", "-O2", "-shared", "-Xcompiler", "-fPIC", "-I", CSRC,
-                    os.path.join(ROOT, "tests", "harness", "adjoint_harness.cu"), "-o", so], check=True)
-    L = ct.CDLL(so)
+    L = ct.CDLL(harness_build.build_harness("adjoint_harness"))
     for n in ("a_eos", "a_eos_vjp"):
         getattr(L, n).argtypes = [DP, ct.POINTER(ct.c_int), ct.c_double, ct.c_double] + \
             ([DP] if n == "a_eos" else [ct.c_double, ct.c_double, DP])

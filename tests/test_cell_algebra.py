@@ -6,31 +6,20 @@ and the EOS of csrc/lbm_cell.cuh are compiled for the host by nvcc and
 compared cell by cell, so that algebra mistakes show up before any GPU run.
 """
 import ctypes as ct
-import os
-import shutil
-import subprocess
-import tempfile
 
 import numpy as np
 import pytest
 
+import harness_build
 from oracle import Oracle, feq19 as ofeq19
 from paper_2206_00946_gb300 import workloads as W
-
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-CSRC = os.path.join(ROOT, "paper_2206_00946_gb300", "csrc")
 
 
 @pytest.fixture(scope="module")
 def H():
-    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
-    if not os.path.exists(nvcc):
+    if not harness_build.nvcc():
         pytest.skip("nvcc not available")
-    d = tempfile.mkdtemp()
-    so = os.path.join(d, "cell_harness.so")
-    subprocess.run([nvcc, "-std=c++17", "-O2", "-shared", "-Xcompiler", "-fPIC", "-I", CSRC,
-                    os.path.join(ROOT, "tests", "harness", "cell_harness.cu"), "-o", so], check=True)
-    return ct.CDLL(so)
+    return ct.CDLL(harness_build.build_harness("cell_harness"))
 
 
 def _fp(a):

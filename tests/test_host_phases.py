@@ -15,34 +15,22 @@ plan and the persistent kernel's stage order), whose ordering of conflicting
 stages is checked at the end of this file.
 """
 import ctypes as ct
-import os
-import shutil
-import subprocess
-import tempfile
 
 import numpy as np
 import pytest
 
+import harness_build
 from cases import (CASES, HALF_ULP, STORAGES_16, W7, _face_nodes, _local_refs, _storage_bound_ok, case_params,
                    droplet_state, f32, pop_err)
 from oracle import Oracle
 from paper_2206_00946_gb300 import lbm, workloads as W
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-CSRC = os.path.join(ROOT, "paper_2206_00946_gb300", "csrc")
-
 
 @pytest.fixture(scope="module")
 def H():
-    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
-    if not os.path.exists(nvcc):
+    if not harness_build.nvcc():
         pytest.skip("nvcc not available")
-    d = tempfile.mkdtemp()
-    so = os.path.join(d, "step_harness.so")
-    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-O2", "-shared",
-                    "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
-                    os.path.join(ROOT, "tests", "harness", "step_harness.cu"), "-o", so], check=True)
-    L = ct.CDLL(so)
+    L = ct.CDLL(harness_build.build_harness("step_harness", ("-gencode", "arch=compute_103a,code=sm_103a")))
     L.h_run.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p]
     return L
 
