@@ -100,6 +100,25 @@ def slab(Tc, rho_v, rho_l, nx=16, ny=16, nz=64, W=2.0, dT_bottom=0.02, lam=(0.4,
     return p, rho0, T0
 
 
+def conduction_column(Tc, rho_v, rho_l, L=40, W=4.0, Th_frac=1.0, Ts_frac=0.86, lam=(0.4, 0.2), cv=5.0):
+    """Saturated liquid-vapour column of Sec. 4.1, reduced to 1 x 1 x L (the paper's
+    200 x 10 x 10 is periodic in the two short directions, so y,z-uniform data make it
+    one-dimensional; the column runs along z here).
+
+    Vapour fills z < L/2 next to the hot wall z = 0 (Th_frac Tc), liquid the upper half
+    next to the wall at T_s; tanh profile of width W between the coexistence densities,
+    everything initially at T_s; conductivities lam = (liquid, vapour).
+    """
+    Ts = Ts_frac * Tc
+    z = np.arange(L, dtype=np.float64) + 0.5
+    rho0 = tanh_profile(L / 2.0 - z, rho_v, rho_l, W).reshape(L, 1, 1)
+    T0 = np.full_like(rho0, Ts)
+    p = base_params(1, 1, L, rho_l=rho_l, rho_v=rho_v, lambda_l=lam[0], lambda_v=lam[1], cv=cv,
+                    face_kind=[PERIODIC, PERIODIC, PERIODIC, PERIODIC, WALL, WALL],
+                    face_T=[0, 0, 0, 0, Th_frac * Tc, Ts])
+    return p, rho0, T0
+
+
 def droplet(Tc, rho_v, rho_l, n=128, R=15.0, W=5.0, seed=2206, amp=1e-4, Ts_frac=0.86, Tg_frac=1.0,
             lam=1.0 / 3.0, faces=OPEN, shape=None):
     """Spherical droplet of radius R at the domain centre in vapor at coexistence density.

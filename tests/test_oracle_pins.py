@@ -700,3 +700,91 @@ def test_vartheta_one_removes_the_second_order_time_error_of_diffusion():
         rates.append(-np.log(a2 / a1) / 80)
     r0, r1 = rates
     assert abs((r0 - r1) - a * a / 2) < 0.15 * a * a / 2, (r0, r1, a)
+
+
+# ----------------------------------------- Sec. 4.1: two-phase conduction ----
+
+def _steady_column(thermo, cv, tol=1e-10, chunk=50000, cap=1_500_000):
+    """The Sec. 4.1 column run until T changes by less than tol per 1000 steps."""
+    p, rho0, T0 = W.conduction_column(thermo["Tc"], thermo["rho_v"], thermo["rho_l"], cv=cv)
+    o = Oracle(p)
+    f, g = o.init_state(rho0, T0)
+    T = g.sum(0)
+    for n in range(chunk, cap + 1, chunk):
+        st, f, g = o.run(f, g, chunk)
+        assert st == 0
+        Tn = g.sum(0)
+        res = np.abs(Tn - T).max() * 1000 / chunk
+        T = Tn
+        if res < tol:
+            break
+    st, m = o.macros(f, g)
+    assert st == 0
+    return p, m, res
+
+
+@pytest.mark.slow
+def test_sec41_two_phase_conduction_reaches_the_fourier_profile(thermo):
+    """Sec. 4.1: vapour next to a wall at T_c, liquid next to a wall at T_s (λ_l = 0.4,
+    λ_v = 0.2).  At the steady state heat crosses the interface without sources, so the
+    flux λ ∂T/∂z is the same everywhere (Fourier's law, continuity of flux): the bulk slope
+    ratio vapour : liquid is λ_l : λ_v = 2 (the paper reports 1.9507), and the profile is
+    T_h - (T_h - T_s) ∫dz/λ / ∫_0^L dz/λ with the model's λ(ρ).  The steady profile does
+    not depend on c_v (the paper's remark).  The column is shortened from 200 to 40 cells
+    so that the steady state (time ~ L^2) is reached in 0.5 M steps."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    with ThreadPoolExecutor(2) as ex:  # the oracle releases the GIL
+        runs = list(ex.map(lambda cv: _steady_column(thermo, cv), (5.0, 3.0)))
+    (p, m, res), (_, m3, res3) = runs
+    assert res < 1e-10 and res3 < 1e-10
+    T, rho, L = m["T"], m["rho"], p["nz"]
+    Tc, Ts = thermo["Tc"], thermo["Ts"]
+    assert abs(T[0] - Tc) < 1e-12 and abs(T[-1] - Ts) < 1e-12
+    assert np.abs(m["uz"]).max() < 1e-10
+    # bulk slopes away from the walls and 2W from the interface
+    z = np.arange(L, dtype=float)
+    zi = np.interp(0.5 * (thermo["rho_v"] + thermo["rho_l"]), rho, z)
+    vap, liq = (z >= 2) & (z <= zi - 8), (z >= zi + 8) & (z <= L - 3)
+    ratio = np.polyfit(z[vap], T[vap], 1)[0] / np.polyfit(z[liq], T[liq], 1)[0]
+    assert 1.90 <= ratio <= 2.05, ratio
+    # Fourier's law with the conductivity field of the model
+    lam = p["lambda_v"] + (p["lambda_l"] - p["lambda_v"]) * W.liquid_fraction(rho, p["rho_v"], p["rho_l"])
+    J = -lam[1:-1] * (T[2:] - T[:-2]) / 2
+    assert np.ptp(J) < 0.02 * J.mean() and J.min() > 0
+    R = np.concatenate([[0.0], np.cumsum(0.5 * (1 / lam[1:] + 1 / lam[:-1]))])
+    T_an = Tc - (Tc - Ts) * R / R[-1]
+    assert np.abs(T - T_an).max() < 5e-3 * (Tc - Ts)
+    # independent of c_v
+    np.testing.assert_allclose(m3["T"], T, rtol=2e-6)
+    np.testing.assert_allclose(m3["rho"], rho, rtol=2e-6)
+
+
+def test_heat_balance_of_eq12_at_rest_with_uniform_psi(thermo):
+    """Eq. 12 integrated over a periodic box: ∫ρ c_v ∂T/∂t dV = -∫F̄ dV, since ∇·(λ∇T)
+    integrates to zero.  A state at rest whose temperature makes p_EOS - ρ/3, hence ψ,
+    uniform has F = 0 (Eq. 6), u = 0 and F̄ = 0, while T and ρ vary; so one step must keep
+    Σ ρ(t) c_v (T(t+1) - T(t)) = 0 while heat moves between cells.  This fixes where ρ c_v
+    is taken in Eq. 13 (reading A8, the destination node): at the source node the sum is
+    off by terms of order |∇ρ| |∇T|."""
+    n = 6
+    x, y, z = W.grid(n, n, n)
+    k = 2 * np.pi / n
+    rho = thermo["rho_v"] * (1.0 + 0.02 * np.sin(k * x) + 0.015 * np.cos(k * y) * np.sin(k * z))
+    p = W.base_params(n, n, n, rho_v=thermo["rho_v"], rho_l=thermo["rho_l"], lambda_l=0.4, lambda_v=0.2)
+    o = Oracle(p)
+    K = o.p_eos(thermo["rho_v"], thermo["Ts"]) - thermo["rho_v"] / 3
+    T = np.full(rho.size, thermo["Ts"])
+    for c, r in enumerate(rho.reshape(-1)):  # Newton on p(ρ, T) - ρ/3 = K
+        for _ in range(30):
+            T[c] -= (o.p_eos(r, T[c]) - r / 3 - K) / o.dpdT(r, T[c])
+    assert 0.7 < T.min() / thermo["Tc"] and T.max() / thermo["Tc"] < 1.0
+    f, g = o.init_state(rho, T)
+    st, f1, g1, d = o.step(f, g, diag=True)
+    assert st == 0
+    assert np.abs(d["psi"] - d["psi"].mean()).max() < 1e-13 * d["psi"].mean()
+    assert max(np.abs(d[q]).max() for q in ("Fx", "Fy", "Fz", "ux", "uy", "uz")) < 1e-15
+    dT = g1.sum(0) - g.sum(0)
+    w = d["rho"] * p["cv"]
+    assert np.abs(dT).max() > 1e-6 * thermo["Ts"]  # heat does move
+    assert abs(np.sum(w * dT)) < 1e-12 * np.sum(np.abs(w * dT))
