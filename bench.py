@@ -1,27 +1,32 @@
 #!/usr/bin/env python3
 """Benchmark of the fused D3Q19 + D3Q7 time step (thermal pseudopotential MRT-LBM, arXiv 2206.00946).
 
-Workload (one "step" = one lattice-Boltzmann time step over the whole domain):
-d^2-law droplet on a 128^3 lattice, radius 15, seeded +-1e-4 density noise,
-constant-pressure faces on all six sides (rho_b = rho_v), T = T_c on the faces,
-FP32 populations.  Metric: million lattice updates per second (MLUPS), whole
-job, and the fraction of the measured HBM copy bandwidth that the 208 bytes of
-algorithmic traffic per lattice update reach.
+Workload (one "step" = one lattice-Boltzmann time step over the whole domain),
+by default the heated-surface droplet: a 256 x 256 x 128 lattice, hemispherical
+droplet of radius 30 on a bounce-back bottom wall at 0.96 T_c (contact angle
+90 degrees), constant-pressure top face (rho_b = rho_v, T_s), periodic in x
+and y, FP32 populations (1.75 GB double-buffered, far above L2).  Metric:
+million lattice updates per second (MLUPS), whole job, and the fraction of the
+measured HBM copy bandwidth that the 208 bytes of algorithmic traffic per
+lattice update reach.  --workload droplet selects the d^2-law droplet
+(128^3, radius 15, open faces on all six sides) instead.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--storage f32|f16|bf16|f16local] [--schedule slabs|phases|fused]
+                    [--workload sessile|droplet] [--storage f32|f16|bf16|f16local]
+                    [--schedule slabs|phases|fused]
 
 The JSON line also carries the roofline of the dominant kernel (each kernel timed
 alone with CUDA events in the phase schedule, charged its own algorithmic bytes),
 the end-to-end rate through host buffers, the FP64 CPU oracle on a bounded sample
-(cpu_baseline), the adjoint/forward cost on a 64^3 droplet over 2000 steps with
+on all host cores and on one (cpu_baseline), the 128^3 d^2-law droplet
+(droplet_128), the adjoint/forward cost on a 64^3 droplet over 2000 steps with
 checkpoints every 100 (adjoint), 48 uneven droplet domains stepped as one batch
 (batched), and the 512^3 heated-plate pool with 64 droplets in FP16-shifted
 storage (large), the step time with the correction term of Eq. 16
 (vartheta = 1) against without (vartheta), and the rate in each population
-storage form (storage_forms: FP32, FP16 with one global shift, FP16 with
-per-cell references); --no-adjoint / --no-batched / --no-large /
---no-vartheta / --no-storage / --no-cpu-baseline skip those.
+storage form (storage_forms: FP32, FP16 and BF16 with one global shift, FP16
+with per-cell references); --no-adjoint / --no-batched / --no-large /
+--no-vartheta / --no-storage / --no-droplet / --no-cpu-baseline skip those.
 
 N > 1 (torchrun, one rank per GPU) runs N independent replicas of the domain
 (weak scaling, no collective on the data path).  --impl reference times the
@@ -58,7 +63,18 @@ def kernel_alg_bytes(kernel: str, esize: int):
             "phaseC7": 2 * 7 * esize,   # D3Q7 collide + relaxed push: g read and written
             "phaseA": 26 * esize,       # macroscopic fields: f and g read
             "fused": 2 * 26 * esize}.get(kernel)
-WORKLOAD = "d2-law droplet 128^3, R=15, W=5, open (Zou-He) faces rho_b=rho_v, T_faces=T_c, seed 2206"
+WORKLOADS = {
+    "sessile": "droplet on a heated surface 256x256x128, R=30, W=5, bottom wall 0.96 T_c (theta 90), "
+               "open top rho_b=rho_v at T_s, periodic x/y",
+    "droplet": "d2-law droplet 128^3, R=15, W=5, open (Zou-He) faces rho_b=rho_v, T_faces=T_c, seed 2206",
+}
+
+
+def workload(name, Tc, rv, rl, n=None):
+    """(params, rho0, T0) of a named workload (n: side of the droplet lattice)."""
+    if name == "sessile":
+        return W.sessile(Tc, rv, rl)
+    return W.droplet(Tc, rv, rl, n=n or 128, R=15.0)
 
 
 def peaks():
@@ -324,15 +340,15 @@ def vartheta_cost(lbm, p, rho0, T0, stream, steps=2000, warmup=50):
 
 
 def storage_cost(lbm, p, rho0, T0, stream, steps=2000, warmup=50):
-    """MLUPS of the workload in each population storage form (slab schedule): FP32, FP16 with
-    one global shift, and FP16 with per-cell references.  A form whose run reports an error
+    """MLUPS of the workload in each population storage form (slab schedule): FP32, FP16 and
+    BF16 with one global shift, and FP16 with per-cell references.  A form whose run reports an error
     status is recorded with that status instead of a rate."""
     import torch
     rho_d = torch.tensor(rho0.reshape(-1), dtype=torch.float32, device="cuda")
     T_d = torch.tensor(T0.reshape(-1), dtype=torch.float32, device="cuda")
     N = p["nx"] * p["ny"] * p["nz"]
     out = {"steps": steps}
-    for name in ("f32", "f16", "f16local"):
+    for name in ("f32", "f16", "bf16", "f16local"):
         lat = None
         try:
             lat = lbm.Lattice(dict(p, storage=STORAGE[name][0], schedule=lbm.SCHED_SLABS), rho_d, T_d,
@@ -353,8 +369,9 @@ def storage_cost(lbm, p, rho0, T0, stream, steps=2000, warmup=50):
         finally:
             if lat is not None:
                 lat.close()
-    if "mlups" in out["f32"] and "mlups" in out["f16local"]:
-        out["f16local_over_f32"] = out["f16local"]["mlups"] / out["f32"]["mlups"]
+    for name in ("f16", "bf16", "f16local"):
+        if "mlups" in out["f32"] and "mlups" in out[name]:
+            out[f"{name}_over_f32"] = out[name]["mlups"] / out["f32"]["mlups"]
     return out
 
 
@@ -367,52 +384,98 @@ def thermo_product():
     return Tc, rv, rl
 
 
-def cpu_oracle_sample(p, rho0, T0, steps: int):
-    """Oracle (FP64, single thread, as it stands) on the workload for `steps` steps; returns MLUPS."""
+def cpu_oracle_sample(p, rho0, T0, steps: int, omp: bool = False):
+    """Oracle (FP64, as it stands; omp=True: the same source built with OpenMP over z, all
+    host cores) on the workload for `steps` steps; returns (MLUPS, seconds, threads)."""
     from oracle import Oracle
-    o = Oracle(p)
+    o = Oracle(p, omp=omp)
+    threads = o.threads()
     f, g = o.init_state(rho0, T0)
     t0 = time.perf_counter()
     st, f, g = o.run(f, g, steps)
     dt = time.perf_counter() - t0
-    return p["nx"] * p["ny"] * p["nz"] * steps / dt / 1e6, dt
+    return p["nx"] * p["ny"] * p["nz"] * steps / dt / 1e6, dt, threads
+
+
+def sub_box(p, rho0, T0, s, sz):
+    """A centred s x s x sz sub-box of a workload (z from the bottom: the wall and the
+    droplet stay in it), the same face kinds."""
+    nx, ny, nz = p["nx"], p["ny"], p["nz"]
+    s, sz = min(s, nx, ny), min(sz, nz)
+    x0, y0 = (nx - s) // 2, (ny - s) // 2
+    z0 = 0 if p["face_kind"][4] == W.WALL else (nz - sz) // 2
+    sl = (slice(z0, z0 + sz), slice(y0, y0 + s), slice(x0, x0 + s))
+    r, t = (np.ascontiguousarray(a.reshape(nz, ny, nx)[sl]) for a in (rho0, T0))
+    return dict(p, nx=s, ny=s, nz=sz), r, t
 
 
 def run_reference(args, rank, world):
-    """The oracle on host cores: each timed step one lattice update of a bounded sub-box of the workload."""
+    """The oracle on all host cores (its OpenMP build): each timed step one lattice update of
+    the workload, or of a centred sub-box of it when the whole run would exceed ~2 minutes."""
     if rank != 0:
         return 0
     from oracle import Oracle
     o0 = Oracle(W.base_params(4, 4, 4))
     Tc = o0.Tc()
     rv, rl, _ = o0.maxwell(0.86 * Tc)
-    p, rho0, T0 = W.droplet(Tc, rv, rl, n=128, R=15.0)
-    # sub-box around the droplet, sized so that warmup + steps take about two minutes
-    budget_s, us_per_lu = 120.0, 5.0
-    cells = max(8 ** 3, int(budget_s / (us_per_lu * 1e-6) / max(1, args.steps + args.warmup)))
-    s = int(round(cells ** (1.0 / 3.0)))
-    s = max(8, min(128, s))
-    lo = 64 - s // 2
-    sub = (slice(lo, lo + s),) * 3
-    q = dict(p, nx=s, ny=s, nz=s)
-    o = Oracle(q)
-    f, g = o.init_state(np.ascontiguousarray(rho0[sub]), np.ascontiguousarray(T0[sub]))
-    for _ in range(args.warmup):
-        _, f, g = o.step(f, g)
+    p, rho0, T0 = workload(args.workload, Tc, rv, rl)
+    # calibrate the rate on a small box, then size the sample to the budget
+    q, r, t = sub_box(p, rho0, T0, 32, 32)
+    rate, _, threads = cpu_oracle_sample(q, r, t, 2, omp=True)
+    budget_s = 120.0
+    cells = int(budget_s * rate * 1e6 / max(1, args.steps + args.warmup))
+    N = p["nx"] * p["ny"] * p["nz"]
+    if cells >= N:
+        q, r, t = p, rho0, T0
+        sample = f"the whole {args.workload} workload, one lattice update per timed step"
+    else:
+        frac = (cells / N) ** (1.0 / 3.0)
+        sxy = max(8, int(frac * min(p["nx"], p["ny"])))
+        sz = max(8, int(frac * p["nz"]))
+        q, r, t = sub_box(p, rho0, T0, sxy, sz)
+        sample = (f"{q['nx']}x{q['ny']}x{q['nz']} centred sub-box of the {args.workload} workload, "
+                  f"one lattice update per timed step")
+    o = Oracle(q, omp=True)
+    f, g = o.init_state(r, t)
+    _, f, g = o.run(f, g, args.warmup)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        _, f, g = o.step(f, g)
+    _, f, g = o.run(f, g, args.steps)
     dt = time.perf_counter() - t0
-    mlups = s ** 3 * args.steps / dt / 1e6
-    sample = f"{s}^3 sub-box at the droplet centre of the 128^3 workload, one lattice update per timed step"
+    mlups = q["nx"] * q["ny"] * q["nz"] * args.steps / dt / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
-            "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "sample": sample},
+            "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def droplet_rate(lbm, Tc, rv, rl, stream, steps=2000, warmup=50):
+    """Steady rate of the 128^3 d^2-law droplet (open faces on all six sides), slab schedule, FP32."""
+    import torch
+    p, rho0, T0 = workload("droplet", Tc, rv, rl)
+    p["schedule"] = lbm.SCHED_SLABS
+    N = p["nx"] * p["ny"] * p["nz"]
+    lat = lbm.Lattice(p, torch.tensor(rho0.reshape(-1), dtype=torch.float32, device="cuda"),
+                      torch.tensor(T0.reshape(-1), dtype=torch.float32, device="cuda"), stream=stream.cuda_stream)
+    lat.lbm_step(warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat.lbm_step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = lat.lbm_sync()
+    lat.close()
+    if st != lbm.OK:
+        raise SystemExit(f"droplet run failed: {lbm.lbm_status_string(st)}")
+    ms = e0.elapsed_time(e1) / steps
+    mlups = N / (ms * 1e-3) / 1e6
+    peak = peaks().get("hbm_gbs", 6800.0)
+    return {"workload": WORKLOADS["droplet"], "steps": steps, "value": mlups, "unit": UNIT, "ms_per_step": ms,
+            "step_frac": BYTES_PER_LU * mlups * 1e6 / 1e9 / peak}
 
 
 def main():
@@ -421,7 +484,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=128, help="lattice side (the workload is 128)")
+    ap.add_argument("--workload", default="sessile", choices=list(WORKLOADS))
+    ap.add_argument("--n", type=int, default=128, help="lattice side of the droplet workload (128)")
     ap.add_argument("--schedule", default="slabs", choices=["fused", "phases", "slabs"])
     ap.add_argument("--storage", default="f32", choices=list(STORAGE))
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -431,6 +495,7 @@ def main():
     ap.add_argument("--adjoint-side", type=int, default=64, help="cube side of the adjoint workload (64)")
     ap.add_argument("--no-vartheta", action="store_true", help="skip the vartheta = 1 cost measurement")
     ap.add_argument("--no-storage", action="store_true", help="skip the storage-form comparison")
+    ap.add_argument("--no-droplet", action="store_true", help="skip the 128^3 droplet rate")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = dist_env()
@@ -448,7 +513,7 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
 
     Tc, rv, rl = thermo_product()
-    p, rho0, T0 = W.droplet(Tc, rv, rl, n=args.n, R=15.0)
+    p, rho0, T0 = workload(args.workload, Tc, rv, rl, args.n)
     p["schedule"] = {"fused": lbm.SCHED_FUSED, "phases": lbm.SCHED_PHASES, "slabs": lbm.SCHED_SLABS}[args.schedule]
     p["storage"], esize = STORAGE[args.storage]
     step_bytes = 26 * 2 * esize  # algorithmic bytes per lattice update in this storage
@@ -538,6 +603,9 @@ def main():
     storage_forms = None
     if args.storage == "f32" and not args.no_storage:
         storage_forms = storage_cost(lbm, p, rho0, T0, stream)
+    droplet = None
+    if args.workload != "droplet" and not args.no_droplet:
+        droplet = droplet_rate(lbm, Tc, rv, rl, stream)
 
     if rank != 0:
         if dist:
@@ -553,15 +621,21 @@ def main():
     traffic = ncu_traffic(dom + ("" if args.storage == "f32" else "_" + args.storage), digest, N)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        steps_cpu = 2
-        mlups_cpu, dt = cpu_oracle_sample(p, rho0, T0, steps_cpu)
-        cpu = {"value": mlups_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{steps_cpu} full steps of the {args.n}^3 workload ({dt:.1f} s, single thread)"}
+        # the oracle as it stands on all host cores (OpenMP over z) and on one core, on whole
+        # steps of the same workload
+        mlups_omp, dt_omp, threads = cpu_oracle_sample(p, rho0, T0, 2, omp=True)
+        mlups_1, dt_1, _ = cpu_oracle_sample(p, rho0, T0, 1)
+        cpu = {"value": mlups_omp, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"2 full steps of the {args.workload} workload ({dt_omp:.1f} s, OpenMP over z, "
+                         f"{threads} threads)",
+               "single_thread": {"value": mlups_1, "unit": UNIT, "cores": 1,
+                                 "sample": f"1 full step of the {args.workload} workload ({dt_1:.1f} s)"}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.n == 128 else WORKLOAD.replace("128^3", f"{args.n}^3"),
+        "config": {"workload": (WORKLOADS[args.workload] if args.workload == "sessile" or args.n == 128
+                                else WORKLOADS["droplet"].replace("128^3", f"{args.n}^3")),
                    "cells": N, "schedule": args.schedule, "parallelism": f"replicas x{world}",
                    "storage": {"f32": "f32", "f16": "f16 shifted by w_i rho_ref / w_i T_ref",
                                "bf16": "bf16 shifted by w_i rho_ref / w_i T_ref",
@@ -579,6 +653,7 @@ def main():
                      "kernels": {k: {"launches": v[0], "ms_per_launch": v[1] / v[0],
                                      "share": v[1] / sum(w[1] for w in prof.values())} for k, v in prof.items()}},
         "cpu_baseline": cpu,
+        "droplet_128": droplet,
         "adjoint": adj,
         "batched": batched,
         "large": large,

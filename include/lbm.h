@@ -38,8 +38,6 @@
  * beyond rounding):
  *   LBM_SLAB_PLANES, LBM_SLAB_STREAMS, LBM_GRAPH_STEPS  planes per slab, streams
  *       and steps per CUDA graph of the pipelined slab schedule (read by lbm_init);
- *   LBM_BULK  stage phase C's tiles in shared memory with cp.async.bulk (FP32,
- *       N a multiple of 4; read by lbm_init);
  *   LBM_ADJ_EAGER, LBM_ADJ_NOPDL  launch every adjoint step on its own instead of
  *       replaying K-step segments from graphs / without programmatic dependent
  *       launches (read by each lbm_adjoint_step).
@@ -189,13 +187,21 @@ int lbm_adjoint_state(lbm_ctx* ctx, float* f_bar, float* g_bar, int mem);
  * the persistent launch (threads per CTA 128/256, CTAs per SM 1-4, cells per
  * tile 1024-8192) or one launch per phase over the same tile list (reported
  * as ctas_per_sm = 0).  Outputs may be NULL.
- * lbm_batch_cells returns the total number of cells. */
+ * lbm_batch_cells returns the total number of cells.
+ * After LBM_ERR_TIMEOUT from lbm_batch_sync the domains hold partial states
+ * (some phases of the last step ran, others did not): set them again
+ * (lbm_set_state) before stepping; lbm_batch_sync has already reset the
+ * barrier and the abort flag, so the batch then steps like a new one.
+ * lbm_batch_inject_stall (failure-detection tests) makes the next persistent
+ * launch's first grid barrier unable to complete, so that its bounded waits
+ * give up; LBM_ERR_ARG when the batch runs one launch per phase (no barrier). */
 typedef struct lbm_batch lbm_batch;
 int lbm_batch_create(lbm_batch** out, lbm_ctx* const* ctxs, int n);
 int lbm_batch_tune(lbm_batch* batch, int* threads, int* ctas_per_sm, int* tile_cells);
 int lbm_batch_step(lbm_batch* batch, int n);
 int lbm_batch_sync(lbm_batch* batch);
 long long lbm_batch_cells(const lbm_batch* batch);
+int lbm_batch_inject_stall(lbm_batch* batch);
 void lbm_batch_destroy(lbm_batch* batch);
 
 /* Per-node Dirichlet temperature of non-periodic face `face` (Sec. 3.1): an
@@ -274,8 +280,10 @@ int lbm_profile_read(lbm_ctx* ctx, long long* launches, double* ms, int nkinds);
  * Scratch: a fixed device array of 4096 x 4 doubles (128 KiB) inside the
  * library, held by every GPU that loads the library until the process exits.
  * n_cells may be at most 4096 * 8192 = 33,554,432; larger sizes return
- * LBM_ERR_ARG before any device work.  The first call on each device looks up
- * the array's device address; make that first call before any stream capture.
+ * LBM_ERR_ARG before any device work.  Every call looks up the array's device
+ * address on the current device (cudaGetSymbolAddress, which enqueues no work)
+ * and passes it to the kernels; make the first call on a device before any
+ * stream capture, since that lookup may initialise the module on the device.
  * All calls share the one array, which keeps the last call's partial sums, so
  * calls that overlap on the GPU (other streams, other threads) race: serialise
  * them.  Every partial sum a call reads is written by that call first. */

@@ -33,6 +33,17 @@
 /* ---------------------------------------------------------------- tables -- */
 
 /* Appendix, D3Q19 transformation matrix M-hat (rows = moments, columns = i). */
+/* Built with -fopenmp (oracle/build.py, omp=True) the per-cell loops over z run on all
+ * host cores; each iteration writes only its own cells (or, in the streaming loops, a
+ * destination no other source writes), so the result is bit-identical to the serial
+ * build.  Without OpenMP the pragma is empty. */
+#ifdef _OPENMP
+#include <omp.h>
+#define ORC_PAR_Z _Pragma("omp parallel for schedule(static)")
+#else
+#define ORC_PAR_Z
+#endif
+
 static const int MHAT[19][19] = {
     {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1},
     {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0},
@@ -606,17 +617,20 @@ static int fields_t(const orc_params* P, const double* f, const double* g, doubl
                     double* jz, double* T, double* pe, double* dpdT, double* psi, double* Fx, double* Fy,
                     double* Fz, double* ux, double* uy, double* uz) {
   long N = (long)P->nx * P->ny * P->nz;
-  int st = ORC_OK;
+  int nonfinite = 0, psi_bad = 0; /* a non-finite population outranks a psi-domain error */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(| : nonfinite, psi_bad)
+#endif
   for (long c = 0; c < N; ++c) {
     double r = 0, j[3] = {0, 0, 0}, t = 0;
     for (int i = 0; i < 19; ++i) {
       double v = f[i * N + c];
-      if (!isfinite(v)) st = ORC_ERR_NONFINITE;
+      if (!isfinite(v)) nonfinite = 1;
       r += v;
       for (int d = 0; d < 3; ++d) j[d] += C19[i][d] * v;
     }
     for (int i = 0; i < 7; ++i) {
-      if (!isfinite(g[i * N + c])) st = ORC_ERR_NONFINITE;
+      if (!isfinite(g[i * N + c])) nonfinite = 1;
       t += g[i * N + c];
     }
     rho[c] = r;
@@ -628,11 +642,13 @@ static int fields_t(const orc_params* P, const double* f, const double* g, doubl
     dpdT[c] = orc_dpdT(P, r, t);
     double arg = 2.0 * (pe[c] - r / 3.0) / P->G; /* Eq. 7 with dx = dt = 1, c_s^2 = 1/3 */
     if (!(arg >= 0.0)) {
-      if (st == ORC_OK) st = ORC_ERR_PSI_DOMAIN;
+      psi_bad = 1;
       psi[c] = NAN;
     } else
       psi[c] = sqrt(arg);
   }
+  const int st = nonfinite ? ORC_ERR_NONFINITE : (psi_bad ? ORC_ERR_PSI_DOMAIN : ORC_OK);
+  ORC_PAR_Z
   for (int z = 0; z < P->nz; ++z)
     for (int y = 0; y < P->ny; ++y)
       for (int x = 0; x < P->nx; ++x) {
@@ -710,6 +726,7 @@ static int step_impl(const orc_params* P, const double* const* Tface, const doub
   copy_fields(&w, N, diag);
 
   /* step 5: D3Q19 collision at every node, wall and open-face nodes included */
+  ORC_PAR_Z
   for (int z = 0; z < nz; ++z)
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
@@ -729,6 +746,7 @@ static int step_impl(const orc_params* P, const double* const* Tface, const doub
 
   /* step 6: streaming with bounce-back; slots nobody writes stay NaN */
   for (long k = 0; k < 19 * N; ++k) fo[k] = NAN;
+  ORC_PAR_Z
   for (int z = 0; z < nz; ++z)
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x)
@@ -738,6 +756,7 @@ static int step_impl(const orc_params* P, const double* const* Tface, const doub
         }
 
   /* step 7: open faces */
+  ORC_PAR_Z
   for (int z = 0; z < nz; ++z)
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
@@ -778,6 +797,7 @@ static int step_impl(const orc_params* P, const double* const* Tface, const doub
       }
 
   /* step 8: D3Q7 collision */
+  ORC_PAR_Z
   for (int z = 0; z < nz; ++z)
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
@@ -798,6 +818,7 @@ static int step_impl(const orc_params* P, const double* const* Tface, const doub
 
   /* step 9: relaxed streaming, rho c_v at the destination */
   for (long k = 0; k < 7 * N; ++k) go[k] = g[k];
+  ORC_PAR_Z
   for (int z = 0; z < nz; ++z)
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x)
@@ -814,7 +835,8 @@ static int step_impl(const orc_params* P, const double* const* Tface, const doub
     double w7[7];
     w7[0] = 1.0 - P->wbar;
     for (int i = 1; i < 7; ++i) w7[i] = P->wbar / 6.0;
-    for (int z = 0; z < nz; ++z)
+    ORC_PAR_Z
+  for (int z = 0; z < nz; ++z)
       for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
           int m = node_faces(P, x, y, z);
@@ -910,4 +932,16 @@ void orc_init_state(const orc_params* P, const double* rho0, const double* T0, d
     g[c] = (1.0 - P->wbar) * T0[c];
     for (int i = 1; i < 7; ++i) g[i * N + c] = P->wbar / 6.0 * T0[c];
   }
+}
+
+/* Threads the per-cell loops use: n > 0 sets it (OpenMP build only); returns the count in
+ * effect (1 in the serial build). */
+int orc_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }

@@ -88,6 +88,8 @@ int orc_stream_map19(const orc_params* P, int* dst);
 int orc_stream_map7(const orc_params* P, int* src);
 int orc_node_class(const orc_params* P, unsigned char* cls);
 void orc_init_state(const orc_params* P, const double* rho0, const double* T0, double* f, double* g);
+/* threads of the per-cell loops (OpenMP build): n > 0 sets; returns the count in effect */
+int orc_threads(int n);
 
 #ifdef __cplusplus
 }

@@ -39,13 +39,13 @@ class OrcFields(ct.Structure):
     _fields_ = [(n, _PD) for n in ("rho", "T", "psi", "p", "dpdT", "ux", "uy", "uz", "Fx", "Fy", "Fz")]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        path = build_oracle()
+def lib(omp: bool = False):
+    """The serial oracle library, or (omp=True) the same source built with OpenMP."""
+    if omp not in _libs:
+        path = build_oracle(omp=omp)
         L = ct.CDLL(path)
         P = ct.POINTER(OrcParams)
         L.orc_Tc.restype = _D
@@ -77,8 +77,9 @@ def lib():
         L.orc_node_class.argtypes = [P, ct.POINTER(ct.c_ubyte)]
         L.orc_init_state.argtypes = [P, _PD, _PD, _PD, _PD]
         L.orc_init_state.restype = None
-        _lib = L
-    return _lib
+        L.orc_threads.argtypes = [ct.c_int]
+        _libs[omp] = L
+    return _libs[omp]
 
 
 def _ptr(a):
@@ -116,33 +117,35 @@ def _tface_array(tface):
 
 
 class Oracle:
-    """FP64 reference lattice.  params: dict with the orc_params fields."""
+    """FP64 reference lattice.  params: dict with the orc_params fields.  omp=True runs the
+    OpenMP build (the same arithmetic on all host cores; threads() reports the count)."""
 
-    def __init__(self, params: dict):
+    def __init__(self, params: dict, omp: bool = False):
+        self.omp = omp
         self.d = dict(params)
         self.p = make_params(self.d)
         self.shape = (self.p.nz, self.p.ny, self.p.nx)
         self.N = self.p.nx * self.p.ny * self.p.nz
         self.tface = None
-        if lib().orc_check(ct.byref(self.p)) != 0:
+        if lib(self.omp).orc_check(ct.byref(self.p)) != 0:
             raise ValueError("oracle rejects these parameters")
 
     # thermodynamics
     def Tc(self):
-        return lib().orc_Tc(ct.byref(self.p))
+        return lib(self.omp).orc_Tc(ct.byref(self.p))
 
     def p_eos(self, rho, T):
-        return lib().orc_p_eos(ct.byref(self.p), rho, T)
+        return lib(self.omp).orc_p_eos(ct.byref(self.p), rho, T)
 
     def dpdT(self, rho, T):
-        return lib().orc_dpdT(ct.byref(self.p), rho, T)
+        return lib(self.omp).orc_dpdT(ct.byref(self.p), rho, T)
 
     def dpdrho(self, rho, T):
-        return lib().orc_dpdrho(ct.byref(self.p), rho, T)
+        return lib(self.omp).orc_dpdrho(ct.byref(self.p), rho, T)
 
     def maxwell(self, T):
         rv, rl, ps = _D(), _D(), _D()
-        st = lib().orc_maxwell(ct.byref(self.p), T, ct.byref(rv), ct.byref(rl), ct.byref(ps))
+        st = lib(self.omp).orc_maxwell(ct.byref(self.p), T, ct.byref(rv), ct.byref(rl), ct.byref(ps))
         if st != 0:
             raise ValueError("no coexistence at this temperature")
         return rv.value, rl.value, ps.value
@@ -157,7 +160,7 @@ class Oracle:
         T0 = np.ascontiguousarray(T0, dtype=np.float64).reshape(-1)
         f = np.empty((19, self.N))
         g = np.empty((7, self.N))
-        lib().orc_init_state(ct.byref(self.p), _ptr(rho0), _ptr(T0), _ptr(f), _ptr(g))
+        lib(self.omp).orc_init_state(ct.byref(self.p), _ptr(rho0), _ptr(T0), _ptr(f), _ptr(g))
         return f, g
 
     def step(self, f, g, diag=False):
@@ -167,7 +170,7 @@ class Oracle:
         go = np.empty_like(g)
         tf, keep = _tface_array(self.tface)
         flds, out = self._fields_struct() if diag else (None, None)
-        st = lib().orc_step(ct.byref(self.p), tf, _ptr(f), _ptr(g), _ptr(fo), _ptr(go),
+        st = lib(self.omp).orc_step(ct.byref(self.p), tf, _ptr(f), _ptr(g), _ptr(fo), _ptr(go),
                             ct.byref(flds) if diag else None)
         del keep
         if diag:
@@ -178,7 +181,7 @@ class Oracle:
         f = np.array(f, dtype=np.float64).reshape(19, self.N)
         g = np.array(g, dtype=np.float64).reshape(7, self.N)
         tf, keep = _tface_array(self.tface)
-        st = lib().orc_run(ct.byref(self.p), tf, _ptr(f), _ptr(g), int(nsteps))
+        st = lib(self.omp).orc_run(ct.byref(self.p), tf, _ptr(f), _ptr(g), int(nsteps))
         del keep
         return st, f, g
 
@@ -195,7 +198,7 @@ class Oracle:
         Th = np.ascontiguousarray(Th, dtype=np.float64).reshape(2, self.N)
         fo, go, Tho = np.empty_like(f), np.empty_like(g), np.empty_like(Th)
         tf, keep = _tface_array(self.tface)
-        st = lib().orc_step_hist(ct.byref(self.p), tf, _ptr(f), _ptr(g), _ptr(Th), _ptr(fo), _ptr(go), _ptr(Tho))
+        st = lib(self.omp).orc_step_hist(ct.byref(self.p), tf, _ptr(f), _ptr(g), _ptr(Th), _ptr(fo), _ptr(go), _ptr(Tho))
         del keep
         return st, fo, go, Tho
 
@@ -204,9 +207,13 @@ class Oracle:
         g = np.array(g, dtype=np.float64).reshape(7, self.N)
         Th = np.array(Th, dtype=np.float64).reshape(2, self.N)
         tf, keep = _tface_array(self.tface)
-        st = lib().orc_run_hist(ct.byref(self.p), tf, _ptr(f), _ptr(g), _ptr(Th), int(nsteps))
+        st = lib(self.omp).orc_run_hist(ct.byref(self.p), tf, _ptr(f), _ptr(g), _ptr(Th), int(nsteps))
         del keep
         return st, f, g, Th
+
+    def threads(self, n: int = 0):
+        """Threads of the per-cell loops (n > 0 sets them; OpenMP build only)."""
+        return lib(self.omp).orc_threads(int(n))
 
     def _fields_struct(self):
         out = {n: np.empty(self.N) for n, _ in OrcFields._fields_}
@@ -217,22 +224,22 @@ class Oracle:
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(19, self.N)
         g = np.ascontiguousarray(g, dtype=np.float64).reshape(7, self.N)
         s, out = self._fields_struct()
-        st = lib().orc_macros(ct.byref(self.p), _ptr(f), _ptr(g), ct.byref(s))
+        st = lib(self.omp).orc_macros(ct.byref(self.p), _ptr(f), _ptr(g), ct.byref(s))
         return st, out
 
     def stream_map19(self):
         m = np.empty(19 * self.N, dtype=np.int32)
-        lib().orc_stream_map19(ct.byref(self.p), m.ctypes.data_as(ct.POINTER(ct.c_int)))
+        lib(self.omp).orc_stream_map19(ct.byref(self.p), m.ctypes.data_as(ct.POINTER(ct.c_int)))
         return m
 
     def stream_map7(self):
         m = np.empty(7 * self.N, dtype=np.int32)
-        lib().orc_stream_map7(ct.byref(self.p), m.ctypes.data_as(ct.POINTER(ct.c_int)))
+        lib(self.omp).orc_stream_map7(ct.byref(self.p), m.ctypes.data_as(ct.POINTER(ct.c_int)))
         return m
 
     def node_class(self):
         m = np.empty(self.N, dtype=np.uint8)
-        lib().orc_node_class(ct.byref(self.p), m.ctypes.data_as(ct.POINTER(ct.c_ubyte)))
+        lib(self.omp).orc_node_class(ct.byref(self.p), m.ctypes.data_as(ct.POINTER(ct.c_ubyte)))
         return m
 
     # per-cell pieces
@@ -241,26 +248,26 @@ class Oracle:
         ueq = np.ascontiguousarray(ueq, dtype=np.float64)
         F = np.ascontiguousarray(F, dtype=np.float64)
         out = np.empty(19)
-        lib().orc_collide19(ct.byref(self.p), _ptr(f), rho, _ptr(ueq), _ptr(F), _ptr(out))
+        lib(self.omp).orc_collide19(ct.byref(self.p), _ptr(f), rho, _ptr(ueq), _ptr(F), _ptr(out))
         return out
 
     def collide7(self, g, rho, T, u, divu, dpdT, d2T=0.0):
         g = np.ascontiguousarray(g, dtype=np.float64)
         u = np.ascontiguousarray(u, dtype=np.float64)
         out = np.empty(7)
-        lib().orc_collide7(ct.byref(self.p), _ptr(g), rho, T, _ptr(u), divu, dpdT, d2T, _ptr(out))
+        lib(self.omp).orc_collide7(ct.byref(self.p), _ptr(g), rho, T, _ptr(u), divu, dpdT, d2T, _ptr(out))
         return out
 
     def zouhe(self, face, f, F):
         f = np.array(f, dtype=np.float64)
         F = np.ascontiguousarray(F, dtype=np.float64)
-        lib().orc_zouhe(ct.byref(self.p), int(face), _ptr(F), _ptr(f))
+        lib(self.omp).orc_zouhe(ct.byref(self.p), int(face), _ptr(F), _ptr(f))
         return f
 
     def meq19(self, rho, u):
         u = np.ascontiguousarray(u, dtype=np.float64)
         out = np.empty(19)
-        lib().orc_meq19(ct.byref(self.p), rho, _ptr(u), _ptr(out))
+        lib(self.omp).orc_meq19(ct.byref(self.p), rho, _ptr(u), _ptr(out))
         return out
 
 

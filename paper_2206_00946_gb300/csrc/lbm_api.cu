@@ -10,7 +10,6 @@
 #include <vector>
 
 #include "lbm.h"
-#include "lbm_bulk.cuh"
 #include "lbm_fused.cuh"
 #include "lbm_phases.cuh"
 #include "lbm_ctx.cuh"
@@ -20,8 +19,6 @@ using namespace lbm;
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kBulkTile = 256;                                      // cells per staged tile
-constexpr int kBulkSmem = 2 * 26 * kBulkTile * 4 + 2 * 8;           // two stages + two mbarriers
 #ifndef LBM_PHASEC_MINBLOCKS
 #define LBM_PHASEC_MINBLOCKS 4
 #endif
@@ -481,27 +478,16 @@ int step_phases_t(lbm_ctx* c) {
   const int a = c->cur, b = 1 - c->cur;
   const AuxFor<T> X = aux_for<T>(c, a);
   cudaEvent_t e = prof_begin(c);
-  // j is stored only for the staged path, whose separate phase B reads it
   k_phaseA<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, a), gbuf<T>(c, a), X, nullptr, c->err_d, 0,
-                                                   (int)c->N, c->bulk_grid > 0 ? 1 : 0);
+                                                   (int)c->N, 0);
   prof_end(c, 0, e);
-  if (c->bulk_grid > 0) {  // FP32 storage only: staged C19 + C7 after a separate phase B
-    e = prof_begin(c);
-    k_phaseB<<<c->grid, kThreads, 0, c->stream>>>(c->P, c->X, 0, (int)c->N);
-    prof_end(c, 1, e);
-    e = prof_begin(c);
-    k_phaseC_bulk<kBulkTile><<<c->bulk_grid, kBulkTile, kBulkSmem, c->stream>>>(
-        c->P, fbuf<float>(c, a), gbuf<float>(c, a), fbuf<float>(c, b), gbuf<float>(c, b), c->X, c->err_d);
-    prof_end(c, 2, e);
-  } else {
-    e = prof_begin(c);
-    k_phaseBC19<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, a), fbuf<T>(c, b), X, 0, (int)c->N);
-    prof_end(c, 2, e);
-    // the D3Q7 phase needs the velocity of the neighbours: after the whole D3Q19 pass
-    e = prof_begin(c);
-    launch_c7<T>(c, X, c->grid, c->stream, gbuf<T>(c, a), gbuf<T>(c, b), 0, (int)c->N);
-    prof_end(c, 5, e);
-  }
+  e = prof_begin(c);
+  k_phaseBC19<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, a), fbuf<T>(c, b), X, 0, (int)c->N);
+  prof_end(c, 2, e);
+  // the D3Q7 phase needs the velocity of the neighbours: after the whole D3Q19 pass
+  e = prof_begin(c);
+  launch_c7<T>(c, X, c->grid, c->stream, gbuf<T>(c, a), gbuf<T>(c, b), 0, (int)c->N);
+  prof_end(c, 5, e);
   if (c->P.bd_total > 0) {
     e = prof_begin(c);
     k_phaseD<T><<<grid_for(c->P.bd_total), kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, b), gbuf<T>(c, b), X);
@@ -758,6 +744,21 @@ int slab_capture(lbm_ctx* c) {
   return ie == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
+// Captures the graphs of both buffer parities up front (lbm_init), so that the first
+// lbm_step of a run of graph_steps or more steps pays no capture.
+int slab_capture_both(lbm_ctx* c) {
+  SlabPlan& S = *c->slabs;
+  if (S.graph_steps <= 0) return LBM_OK;
+  const int cur = c->cur;
+  int st = LBM_OK;
+  for (int k = 0; k < 2 && st == LBM_OK; ++k) {
+    c->cur = k;
+    if (!S.graph[k]) st = slab_capture(c);
+  }
+  c->cur = cur;
+  return st;
+}
+
 int step_slabs(lbm_ctx* c, int n) {
   SlabPlan& S = *c->slabs;
   cudaEvent_t e = prof_begin(c);
@@ -992,19 +993,9 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
     lbm_destroy(c);
     return LBM_ERR_CUDA;
   }
-  // bulk-staged phase C: opt-in (LBM_BULK=1); measured slower than the unstaged kernel on
-  // GB300 because phase C is bound by its neighbour gathers, not by the population loads
-  if (N % 4 == 0 && p->storage == LBM_STORE_F32 && std::getenv("LBM_BULK") != nullptr) {
-    int per_sm = 0, sms = 0;
-    cudaFuncSetAttribute(k_phaseC_bulk<kBulkTile>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBulkSmem);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phaseC_bulk<kBulkTile>, kBulkTile, kBulkSmem);
-    const long long ntiles = (N + kBulkTile - 1) / kBulkTile;
-    long long g = (long long)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-    c->bulk_grid = (int)(g < ntiles ? g : ntiles);
-  }
   if (p->schedule == LBM_SCHED_SLABS) {
     st = slab_plan_create(c);
+    if (st == LBM_OK) st = slab_capture_both(c);
     if (st != LBM_OK) {
       lbm_destroy(c);
       return st;
@@ -1231,7 +1222,7 @@ int lbm_launches_per_step(const lbm_ctx* c) {
   if (!c) return 0;
   if (c->hp.schedule == LBM_SCHED_SLABS) return (int)c->slabs->order.size();
   if (c->hp.schedule == LBM_SCHED_FUSED) return fused_launches(&c->plan);
-  return (c->P.bd_total > 0 ? 4 : 3) + (c->bulk_grid > 0 ? 0 : 1);
+  return c->P.bd_total > 0 ? 4 : 3;
 }
 
 int lbm_macros(lbm_ctx* c, float* rho, float* ux, float* uy, float* uz, float* T, int mem) {
@@ -1294,17 +1285,6 @@ int lbm_stream_map(lbm_ctx* c, int32_t* map19, int32_t* map7, uint8_t* node_clas
   cudaFree(cl);
   return st;
 }
-
-#ifdef LBM_FUSED_STATS
-int lbm_fused_stats(unsigned long long* out, int reset) {
-  if (cudaMemcpyFromSymbol(out, g_fstats, sizeof(g_fstats)) != cudaSuccess) return LBM_ERR_CUDA;
-  if (reset) {
-    static unsigned long long zero[4096][10];
-    if (cudaMemcpyToSymbol(g_fstats, zero, sizeof(zero)) != cudaSuccess) return LBM_ERR_CUDA;
-  }
-  return LBM_OK;
-}
-#endif
 
 void lbm_destroy(lbm_ctx* c) {
   if (!c) return;

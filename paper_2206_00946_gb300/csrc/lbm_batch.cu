@@ -357,7 +357,15 @@ extern "C" int lbm_batch_sync(lbm_batch* b) {
   if (cudaMemcpyAsync(&ab, b->abort_d, sizeof(int), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
       cudaStreamSynchronize(b->stream) != cudaSuccess)
     return LBM_ERR_CUDA;
-  if (ab) return LBM_ERR_TIMEOUT;
+  if (ab) {
+    // a barrier gave up: reset the barrier and the abort flag so that the batch can
+    // step again once the caller has set the domains' states anew (they are partial)
+    if (cudaMemsetAsync(b->bar_d, 0, 2 * sizeof(unsigned), b->stream) != cudaSuccess ||
+        cudaMemsetAsync(b->abort_d, 0, sizeof(int), b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+      return LBM_ERR_CUDA;
+    return LBM_ERR_TIMEOUT;
+  }
   for (lbm_ctx* c : b->ctx) {
     const int s = lbm_sync(c);
     if (s) return s;
@@ -366,6 +374,18 @@ extern "C" int lbm_batch_sync(lbm_batch* b) {
 }
 
 extern "C" long long lbm_batch_cells(const lbm_batch* b) { return b ? b->cells : 0; }
+
+// Test support: the arrival counter of the grid barrier is set to the grid size,
+// so that no arrival of the next persistent launch completes it (each CTA's wait
+// gives up after its bound and the launch ends).
+extern "C" int lbm_batch_inject_stall(lbm_batch* b) {
+  if (!b || b->mode != 0) return LBM_ERR_ARG;
+  const unsigned v[2] = {(unsigned)b->grid, 0u};
+  return cst(cudaMemcpyAsync(b->bar_d, v, sizeof(v), cudaMemcpyHostToDevice, b->stream)) ||
+                 cst(cudaStreamSynchronize(b->stream))
+             ? LBM_ERR_CUDA
+             : LBM_OK;
+}
 
 // Measured choice of the launch shape: every candidate (threads per CTA, CTAs
 // per SM, cells per tile) runs a few timed steps; the fastest is kept.  The

@@ -68,7 +68,6 @@ struct lbm_ctx {
   double* red_h;
   int red_blocks;
   int grid;
-  int bulk_grid;  // persistent CTAs of the staged phase C (0: unstaged kernel)
   bool has_state;
   cudaStream_t side;  // second stream for the D3Q7 collision
   cudaEvent_t ev_fork, ev_join;

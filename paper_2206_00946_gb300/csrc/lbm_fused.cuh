@@ -77,14 +77,6 @@ __device__ __forceinline__ int fetch_item(const FusedArgs& A) {
   return (item < 0 || item >= A.total_items) ? -1 : item;
 }
 
-#ifdef LBM_FUSED_STATS
-// per CTA: work cycles per phase [0..3], items per phase [4..7], wait cycles [8], total cycles [9]
-__device__ unsigned long long g_fstats[4096][10];
-#define FSTAT(...) __VA_ARGS__
-#else
-#define FSTAT(...)
-#endif
-
 #ifndef LBM_FUSED_MINBLOCKS
 #define LBM_FUSED_MINBLOCKS 2
 #endif
@@ -97,15 +89,12 @@ __global__ void __launch_bounds__(256, LBM_FUSED_MINBLOCKS) k_fused(Params P, Au
   if (threadIdx.x == 0) s_next = fetch_item(A);
   __syncthreads();
   int item = s_next;
-  FSTAT(long long st_t0 = clock64(); long long st_w = 0; long long st_ph[4] = {0, 0, 0, 0};
-        int st_n[4] = {0, 0, 0, 0};)
   while (item >= 0) {
     __syncthreads();  // everyone has read s_next
     const int s = A.item_stage[item];
     const int t = item - A.stage_first[s];
     const int code = A.stages[s];
     const int ph = code >> 24, z = code & 0xffffff;
-    FSTAT(const long long st_a = clock64();)
     if (threadIdx.x == 0) {
       // the next item is claimed now, so its dispatch latency overlaps this item's work
       s_next = *(volatile int*)A.abort ? -1 : fetch_item(A);
@@ -137,7 +126,6 @@ __global__ void __launch_bounds__(256, LBM_FUSED_MINBLOCKS) k_fused(Params P, Au
       s_ok = ok;
     }
     __syncthreads();
-    FSTAT(const long long st_b = clock64(); st_w += st_b - st_a;)
     if (!s_ok) break;
     if (ph == PH_D) {
       const int cnt = boundary_count(P, z);
@@ -159,21 +147,12 @@ __global__ void __launch_bounds__(256, LBM_FUSED_MINBLOCKS) k_fused(Params P, Au
       }
     }
     __syncthreads();
-    FSTAT(st_ph[ph] += clock64() - st_b; st_n[ph] += 1;)
     if (threadIdx.x == 0) {
       __threadfence();
       atomicAdd(A.done + ph * P.nz + z, 1u);
     }
     item = s_next;
   }
-  FSTAT(if (threadIdx.x == 0 && blockIdx.x < 4096) {
-    for (int k = 0; k < 4; ++k) {
-      g_fstats[blockIdx.x][k] += st_ph[k];
-      g_fstats[blockIdx.x][4 + k] += st_n[k];
-    }
-    g_fstats[blockIdx.x][8] += st_w;
-    g_fstats[blockIdx.x][9] += clock64() - st_t0;
-  })
   if (err) atomicOr(A.err, err);
 }
 

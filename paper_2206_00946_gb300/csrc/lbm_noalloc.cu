@@ -11,8 +11,6 @@
 // doubles in device memory).
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "lbm.h"
 #include "lbm_phases.cuh"
 
@@ -79,22 +77,13 @@ __global__ void k_reduce_finish_static(const double* partial, int nblocks, doubl
   }
 }
 
-// Device address of the scratch array, looked up once per device with that
-// device current (the array's name is only a host-side stand-in in host code).
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double* g_scratch_ptr[kMaxDevices] = {};
-
+// Device address of the scratch array on the current device, looked up on every
+// call (the array's name is only a host-side stand-in in host code; the lookup is
+// cheap, enqueues nothing and stays valid across a reset of the device).
 int scratch_for_current_device(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBM_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_reduce_scratch) != cudaSuccess || !p) return LBM_ERR_CUDA;
-    g_scratch_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_reduce_scratch) != cudaSuccess || !p) return LBM_ERR_CUDA;
+  *out = static_cast<double*>(p);
   return LBM_OK;
 }
 

@@ -46,7 +46,7 @@ EXPORTS = ["lbm_init", "lbm_set_state", "lbm_get_state", "lbm_set_face_T", "lbm_
            "lbm_maxwell", "lbm_launches_per_step", "lbm_profile", "lbm_profile_read", "lbm_reduce_static",
            "lbm_checkpoint_bytes", "lbm_checkpoint", "lbm_restore", "lbm_record", "lbm_adjoint_step",
            "lbm_adjoint_state", "lbm_batch_create", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_sync",
-           "lbm_batch_cells", "lbm_batch_destroy", "lbm_inject_stall"]
+           "lbm_batch_cells", "lbm_batch_destroy", "lbm_batch_inject_stall", "lbm_inject_stall"]
 PROFILE_KINDS = ["phaseA", "phaseB", "phaseC", "phaseD", "fused", "phaseC7"]
 
 _lib = None
@@ -103,6 +103,7 @@ def load(path: str = LIB_PATH):
     L.lbm_batch_cells.restype = ct.c_longlong
     L.lbm_batch_destroy.argtypes = [vp]
     L.lbm_batch_destroy.restype = None
+    L.lbm_batch_inject_stall.argtypes = [vp]
     _lib = L
     return L
 
@@ -358,6 +359,9 @@ class Batch:
 
     def lbm_batch_sync(self):
         return load().lbm_batch_sync(self._b)
+
+    def lbm_batch_inject_stall(self):
+        return load().lbm_batch_inject_stall(self._b)
 
     def lbm_batch_tune(self):
         t, c, s = ct.c_int(), ct.c_int(), ct.c_int()

@@ -1,6 +1,7 @@
 """The reference arm of the benchmark (the FP64 oracle on host cores) keeps the JSON
 contract: one line with the metric of the GPU arm, the job throughput, the step time,
-the oracle described as the CPU baseline and an end-to-end figure without transfers."""
+the oracle (its OpenMP build, on all host cores) described as the CPU baseline and an
+end-to-end figure without transfers."""
 import json
 import os
 import subprocess
@@ -21,7 +22,7 @@ def test_reference_arm_prints_one_contract_line():
     assert d["value"] > 0 and d["ms_per_step"] > 0
     assert d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] >= 3  # the warm-up minimum is 3
     assert d["higher_is_better"] is True and d["scaling"] == "weak" and d["vs_baseline"] is None
-    assert d["dtype"] == "f64" and d["data"] == "synthetic" and "128^3" in d["config"]["workload"]
+    assert d["dtype"] == "f64" and d["data"] == "synthetic" and "256x256x128" in d["config"]["workload"]
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == os.cpu_count() and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

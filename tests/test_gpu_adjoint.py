@@ -7,10 +7,16 @@ lbm_adjoint_step (FP32 step, FP64 accumulation) through the autograd wrapper,
 are compared with
   * torch.autograd through the independent FP64 plain-torch step (every
     element), and
-  * central differences of the FP64 C oracle at seeded probe points.
+  * central differences of the FP64 C oracle at seeded probe points, among them
+    the adjoint workload's own check in reduced form: a 12^3 open droplet (the
+    64^3 workload's faces, radius 3), 100 steps with a checkpoint every 10, 32
+    seeded probes of T0 and of the bottom-face temperature field, h = 1e-6 in
+    FP64, gradients within 1e-4 of their largest magnitude.
 Several checkpoint segments and a ragged last segment are exercised (K does
 not divide the step count).
 """
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 
@@ -93,7 +99,7 @@ def test_adjoint_matches_fp64_autograd(kind, n, K, thermo):
     e0 = np.max(np.abs(dT0_g - dT0_r)) / np.max(np.abs(dT0_r))
     eb = np.max(np.abs(dTb_g - dTb_r)) / np.max(np.abs(dTb_r))
     print(f"{kind}: |dL/dT0 err| / max = {e0:.2e}, |dL/dTface err| / max = {eb:.2e}")
-    assert e0 < 1e-3 and eb < 1e-3, (e0, eb)
+    assert e0 < 1e-4 and eb < 1e-4, (e0, eb)
 
 
 def test_adjoint_matches_oracle_differences(thermo):
@@ -129,6 +135,58 @@ def test_adjoint_matches_oracle_differences(thermo):
         b[k] -= h
         fd = (L_oracle(T0, a) - L_oracle(T0, b)) / (2 * h)
         assert abs(dTb_g[k] - fd) <= 2e-3 * scaleb, (k, dTb_g[k], fd)
+
+
+def test_adjoint_matches_fp64_central_differences_at_32_probes(thermo):
+    """The adjoint workload's accuracy check, reduced to a size the FP64 oracle runs 64
+    times in seconds: 12^3 open droplet of radius 3, 100 steps, checkpoints every 10;
+    16 probes of T0 and 16 of the bottom-face (z = 0) temperature field, central
+    differences with h = 1e-6 of the FP64 C oracle; every gradient within 1e-4 of the
+    largest gradient magnitude of its field."""
+    Tc, rv, rl = thermo["Tc"], thermo["rho_v"], thermo["rho_l"]
+    p, rho0, T0 = W.droplet(Tc, rv, rl, n=12, R=3.0, W=2.0, seed=9, amp=1e-3)
+    rho0 = rho0.reshape(-1).astype(np.float32).astype(np.float64)
+    T0 = T0.reshape(-1).astype(np.float32).astype(np.float64)
+    face, n, K = 4, 100, 10
+    rng = np.random.default_rng(2206)
+    Tb = (p["face_T"][face] * (1 + 0.01 * rng.standard_normal(12 * 12))).astype(np.float32).astype(np.float64)
+    wT = rng.standard_normal(T0.size)
+    _, dT0_g, dTb_g = _gpu_grads(p, rho0, T0, face, Tb, wT, n, K)
+
+    def L_oracle(args):
+        T0v, Tbv = args
+        o = Oracle(p)
+        tf = [None] * 6
+        tf[face] = Tbv
+        o.set_face_T(tf)
+        f, g = o.init_state(rho0, T0v)
+        st, f, g = o.run(f, g, n)
+        assert st == 0
+        return float(_loss(torch.tensor(f.sum(0)), torch.tensor(g.sum(0)), p, torch.tensor(wT)))
+
+    h = 1e-6
+    jobs, probes = [], []
+    for c in rng.choice(T0.size, 16, replace=False):
+        a, b = T0.copy(), T0.copy()
+        a[c] += h
+        b[c] -= h
+        jobs += [(a, Tb), (b, Tb)]
+        probes.append(("T0", c))
+    for k in rng.choice(Tb.size, 16, replace=False):
+        a, b = Tb.copy(), Tb.copy()
+        a[k] += h
+        b[k] -= h
+        jobs += [(T0, a), (T0, b)]
+        probes.append(("Tb", k))
+    with ThreadPoolExecutor(8) as ex:  # the oracle releases the GIL
+        Ls = list(ex.map(L_oracle, jobs))
+    worst = 0.0
+    for j, (field, idx) in enumerate(probes):
+        fd = (Ls[2 * j] - Ls[2 * j + 1]) / (2 * h)
+        got, scale = (dT0_g[idx], np.max(np.abs(dT0_g))) if field == "T0" else (dTb_g[idx], np.max(np.abs(dTb_g)))
+        worst = max(worst, abs(got - fd) / scale)
+        assert abs(got - fd) <= 1e-4 * scale, (field, idx, got, fd)
+    print(f"adjoint vs central differences (h = 1e-6, 32 probes): max |err| / scale = {worst:.2e}")
 
 
 @pytest.mark.parametrize("schedule", [lbm.SCHED_PHASES, lbm.SCHED_SLABS, lbm.SCHED_FUSED])

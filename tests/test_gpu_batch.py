@@ -1,4 +1,5 @@
-"""Batched persistent stepping of uneven lattices against stepping each alone.
+"""Batched persistent stepping of uneven lattices against the FP64 oracle run on each
+domain alone, and against stepping each domain alone on the GPU.
 
 Every domain of a batch runs the same per-cell code as the single-lattice phase
 schedule (inlined into one persistent kernel, where a few FMAs contract
@@ -10,7 +11,8 @@ states unchanged; errors of one domain surface through lbm_batch_sync.
 import numpy as np
 import pytest
 
-from cases import F16_LOCAL
+from cases import F16_LOCAL, f32, pop_err
+from oracle import Oracle
 from paper_2206_00946_gb300 import lbm
 from paper_2206_00946_gb300 import workloads as W
 
@@ -43,6 +45,49 @@ def _domains(thermo):
 def _lat(p, rho0, T0, schedule=lbm.SCHED_PHASES):
     return lbm.Lattice(dict(p, schedule=schedule), rho0.reshape(-1).astype(np.float32),
                        T0.reshape(-1).astype(np.float32))
+
+
+@pytest.mark.parametrize("tune", [False, True])
+def test_batch_matches_the_oracle_on_every_domain(tune, thermo):
+    """Every domain of an uneven batch (sides 7 to 24, cell counts that are no multiple of
+    any tile size, walls, open faces, theta != 90) against the oracle stepping that domain
+    alone from the same FP32 state: populations within 1e-5 after one step, rho and T
+    within 1e-3 after 100.  Default launch shape (the persistent kernel) and the tuned one."""
+    doms = _domains(thermo)
+    states, lats = [], []
+    for p, rho0, T0 in doms:
+        f, g = Oracle(p).init_state(rho0, T0)
+        f, g = f32(f), f32(g)
+        states.append((f, g))
+        lat = lbm.Lattice(dict(p, schedule=lbm.SCHED_PHASES))
+        lat.lbm_set_state(f, g)
+        lats.append(lat)
+    assert any(lat.N % 1024 for lat in lats)
+    b = lbm.Batch(lats)
+    if tune:
+        b.lbm_batch_tune()
+    b.lbm_batch_step(1)
+    assert b.lbm_batch_sync() == lbm.OK
+    refs = []
+    for (p, _, _), (f, g), lat in zip(doms, states, lats):
+        o = Oracle(p)
+        st, fo, go = o.step(f.astype(np.float64), g.astype(np.float64))
+        assert st == 0
+        stg, fg, gg = lat.state()
+        assert stg == lbm.OK
+        assert pop_err(fg, fo, thermo) < 1e-5 and pop_err(gg, go, thermo) < 1e-5
+        refs.append((o, fo, go))
+    b.lbm_batch_step(99)
+    assert b.lbm_batch_sync() == lbm.OK
+    for (o, fo, go), lat in zip(refs, lats):
+        st, fo, go = o.run(fo, go, 99)
+        assert st == 0
+        stg, fg, gg = lat.state()
+        for a, r in ((fg.astype(np.float64).sum(0), fo.sum(0)), (gg.astype(np.float64).sum(0), go.sum(0))):
+            assert np.max(np.abs(a - r) / np.abs(r)) < 1e-3
+    b.close()
+    for lat in lats:
+        lat.close()
 
 
 @pytest.mark.parametrize("steps", [1, 13])

@@ -3,7 +3,10 @@
 The persistent schedule's work items wait, with a bound of about 2 s, for the planes they
 read to be finished.  lbm_inject_stall clears the plane-completion counters while keeping
 the step count, so that the next step's waits cannot be satisfied: the waits give up, the
-launch aborts, and the host reads LBM_ERR_TIMEOUT.  The context stays usable.
+launch aborts, and the host reads LBM_ERR_TIMEOUT.  The context stays usable.  The batched
+persistent launch waits at grid barriers with the same bound; lbm_batch_inject_stall
+fills the barrier's arrival counter so that it cannot complete, and after the timeout the
+batch steps like a new one once the domains' states are set again.
 """
 import time
 
@@ -65,3 +68,38 @@ def test_stall_injection_needs_the_persistent_schedule(thermo):
     lat.lbm_step(1)
     assert lat.lbm_inject_stall() == lbm.ERR_ARG
     lat.close()
+
+
+def test_batch_barrier_times_out_and_the_batch_recovers(thermo):
+    doms = [_droplet(thermo, lbm.SCHED_PHASES) for _ in range(2)]
+    lats = [lbm.Lattice(p, rho0, T0) for p, rho0, T0 in doms]
+    b = lbm.Batch(lats)
+    b.lbm_batch_step(2)
+    assert b.lbm_batch_sync() == lbm.OK
+    saved = [lat.state()[1:] for lat in lats]
+    assert b.lbm_batch_inject_stall() == lbm.OK
+    t0 = time.perf_counter()
+    b.lbm_batch_step(1)
+    st = b.lbm_batch_sync()
+    dt = time.perf_counter() - t0
+    assert st == lbm.ERR_TIMEOUT
+    assert 1.0 < dt < 60.0, dt
+    # states set again: the batch steps exactly like a new batch over the same states
+    for lat, (f, g) in zip(lats, saved):
+        lat.lbm_set_state(f, g)
+    b.lbm_batch_step(3)
+    assert b.lbm_batch_sync() == lbm.OK
+    fresh = [lbm.Lattice(doms[0][0]) for _ in lats]
+    for lat, (f, g) in zip(fresh, saved):
+        lat.lbm_set_state(f, g)
+    b2 = lbm.Batch(fresh)
+    b2.lbm_batch_step(3)
+    assert b2.lbm_batch_sync() == lbm.OK
+    for x, y in zip(lats, fresh):
+        _, f1, g1 = x.state()
+        _, f2, g2 = y.state()
+        assert np.array_equal(f1, f2) and np.array_equal(g1, g2)
+    b.close()
+    b2.close()
+    for lat in lats + fresh:
+        lat.close()

@@ -508,30 +508,3 @@ def test_full_size_pool_512(thermo):
     e_rho, e_T = rel(out["f16"][0], out["f32"][0]), rel(out["f16"][1], out["f32"][1])
     print(f"pool 512^3, 5 steps, FP16 vs FP32: rho {e_rho:.2e}, T {e_T:.2e}")
     assert e_rho < 5 * 1.2 * 2.0 ** -11 and e_T < 5 * 0.2 * 2.0 ** -11, (e_rho, e_T)
-
-
-@pytest.mark.parametrize("name", ["periodic", "open_all", "walls_z"])
-def test_bulk_staged_phase_c_matches_oracle(name, thermo, monkeypatch):
-    """The opt-in phase C that stages each tile's populations in shared memory with
-    cp.async.bulk (completion on an mbarrier; LBM_BULK set at lbm_init, FP32, N a
-    multiple of 4) gives the oracle's step, and agrees with the unstaged kernels over
-    20 steps."""
-    p = case_params(name, thermo)
-    f, g = droplet_state(p, thermo, seed=17)
-    st_o, fo, go = Oracle(p).step(f.astype(np.float64), g.astype(np.float64))
-    assert st_o == 0
-    monkeypatch.setenv("LBM_BULK", "1")
-    st, fg, gg = gpu_step(p, f, g, 1, lbm.SCHED_PHASES)
-    assert st == lbm.OK
-    assert pop_err(fg, fo, thermo) < 1e-5
-    assert pop_err(gg, go, thermo) < 1e-5
-    x, y, z = W.grid(p["nx"], p["ny"], p["nz"])
-    r2 = (x - 0.45 * p["nx"]) ** 2 + (y - 0.55 * p["ny"]) ** 2 + (z - 0.5 * p["nz"]) ** 2
-    rho0 = W.perturb(thermo["rho_v"] * (1.0 + 0.03 * np.exp(-r2 / 4.0)), 1e-3, seed=12)
-    f2, g2 = Oracle(p).init_state(rho0, np.full(rho0.shape, thermo["Ts"]))
-    f2, g2 = f32(f2), f32(g2)
-    _, fb, gb = gpu_step(p, f2, g2, 20, lbm.SCHED_PHASES)
-    monkeypatch.delenv("LBM_BULK")
-    _, fu, gu = gpu_step(p, f2, g2, 20, lbm.SCHED_PHASES)
-    assert np.max(np.abs(fb - fu)) <= 1e-5 * np.max(np.abs(fu))
-    assert np.max(np.abs(gb - gu)) <= 1e-5 * np.max(np.abs(gu))

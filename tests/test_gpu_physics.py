@@ -7,9 +7,16 @@
   starts after 8,000 steps, the thermal transient of this geometry (vapor
   diffusivity lambda/(rho_v c_v) = 0.18, 49 cells from face to interface).
   The paper prints only a figure, so the rate K itself is not pinned.
+* Two-phase conduction (Sec. 4.1): the 1 x 1 x 40 column with vapour next to a wall at
+  T_c and liquid next to a wall at T_s reaches the oracle's steady profile, whose bulk
+  slope ratio is lambda_l / lambda_v within the band the oracle pin checks.
 """
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
+
+from oracle import Oracle
 
 from paper_2206_00946_gb300 import lbm
 from paper_2206_00946_gb300 import workloads as W
@@ -48,3 +55,34 @@ def test_d2_law_is_linear_after_the_thermal_transient(thermo):
     r2 = 1 - np.sum((y[sel] - np.polyval(a, t[sel])) ** 2) / np.sum((y[sel] - y[sel].mean()) ** 2)
     print(f"d2 law: K = {-a[0]:.3e} per step (in V^(2/3)), R^2 = {r2:.5f}")
     assert a[0] < 0 and r2 >= 0.99, r2
+
+
+def test_sec41_column_reaches_the_oracle_steady_profile(thermo):
+    p, rho0, T0 = W.conduction_column(thermo["Tc"], thermo["rho_v"], thermo["rho_l"])
+    steps = 600_000  # the oracle is steady (< 1e-10 per 1000 steps) after 0.55 M steps
+
+    def oracle_profile():
+        o = Oracle(p)
+        f, g = o.init_state(rho0, T0)
+        st, f, g = o.run(f, g, steps)
+        assert st == 0
+        return g.sum(0), f.sum(0)
+
+    with ThreadPoolExecutor(1) as ex:
+        ref = ex.submit(oracle_profile)
+        lat = lbm.Lattice(dict(p, schedule=lbm.SCHED_SLABS), rho0.reshape(-1).astype(np.float32),
+                          T0.reshape(-1).astype(np.float32))
+        lat.lbm_step(steps)
+        st, f, g = lat.state()
+        lat.close()
+        To, rho_o = ref.result()
+    assert st == lbm.OK
+    T, rho = g.astype(np.float64).sum(0), f.astype(np.float64).sum(0)
+    eT, erho = np.max(np.abs(T - To) / To), np.max(np.abs(rho - rho_o) / rho_o)
+    z = np.arange(p["nz"], dtype=float)
+    zi = np.interp(0.5 * (thermo["rho_v"] + thermo["rho_l"]), rho, z)
+    vap, liq = (z >= 2) & (z <= zi - 8), (z >= zi + 8) & (z <= p["nz"] - 3)
+    ratio = np.polyfit(z[vap], T[vap], 1)[0] / np.polyfit(z[liq], T[liq], 1)[0]
+    print(f"Sec. 4.1 column on the GPU: slope ratio {ratio:.4f}, max rel err T {eT:.2e}, rho {erho:.2e}")
+    assert eT < 1e-3 and erho < 1e-3
+    assert 1.90 <= ratio <= 2.05

@@ -60,3 +60,35 @@ def test_static_scratch_rejects_sizes_beyond_its_maximum():
     assert st == lbm.ERR_ARG
     with pytest.raises(ValueError):
         lbm.lbm_reduce_static(dummy, dummy, 4096 * 8192 + 1, 5.0, 0.38, 6.5, out, None)
+
+
+def test_static_scratch_counts_a_non_finite_cell_like_lbm_reduce():
+    """One population set to NaN: the cell is counted in out[3] and left out of the three
+    sums, exactly as lbm_reduce does on the same state."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p0 = W.base_params(4, 4, 4)
+    Tc = lbm.lbm_Tc(p0)
+    rv, rl, _ = lbm.lbm_maxwell(p0, 0.86 * Tc)
+    n = 16
+    p, rho0, T0 = W.droplet(Tc, rv, rl, n=n, R=4.0, W=3.0, seed=5)
+    N = p["nx"] * p["ny"] * p["nz"]
+    f, g = W.random_populations(n, n, n, rho0.reshape(-1), T0.reshape(-1), W.W19, W.w7(p["wbar"]), 0.01, 5)
+    f[7, 123] = np.nan
+    f_d = torch.tensor(f, dtype=torch.float32, device="cuda").contiguous()
+    g_d = torch.tensor(g, dtype=torch.float32, device="cuda").contiguous()
+    lat = lbm.Lattice(p)
+    lat.lbm_set_state(f_d, g_d)
+    st, ref = lat.lbm_reduce()
+    lat.close()
+    assert st in (lbm.OK, lbm.ERR_NONFINITE)
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    st = lbm.lbm_reduce_static(f_d, g_d, N, p["cv"], p["rho_v"], p["rho_l"], out,
+                               torch.cuda.current_stream().cuda_stream)
+    assert st == lbm.OK
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert got[3] == ref[3] == 1
+    np.testing.assert_allclose(got[:3], ref[:3], rtol=1e-9)
+    assert np.all(np.isfinite(got[:3]))
