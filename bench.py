@@ -62,6 +62,8 @@ def kernel_alg_bytes(kernel: str, esize: int):
     return {"phaseC": 2 * 19 * esize,   # D3Q19 collide + push: f read and written
             "phaseC7": 2 * 7 * esize,   # D3Q7 collide + relaxed push: g read and written
             "phaseA": 26 * esize,       # macroscopic fields: f and g read
+            "march19": 45 * esize,      # macros, force, D3Q19 collide + push: f and g read, f written
+            "march7": 2 * 7 * esize,    # D3Q7 collide + relaxed push: g read and written
             "fused": 2 * 26 * esize}.get(kernel)
 WORKLOADS = {
     "sessile": "droplet on a heated surface 256x256x128, R=30, W=5, bottom wall 0.96 T_c (theta 90), "
@@ -486,7 +488,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sessile", choices=list(WORKLOADS))
     ap.add_argument("--n", type=int, default=128, help="lattice side of the droplet workload (128)")
-    ap.add_argument("--schedule", default="slabs", choices=["fused", "phases", "slabs"])
+    ap.add_argument("--schedule", default="slabs", choices=["fused", "phases", "slabs", "march"])
     ap.add_argument("--storage", default="f32", choices=list(STORAGE))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward cost measurement")
@@ -514,7 +516,8 @@ def main():
 
     Tc, rv, rl = thermo_product()
     p, rho0, T0 = workload(args.workload, Tc, rv, rl, args.n)
-    p["schedule"] = {"fused": lbm.SCHED_FUSED, "phases": lbm.SCHED_PHASES, "slabs": lbm.SCHED_SLABS}[args.schedule]
+    p["schedule"] = {"fused": lbm.SCHED_FUSED, "phases": lbm.SCHED_PHASES, "slabs": lbm.SCHED_SLABS,
+                     "march": lbm.SCHED_MARCH}[args.schedule]
     p["storage"], esize = STORAGE[args.storage]
     step_bytes = 26 * 2 * esize  # algorithmic bytes per lattice update in this storage
     N = p["nx"] * p["ny"] * p["nz"]
@@ -560,7 +563,7 @@ def main():
     # concurrent sub-range launches, so its kernels are timed here in the phase
     # schedule: the same kernels, one launch per phase over the whole lattice.
     nl = min(args.steps, 200)
-    q = dict(p, schedule=p["schedule"] if args.schedule == "fused" else lbm.SCHED_PHASES)
+    q = dict(p, schedule=p["schedule"] if args.schedule in ("fused", "march") else lbm.SCHED_PHASES)
     latp = lbm.Lattice(q, rho_d, T_d, stream=stream.cuda_stream)
     latp.lbm_step(args.warmup)
     latp.lbm_profile(True)
@@ -645,7 +648,9 @@ def main():
                      "frac": achieved / peak if achieved else None, "traffic": traffic,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)",
                      "kernel": dom, "alg_bytes_per_cell": alg, "per_launch_ms": per_launch_ms,
-                     "kernel_timing": "CUDA events on the kernel's stream, phase schedule, whole-lattice launches",
+                     "kernel_timing": ("CUDA events on the kernel's stream, "
+                                       + ("z-marching schedule" if args.schedule == "march" else
+                                          "phase schedule, whole-lattice launches")),
                      "kernel_src_sha": digest,
                      "step_bytes_per_lu": step_bytes,
                      "step_effective_GBs": step_bytes * N / (ms_step * 1e-3) / 1e9,

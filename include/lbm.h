@@ -38,6 +38,8 @@
  * beyond rounding):
  *   LBM_SLAB_PLANES, LBM_SLAB_STREAMS, LBM_GRAPH_STEPS  planes per slab, streams
  *       and steps per CUDA graph of the pipelined slab schedule (read by lbm_init);
+ *   LBM_MARCH_ZCHUNKS  z-ranges per tile column of the z-marching schedule (read by
+ *       lbm_init; by default chosen from the lattice and the occupancy);
  *   LBM_ADJ_EAGER, LBM_ADJ_NOPDL  launch every adjoint step on its own instead of
  *       replaying K-step segments from graphs / without programmatic dependent
  *       launches (read by each lbm_adjoint_step).
@@ -73,7 +75,7 @@ typedef enum {
                                  step that wrote it (8 bytes per cell, twice, kept by the library) */
 } lbm_storage;
 typedef enum { LBM_MEM_DEVICE = 0, LBM_MEM_HOST = 1 } lbm_mem;
-typedef enum { LBM_SCHED_FUSED = 0, LBM_SCHED_PHASES = 1, LBM_SCHED_SLABS = 2 } lbm_schedule;
+typedef enum { LBM_SCHED_FUSED = 0, LBM_SCHED_PHASES = 1, LBM_SCHED_SLABS = 2, LBM_SCHED_MARCH = 3 } lbm_schedule;
 
 /* Problem statement.  Physical parameters follow the paper's notation. */
 typedef struct lbm_params {
@@ -94,7 +96,11 @@ typedef struct lbm_params {
                                     taken to be at rest before, and checkpoints carry the history);
                                     lbm_record and batching need 0 */
   int meq_printed;               /* 0: m^eq = M-hat f^eq; 1: rows 16-18 exactly as printed in Eq. 9 */
-  int wall_ueq_zero;             /* 1: u^eq = 0 and u = 0 at bounce-back wall nodes (Sec. 3.1) */
+  int wall_ueq_zero;             /* at bounce-back wall nodes the real velocity u is 0 (Sec. 3.1: the
+                                    wall-node velocity is specified by the no-slip condition) in the
+                                    outputs, in div u and in Fbar; the collision's u^eq there is 0
+                                    when 1 (the node's momentum leaves the collision as F), or the
+                                    node's own j / rho when 0 */
   int eos_kind;                  /* 0: Peng-Robinson; 1: ideal gas p = eos_c0 * rho (verification) */
   double eos_c0;
   int face_kind[6];              /* lbm_face_kind per face; periodic faces come in pairs; a wall face
@@ -108,8 +114,13 @@ typedef struct lbm_params {
   double store_rho_ref;          /* global shift rho_ref of the 16-bit storage (e.g. rho_v) */
   double store_T_ref;            /* global shift T_ref of the 16-bit storage (e.g. the mean temperature) */
   int schedule;                  /* lbm_schedule: one persistent launch per step (FUSED), one launch
-                                    per phase (PHASES), or per phase and z-slab on several streams,
-                                    replayed from a CUDA graph (SLABS) */
+                                    per phase (PHASES), per phase and z-slab on several streams,
+                                    replayed from a CUDA graph (SLABS), or two z-marching stencil
+                                    kernels that read the populations once (phases A, B and the
+                                    D3Q19 part of C in one, the D3Q7 part in the other) followed by
+                                    the face rules, replayed from a CUDA graph (MARCH; walls must
+                                    have a contact angle of 90 degrees and 19 N must fit in 32 bits,
+                                    else LBM_ERR_ARG) */
 } lbm_params;
 
 /* Creates a context on the current CUDA device and, if rho0 and T0 are not
@@ -261,8 +272,9 @@ int lbm_maxwell(const lbm_params* p, double T, double* rho_v, double* rho_l, dou
  * first nkinds kernel kinds, the number of launches and their total device
  * time in milliseconds since the last clear (host arrays, may be NULL).
  * Kinds: 0 phase A (macro/psi), 1 phase B (force/velocity), 2 phase C
- * (D3Q19 collide + stream, or both lattices when staged), 3 phase D
- * (boundary), 4 fused step, 5 phase C of the D3Q7 lattice (side stream). */
+ * (D3Q19 collide + stream), 3 phase D (boundary), 4 fused step, 5 phase C of
+ * the D3Q7 lattice, 6 the z-marching kernel of phases A, B and the D3Q19 part
+ * of C, 7 the z-marching kernel of the D3Q7 part of C. */
 int lbm_profile(lbm_ctx* ctx, int enable);
 int lbm_profile_read(lbm_ctx* ctx, long long* launches, double* ms, int nkinds);
 

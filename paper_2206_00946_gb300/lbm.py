@@ -21,7 +21,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_PSI_DOMAIN, ERR_TIMEOUT, ERR_STATE = 0
 FACE_PERIODIC, FACE_WALL, FACE_OPEN = 0, 1, 2
 STORE_F32, STORE_F16_SHIFTED, STORE_BF16_SHIFTED, STORE_F16_LOCAL = 0, 1, 2, 3
 MEM_DEVICE, MEM_HOST = 0, 1
-SCHED_FUSED, SCHED_PHASES, SCHED_SLABS = 0, 1, 2
+SCHED_FUSED, SCHED_PHASES, SCHED_SLABS, SCHED_MARCH = 0, 1, 2, 3
 
 _D = ct.c_double
 
@@ -47,7 +47,7 @@ EXPORTS = ["lbm_init", "lbm_set_state", "lbm_get_state", "lbm_set_face_T", "lbm_
            "lbm_checkpoint_bytes", "lbm_checkpoint", "lbm_restore", "lbm_record", "lbm_adjoint_step",
            "lbm_adjoint_state", "lbm_batch_create", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_sync",
            "lbm_batch_cells", "lbm_batch_destroy", "lbm_batch_inject_stall", "lbm_inject_stall"]
-PROFILE_KINDS = ["phaseA", "phaseB", "phaseC", "phaseD", "fused", "phaseC7"]
+PROFILE_KINDS = ["phaseA", "phaseB", "phaseC", "phaseD", "fused", "phaseC7", "march19", "march7"]
 
 _lib = None
 
