@@ -19,14 +19,14 @@ The JSON line also carries the roofline of the dominant kernel (each kernel time
 alone with CUDA events in the phase schedule, charged its own algorithmic bytes),
 the end-to-end rate through host buffers, the FP64 CPU oracle on a bounded sample
 on all host cores and on one (cpu_baseline), the 128^3 d^2-law droplet
-(droplet_128), the adjoint/forward cost on a 64^3 droplet over 2000 steps with
+(droplet_128), the paper's own geometries of Secs. 4.2 and 4.3 (paper_cases), the adjoint/forward cost on a 64^3 droplet over 2000 steps with
 checkpoints every 100 (adjoint), 48 uneven droplet domains stepped as one batch
 (batched), and the 512^3 heated-plate pool with 64 droplets in FP16-shifted
 storage (large), the step time with the correction term of Eq. 16
 (vartheta = 1) against without (vartheta), and the rate in each population
 storage form (storage_forms: FP32, FP16 and BF16 with one global shift, FP16
 with per-cell references); --no-adjoint / --no-batched / --no-large /
---no-vartheta / --no-storage / --no-droplet / --no-cpu-baseline skip those.
+--no-vartheta / --no-storage / --no-droplet / --no-paper-cases / --no-cpu-baseline skip those.
 
 N > 1 (torchrun, one rank per GPU) runs N independent replicas of the domain
 (weak scaling, no collective on the data path).  --impl reference times the
@@ -62,8 +62,6 @@ def kernel_alg_bytes(kernel: str, esize: int):
     return {"phaseC": 2 * 19 * esize,   # D3Q19 collide + push: f read and written
             "phaseC7": 2 * 7 * esize,   # D3Q7 collide + relaxed push: g read and written
             "phaseA": 26 * esize,       # macroscopic fields: f and g read
-            "march19": 45 * esize,      # macros, force, D3Q19 collide + push: f and g read, f written
-            "march7": 2 * 7 * esize,    # D3Q7 collide + relaxed push: g read and written
             "fused": 2 * 26 * esize}.get(kernel)
 WORKLOADS = {
     "sessile": "droplet on a heated surface 256x256x128, R=30, W=5, bottom wall 0.96 T_c (theta 90), "
@@ -377,6 +375,37 @@ def storage_cost(lbm, p, rho0, T0, stream, steps=2000, warmup=50):
     return out
 
 
+def paper_cases(lbm, Tc, rv, rl, stream, steps=400, warmup=20):
+    """Rates of the paper's own geometries, FP32, slab schedule: the d^2-law droplet of Sec. 4.2
+    as the paper runs it (100^3, R = 25, periodic velocity field, every boundary node layer held
+    at T_c) and the droplet on a heated surface of Sec. 4.3 (160 x 160 x 100, diameter 70,
+    contact angle 120 degrees, wall at 0.8931 T_c, the paper's a = 3/49)."""
+    import torch
+    out = {}
+    pa = W.base_params(4, 4, 4, a=3.0 / 49.0)
+    Tc3 = lbm.lbm_Tc(pa)
+    cases = {"sec42_droplet_100": W.droplet(Tc, rv, rl, n=100, R=25.0, faces=W.PERIODIC),
+             "sec43_heated_surface_160x160x100": W.heated_surface(Tc3, rv, rl)}
+    for name, (p, rho0, T0) in cases.items():
+        p = dict(p, schedule=lbm.SCHED_SLABS)
+        N = p["nx"] * p["ny"] * p["nz"]
+        lat = lbm.Lattice(p, torch.tensor(rho0.reshape(-1), dtype=torch.float32, device="cuda"),
+                          torch.tensor(T0.reshape(-1), dtype=torch.float32, device="cuda"), stream=stream.cuda_stream)
+        lat.lbm_step(warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lat.lbm_step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = lat.lbm_sync()
+        lat.close()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = ({"cells": N, "steps": steps, "value": N / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms}
+                     if st == lbm.OK else {"status": lbm.lbm_status_string(st)})
+    return out
+
+
 def thermo_product():
     """T_c and the coexistence densities from the library's host helpers (not the oracle)."""
     from paper_2206_00946_gb300 import lbm
@@ -488,7 +517,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sessile", choices=list(WORKLOADS))
     ap.add_argument("--n", type=int, default=128, help="lattice side of the droplet workload (128)")
-    ap.add_argument("--schedule", default="slabs", choices=["fused", "phases", "slabs", "march"])
+    ap.add_argument("--schedule", default="slabs", choices=["fused", "phases", "slabs"])
     ap.add_argument("--storage", default="f32", choices=list(STORAGE))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward cost measurement")
@@ -498,6 +527,7 @@ def main():
     ap.add_argument("--no-vartheta", action="store_true", help="skip the vartheta = 1 cost measurement")
     ap.add_argument("--no-storage", action="store_true", help="skip the storage-form comparison")
     ap.add_argument("--no-droplet", action="store_true", help="skip the 128^3 droplet rate")
+    ap.add_argument("--no-paper-cases", action="store_true", help="skip the Sec. 4.2 and 4.3 geometries")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = dist_env()
@@ -516,8 +546,7 @@ def main():
 
     Tc, rv, rl = thermo_product()
     p, rho0, T0 = workload(args.workload, Tc, rv, rl, args.n)
-    p["schedule"] = {"fused": lbm.SCHED_FUSED, "phases": lbm.SCHED_PHASES, "slabs": lbm.SCHED_SLABS,
-                     "march": lbm.SCHED_MARCH}[args.schedule]
+    p["schedule"] = {"fused": lbm.SCHED_FUSED, "phases": lbm.SCHED_PHASES, "slabs": lbm.SCHED_SLABS}[args.schedule]
     p["storage"], esize = STORAGE[args.storage]
     step_bytes = 26 * 2 * esize  # algorithmic bytes per lattice update in this storage
     N = p["nx"] * p["ny"] * p["nz"]
@@ -563,7 +592,7 @@ def main():
     # concurrent sub-range launches, so its kernels are timed here in the phase
     # schedule: the same kernels, one launch per phase over the whole lattice.
     nl = min(args.steps, 200)
-    q = dict(p, schedule=p["schedule"] if args.schedule in ("fused", "march") else lbm.SCHED_PHASES)
+    q = dict(p, schedule=p["schedule"] if args.schedule == "fused" else lbm.SCHED_PHASES)
     latp = lbm.Lattice(q, rho_d, T_d, stream=stream.cuda_stream)
     latp.lbm_step(args.warmup)
     latp.lbm_profile(True)
@@ -609,6 +638,9 @@ def main():
     droplet = None
     if args.workload != "droplet" and not args.no_droplet:
         droplet = droplet_rate(lbm, Tc, rv, rl, stream)
+    papers = None
+    if args.storage == "f32" and not args.no_paper_cases:
+        papers = paper_cases(lbm, Tc, rv, rl, stream)
 
     if rank != 0:
         if dist:
@@ -648,9 +680,7 @@ def main():
                      "frac": achieved / peak if achieved else None, "traffic": traffic,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)",
                      "kernel": dom, "alg_bytes_per_cell": alg, "per_launch_ms": per_launch_ms,
-                     "kernel_timing": ("CUDA events on the kernel's stream, "
-                                       + ("z-marching schedule" if args.schedule == "march" else
-                                          "phase schedule, whole-lattice launches")),
+                     "kernel_timing": "CUDA events on the kernel's stream, phase schedule, whole-lattice launches",
                      "kernel_src_sha": digest,
                      "step_bytes_per_lu": step_bytes,
                      "step_effective_GBs": step_bytes * N / (ms_step * 1e-3) / 1e9,
@@ -659,6 +689,7 @@ def main():
                                      "share": v[1] / sum(w[1] for w in prof.values())} for k, v in prof.items()}},
         "cpu_baseline": cpu,
         "droplet_128": droplet,
+        "paper_cases": papers,
         "adjoint": adj,
         "batched": batched,
         "large": large,

@@ -38,8 +38,6 @@
  * beyond rounding):
  *   LBM_SLAB_PLANES, LBM_SLAB_STREAMS, LBM_GRAPH_STEPS  planes per slab, streams
  *       and steps per CUDA graph of the pipelined slab schedule (read by lbm_init);
- *   LBM_MARCH_ZCHUNKS  z-ranges per tile column of the z-marching schedule (read by
- *       lbm_init; by default chosen from the lattice and the occupancy);
  *   LBM_ADJ_EAGER, LBM_ADJ_NOPDL  launch every adjoint step on its own instead of
  *       replaying K-step segments from graphs / without programmatic dependent
  *       launches (read by each lbm_adjoint_step).
@@ -75,7 +73,7 @@ typedef enum {
                                  step that wrote it (8 bytes per cell, twice, kept by the library) */
 } lbm_storage;
 typedef enum { LBM_MEM_DEVICE = 0, LBM_MEM_HOST = 1 } lbm_mem;
-typedef enum { LBM_SCHED_FUSED = 0, LBM_SCHED_PHASES = 1, LBM_SCHED_SLABS = 2, LBM_SCHED_MARCH = 3 } lbm_schedule;
+typedef enum { LBM_SCHED_FUSED = 0, LBM_SCHED_PHASES = 1, LBM_SCHED_SLABS = 2 } lbm_schedule;
 
 /* Problem statement.  Physical parameters follow the paper's notation. */
 typedef struct lbm_params {
@@ -114,13 +112,14 @@ typedef struct lbm_params {
   double store_rho_ref;          /* global shift rho_ref of the 16-bit storage (e.g. rho_v) */
   double store_T_ref;            /* global shift T_ref of the 16-bit storage (e.g. the mean temperature) */
   int schedule;                  /* lbm_schedule: one persistent launch per step (FUSED), one launch
-                                    per phase (PHASES), per phase and z-slab on several streams,
-                                    replayed from a CUDA graph (SLABS), or two z-marching stencil
-                                    kernels that read the populations once (phases A, B and the
-                                    D3Q19 part of C in one, the D3Q7 part in the other) followed by
-                                    the face rules, replayed from a CUDA graph (MARCH; walls must
-                                    have a contact angle of 90 degrees and 19 N must fit in 32 bits,
-                                    else LBM_ERR_ARG) */
+                                    per phase (PHASES), or per phase and z-slab on several streams,
+                                    replayed from a CUDA graph (SLABS) */
+  int face_T_fixed[6];           /* 1: the node layer of face f holds the Dirichlet temperature
+                                    face_T[f] (non-equilibrium extrapolation, Sec. 3.1) even where
+                                    the face is periodic for the flow -- the droplet of Sec. 4.2
+                                    (periodic velocity field, temperature fixed at the boundaries);
+                                    non-periodic faces hold theirs regardless.  A periodic axis with
+                                    a held layer needs >= 3 cells; lbm_record needs 0 everywhere */
 } lbm_params;
 
 /* Creates a context on the current CUDA device and, if rho0 and T0 are not
@@ -273,8 +272,7 @@ int lbm_maxwell(const lbm_params* p, double T, double* rho_v, double* rho_l, dou
  * time in milliseconds since the last clear (host arrays, may be NULL).
  * Kinds: 0 phase A (macro/psi), 1 phase B (force/velocity), 2 phase C
  * (D3Q19 collide + stream), 3 phase D (boundary), 4 fused step, 5 phase C of
- * the D3Q7 lattice, 6 the z-marching kernel of phases A, B and the D3Q19 part
- * of C, 7 the z-marching kernel of the D3Q7 part of C. */
+ * the D3Q7 lattice. */
 int lbm_profile(lbm_ctx* ctx, int enable);
 int lbm_profile_read(lbm_ctx* ctx, long long* launches, double* ms, int nkinds);
 

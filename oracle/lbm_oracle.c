@@ -421,6 +421,9 @@ int orc_check(const orc_params* P) {
     if ((k0 == ORC_PERIODIC) != (k1 == ORC_PERIODIC)) return ORC_ERR_ARG;
     if (k0 != ORC_PERIODIC && dims(P, a) < 3) return ORC_ERR_ARG;
   }
+  /* a node layer held at a fixed temperature on a periodic axis needs an inward neighbour */
+  for (int f = 0; f < 6; ++f)
+    if (P->face_T_fixed[f] && P->face_kind[f] == ORC_PERIODIC && dims(P, f / 2) < 3) return ORC_ERR_ARG;
   /* a wall face may not share an edge with an open face */
   for (int f1 = 0; f1 < 6; ++f1)
     for (int f2 = 0; f2 < 6; ++f2)
@@ -436,6 +439,19 @@ static int node_faces(const orc_params* P, int x, int y, int z) {
     if (q[a] == 0) m |= 1 << (2 * a);
     if (q[a] == dims(P, a) - 1) m |= 1 << (2 * a + 1);
   }
+  return m;
+}
+
+/* bit f set <=> the node lies on face f and that face's node layer carries a Dirichlet
+ * temperature: every non-periodic face, and a periodic face marked face_T_fixed */
+static int node_tfaces(const orc_params* P, int x, int y, int z) {
+  int q[3] = {x, y, z}, m = 0;
+  for (int a = 0; a < 3; ++a)
+    for (int s = 0; s < 2; ++s) {
+      const int f = 2 * a + s;
+      if (P->face_kind[f] == ORC_PERIODIC && !P->face_T_fixed[f]) continue;
+      if (q[a] == (s ? dims(P, a) - 1 : 0)) m |= 1 << f;
+    }
   return m;
 }
 
@@ -839,7 +855,7 @@ static int step_impl(const orc_params* P, const double* const* Tface, const doub
   for (int z = 0; z < nz; ++z)
       for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
-          int m = node_faces(P, x, y, z);
+          int m = node_tfaces(P, x, y, z);
           if (!m) continue;
           int q[3] = {x, y, z}, nf = 0;
           double Tb = 0.0;

@@ -39,6 +39,10 @@ typedef struct {
   double face_T[6];                  /* Dirichlet temperature of each non-periodic face */
   double face_rho[6];                /* prescribed density of an open (constant-pressure) face */
   double face_theta_deg[6];          /* contact angle of a wall face (Eq. 36) */
+  int face_T_fixed[6];               /* 1: the node layer of face f holds the Dirichlet temperature
+                                        face_T[f] even where the face is periodic for the flow
+                                        (the droplet of Sec. 4.2: periodic velocity field,
+                                        temperature fixed at the boundaries) */
 } orc_params;
 
 /* Optional per-cell fields at time t written by orc_step / orc_macros (NULL = skip). */

@@ -31,7 +31,7 @@ class OrcParams(ct.Structure):
         ("vartheta", ct.c_int), ("meq_printed", ct.c_int), ("wall_ueq_zero", ct.c_int),
         ("eos_kind", ct.c_int), ("eos_c0", _D),
         ("face_kind", ct.c_int * 6), ("face_T", _D * 6), ("face_rho", _D * 6),
-        ("face_theta_deg", _D * 6),
+        ("face_theta_deg", _D * 6), ("face_T_fixed", ct.c_int * 6),
     ]
 
 

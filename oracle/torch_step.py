@@ -71,6 +71,8 @@ class TorchStep:
         for fc, k in enumerate(self.kind):
             if k == WALL and float(p["face_theta_deg"][fc]) != 90.0:
                 raise NotImplementedError("wetting ghost layer with theta != 90 degrees")
+            if k == PERIODIC and int(p.get("face_T_fixed", [0] * 6)[fc]):
+                raise NotImplementedError("held temperature layer on a periodic face")
         dt = torch.float64
         self.M = torch.tensor(mhat_rows(C19), dtype=dt)
         self.Minv = torch.linalg.inv(self.M)

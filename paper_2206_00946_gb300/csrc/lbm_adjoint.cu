@@ -754,7 +754,9 @@ extern "C" int lbm_record(lbm_ctx* c, int n, int K) {
   if (!c->has_state) return LBM_ERR_STATE;
   if (c->hp.storage != LBM_STORE_F32 || c->hp.vartheta) return LBM_ERR_ARG;
   for (int f = 0; f < 6; ++f)
-    if (c->hp.face_kind[f] == LBM_FACE_WALL && c->hp.face_theta_deg[f] != 90.0) return LBM_ERR_ARG;
+    if ((c->hp.face_kind[f] == LBM_FACE_WALL && c->hp.face_theta_deg[f] != 90.0) ||
+        (c->hp.face_kind[f] == LBM_FACE_PERIODIC && c->hp.face_T_fixed[f]))
+      return LBM_ERR_ARG;
   adj_free(c);
   AdjRec* r = new (std::nothrow) AdjRec();
   if (!r) return LBM_ERR_ARG;

@@ -11,7 +11,6 @@
 
 #include "lbm.h"
 #include "lbm_fused.cuh"
-#include "lbm_march.cuh"
 #include "lbm_phases.cuh"
 #include "lbm_ctx.cuh"
 
@@ -130,7 +129,7 @@ __global__ void __launch_bounds__(256, 3) k_phaseD(Params P, T* fB, T* gB, AuxFo
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < (int)P.bd_total; k += gridDim.x * blockDim.x) {
     int x, y, z;
     boundary_candidate(P, k, x, y, z);
-    const int m = node_faces(P, x, y, z);
+    const int m = node_tfaces(P, x, y, z);
     if (m) phaseD(P, cell_of(P, x, y, z), x, y, z, m, fB, gB, X);
   }
 }
@@ -143,7 +142,7 @@ __global__ void __launch_bounds__(256, 3) k_phaseD_planes(Params P, T* fB, T* gB
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
     int x, y;
     boundary_xy(P, z, k, x, y);
-    const int m = node_faces(P, x, y, z);
+    const int m = node_tfaces(P, x, y, z);
     if (m) phaseD(P, cell_of(P, x, y, z), x, y, z, m, fB, gB, X);
   }
 }
@@ -256,15 +255,8 @@ int check_params(const lbm_params* p) {
       p->storage != LBM_STORE_F16_LOCAL)
     return LBM_ERR_ARG;
   if (p->storage != LBM_STORE_F32 && p->schedule == LBM_SCHED_FUSED) return LBM_ERR_ARG;  // FP32 only
-  if (p->schedule != LBM_SCHED_FUSED && p->schedule != LBM_SCHED_PHASES && p->schedule != LBM_SCHED_SLABS &&
-      p->schedule != LBM_SCHED_MARCH)
+  if (p->schedule != LBM_SCHED_FUSED && p->schedule != LBM_SCHED_PHASES && p->schedule != LBM_SCHED_SLABS)
     return LBM_ERR_ARG;
-  if (p->schedule == LBM_SCHED_MARCH) {
-    // population offsets are 32-bit there; walls need the 90-degree ghost rule
-    if (19LL * N > 4294967295LL) return LBM_ERR_ARG;
-    for (int f = 0; f < 6; ++f)
-      if (p->face_kind[f] == LBM_FACE_WALL && p->face_theta_deg[f] != 90.0) return LBM_ERR_ARG;
-  }
   if (p->eos_kind != 0 && p->eos_kind != 1) return LBM_ERR_ARG;
   if (!(p->cv > 0) || !(p->wbar > 0 && p->wbar < 1) || !(p->lambda_l > 0) || !(p->lambda_v > 0)) return LBM_ERR_ARG;
   if (p->lambda_l != p->lambda_v && !(p->rho_l > p->rho_v)) return LBM_ERR_ARG;
@@ -283,6 +275,10 @@ int check_params(const lbm_params* p) {
         return LBM_ERR_ARG;
   for (int f = 0; f < 6; ++f)
     if (p->face_kind[f] == LBM_FACE_OPEN && !(p->face_rho[f] > 0)) return LBM_ERR_ARG;
+  for (int f = 0; f < 6; ++f) {
+    if (p->face_T_fixed[f] != 0 && p->face_T_fixed[f] != 1) return LBM_ERR_ARG;
+    if (p->face_T_fixed[f] && p->face_kind[f] == LBM_FACE_PERIODIC && n[f / 2] < 3) return LBM_ERR_ARG;
+  }
   return LBM_OK;
 }
 
@@ -295,9 +291,10 @@ Params make_device_params(const lbm_params& p) {
   P.N = (long long)p.nx * p.ny * p.nz;
   fdiv_init((unsigned)p.nx, P.dnx_mul, P.dnx_shr);
   fdiv_init((unsigned)p.ny, P.dny_mul, P.dny_shr);
+  for (int f = 0; f < 6; ++f) P.tface[f] = p.face_kind[f] != LBM_FACE_PERIODIC || p.face_T_fixed[f] != 0;
   {
-    const bool xnp = p.face_kind[0] != LBM_FACE_PERIODIC, ynp = p.face_kind[2] != LBM_FACE_PERIODIC;
-    const bool znp = p.face_kind[4] != LBM_FACE_PERIODIC;
+    const bool xnp = P.tface[0] || P.tface[1], ynp = P.tface[2] || P.tface[3];
+    const bool znp = P.tface[4] || P.tface[5];
     P.bd_zplanes = znp ? 2 : 0;
     P.bd_perim = (xnp && ynp) ? 2 * p.nx + 2 * (p.ny - 2) : (xnp ? 2 * p.ny : (ynp ? 2 * p.nx : 0));
     fdiv_init((unsigned)(p.nx * p.ny), P.dpl_mul, P.dpl_shr);
@@ -338,7 +335,7 @@ Params make_device_params(const lbm_params& p) {
     double s = 0;
     int n = 0;
     for (int f = 0; f < 6; ++f)
-      if (p.face_kind[f] != LBM_FACE_PERIODIC) {
+      if (P.tface[f]) {
         s += p.face_T[f];
         ++n;
       }
@@ -693,7 +690,7 @@ int slab_enqueue_step_t(lbm_ctx* c, bool first) {
       default: {
         int maxcnt = 0;
         for (int z = z0; z < z1; ++z) {
-          const bool zb = c->P.face_kind[4] != FACE_PERIODIC && (z == 0 || z == c->P.nz - 1);
+          const bool zb = (c->P.tface[4] || c->P.tface[5]) && (z == 0 || z == c->P.nz - 1);
           maxcnt = std::max(maxcnt, zb ? plane : c->P.bd_perim);
         }
         dim3 gd((unsigned)std::max(1, (maxcnt + kThreads - 1) / kThreads), (unsigned)(z1 - z0));
@@ -788,113 +785,6 @@ int step_slabs(lbm_ctx* c, int n) {
   prof_end(c, 4, e);
   return st;
 }
-}  // namespace
-
-namespace {
-
-// ------------------------------------------------------------ z-marching --
-// Launch grid of the z-marching kernels: 32 x 8 tiles of the xy-plane times nzc z-ranges.
-// nzc fills the GPU with about one wave of CTAs; each z-range re-reads two planes next to
-// it (its neighbours' first or last), so ranges are kept to 8 planes or more.
-int march_plan_create(lbm_ctx* c) {
-  MarchPlan* M = new (std::nothrow) MarchPlan();
-  if (!M) return LBM_ERR_ARG;
-  c->march = M;
-  const int tx = (c->P.nx + kMarchTX - 1) / kMarchTX, ty = (c->P.ny + kMarchTY - 1) / kMarchTY;
-  int sms = 0, occ = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_march19<float>, kMarchThreads, 0);
-  const long long wave = (long long)std::max(1, sms) * std::max(1, occ);
-  const long long tiles = (long long)tx * ty;
-  int nzc = env_int("LBM_MARCH_ZCHUNKS", 0);
-  if (nzc <= 0) nzc = (int)std::max(1LL, std::min((long long)(c->P.nz / 8), wave / tiles));
-  nzc = std::max(1, std::min(nzc, c->P.nz));
-  M->zchunk = (c->P.nz + nzc - 1) / nzc;
-  nzc = (c->P.nz + M->zchunk - 1) / M->zchunk;
-  M->grid = dim3((unsigned)tx, (unsigned)ty, (unsigned)nzc);
-  M->graph_steps = std::max(0, env_int("LBM_GRAPH_STEPS", 8));
-  if (M->graph_steps & 1) M->graph_steps += 1;  // even: the buffers return to their parity
-  return cuda_status(cudaStreamCreateWithFlags(&M->cs, cudaStreamNonBlocking));
-}
-
-void march_plan_destroy(MarchPlan* M) {
-  if (!M) return;
-  for (int k = 0; k < 2; ++k)
-    if (M->graph[k]) cudaGraphExecDestroy(M->graph[k]);
-  if (M->cs) {
-    cudaStreamSynchronize(M->cs);
-    cudaStreamDestroy(M->cs);
-  }
-  delete M;
-}
-
-// One step (buffers cur -> 1 - cur) on stream s: the two marching kernels, then the face
-// rules on the new state.
-template <typename T>
-int march_enqueue_step_t(lbm_ctx* c, cudaStream_t s) {
-  const MarchPlan& M = *c->march;
-  const int a = c->cur, b = 1 - c->cur;
-  const AuxFor<T> X = aux_for<T>(c, a);
-  const bool prof = s == c->stream;
-  cudaEvent_t e = prof ? prof_begin(c) : nullptr;
-  k_march19<T><<<M.grid, kMarchThreads, 0, s>>>(c->P, fbuf<T>(c, a), gbuf<T>(c, a), fbuf<T>(c, b), X, c->err_d,
-                                                M.zchunk);
-  if (prof) prof_end(c, 6, e);
-  e = prof ? prof_begin(c) : nullptr;
-  if (c->P.vartheta)
-    k_march7<T, 1><<<M.grid, kMarchThreads, 0, s>>>(c->P, gbuf<T>(c, a), gbuf<T>(c, b), X, M.zchunk);
-  else
-    k_march7<T, 0><<<M.grid, kMarchThreads, 0, s>>>(c->P, gbuf<T>(c, a), gbuf<T>(c, b), X, M.zchunk);
-  if (prof) prof_end(c, 7, e);
-  if (c->P.bd_total > 0) {
-    e = prof ? prof_begin(c) : nullptr;
-    k_phaseD<T><<<grid_for(c->P.bd_total), kThreads, 0, s>>>(c->P, fbuf<T>(c, b), gbuf<T>(c, b), X);
-    if (prof) prof_end(c, 3, e);
-  }
-  c->cur = b;
-  return cuda_status(cudaGetLastError());
-}
-
-int march_enqueue_step(lbm_ctx* c, cudaStream_t s) { return LBM_WITH_STORAGE(c, march_enqueue_step_t, c, s); }
-
-// Captures graph_steps steps from buffer parity k into graph[k], for both parities.
-int march_capture_both(lbm_ctx* c) {
-  MarchPlan& M = *c->march;
-  if (M.graph_steps <= 0) return LBM_OK;
-  const int cur = c->cur;
-  int st = LBM_OK;
-  for (int k = 0; k < 2 && st == LBM_OK; ++k) {
-    c->cur = k;
-    cudaGraph_t g = nullptr;
-    if (cudaStreamBeginCapture(M.cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-      st = LBM_ERR_CUDA;
-      break;
-    }
-    for (int n = 0; n < M.graph_steps && st == LBM_OK; ++n) st = march_enqueue_step(c, M.cs);
-    const cudaError_t e = cudaStreamEndCapture(M.cs, &g);
-    if (st == LBM_OK && e == cudaSuccess && g)
-      st = cuda_status(cudaGraphInstantiate(&M.graph[k], g, 0));
-    else
-      st = LBM_ERR_CUDA;
-    if (g) cudaGraphDestroy(g);
-  }
-  c->cur = cur;
-  cudaGetLastError();
-  return st;
-}
-
-int step_march(lbm_ctx* c, int n) {
-  MarchPlan& M = *c->march;
-  int st = LBM_OK, done = 0;
-  // whole graphs while profiling is off (profiling times each kernel on its own)
-  if (!c->profiling && M.graph_steps > 0) {
-    for (; n - done >= M.graph_steps && st == LBM_OK; done += M.graph_steps)
-      st = cuda_status(cudaGraphLaunch(M.graph[c->cur], c->stream));  // parity unchanged: graph_steps is even
-  }
-  for (; done < n && st == LBM_OK; ++done) st = march_enqueue_step(c, c->stream);
-  return st;
-}
-
 }  // namespace
 
 namespace {
@@ -1086,7 +976,7 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
   ok = ok && cudaMalloc(&c->red_out, sizeof(double) * 4) == cudaSuccess;
   ok = ok && cudaMallocHost(&c->red_h, sizeof(double) * 4) == cudaSuccess;
   for (int f = 0; f < 6 && ok; ++f) {
-    if (p->face_kind[f] == LBM_FACE_PERIODIC) continue;
+    if (!c->P.tface[f]) continue;
     c->tface_n[f] = face_len(*p, f);
     ok = cudaMalloc(&c->tface[f], sizeof(float) * c->tface_n[f]) == cudaSuccess;
     if (ok) {
@@ -1107,14 +997,6 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
   if (cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream) != cudaSuccess) {
     lbm_destroy(c);
     return LBM_ERR_CUDA;
-  }
-  if (p->schedule == LBM_SCHED_MARCH) {
-    st = march_plan_create(c);
-    if (st == LBM_OK) st = march_capture_both(c);
-    if (st != LBM_OK) {
-      lbm_destroy(c);
-      return st;
-    }
   }
   if (p->schedule == LBM_SCHED_SLABS) {
     st = slab_plan_create(c);
@@ -1304,7 +1186,6 @@ int lbm_step(lbm_ctx* c, int n) {
   if (!c || n < 0) return LBM_ERR_ARG;
   if (!c->has_state) return LBM_ERR_STATE;
   if (c->hp.schedule == LBM_SCHED_SLABS) return n > 0 ? step_slabs(c, n) : LBM_OK;
-  if (c->hp.schedule == LBM_SCHED_MARCH) return n > 0 ? step_march(c, n) : LBM_OK;
   for (int s = 0; s < n; ++s) {
     int st;
     if (c->hp.schedule == LBM_SCHED_FUSED) {
@@ -1345,7 +1226,6 @@ int lbm_profile_read(lbm_ctx* c, long long* launches, double* ms, int nkinds) {
 int lbm_launches_per_step(const lbm_ctx* c) {
   if (!c) return 0;
   if (c->hp.schedule == LBM_SCHED_SLABS) return (int)c->slabs->order.size();
-  if (c->hp.schedule == LBM_SCHED_MARCH) return c->P.bd_total > 0 ? 3 : 2;
   if (c->hp.schedule == LBM_SCHED_FUSED) return fused_launches(&c->plan);
   return c->P.bd_total > 0 ? 4 : 3;
 }
@@ -1435,7 +1315,6 @@ void lbm_destroy(lbm_ctx* c) {
   for (int f = 0; f < 6; ++f) cudaFree(c->tface[f]);
   fused_free(&c->plan);
   slab_plan_destroy(c->slabs);
-  march_plan_destroy(c->march);
   if (c->evs) {
     for (auto& e : *c->evs) {
       cudaEventDestroy(e.a);

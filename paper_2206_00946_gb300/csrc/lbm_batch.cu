@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256) k_batch_step(BatchArgs A) {
         } else {
           int x, y, z;
           boundary_candidate(sP, c, x, y, z);
-          const int m = node_faces(sP, x, y, z);
+          const int m = node_tfaces(sP, x, y, z);
           if (m) phaseD<float>(sP, cell_of(sP, x, y, z), x, y, z, m, sD.f[b], sD.g[b], sD.X);
         }
       }
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256, 4) k_batch_phase(BatchArgs A) {
       } else {
         int x, y, z;
         boundary_candidate(sP, c, x, y, z);
-        const int m = node_faces(sP, x, y, z);
+        const int m = node_tfaces(sP, x, y, z);
         if (m) phaseD<float>(sP, cell_of(sP, x, y, z), x, y, z, m, sD.f[b], sD.g[b], sD.X);
       }
     }

@@ -107,8 +107,9 @@ struct Params {
   int face_kind[6];
   float face_rho[6];
   float tan_wet[6];  // tan(pi/2 - theta) of each wall face (Eq. 36)
-  const float* Tface[6];  // per-node Dirichlet temperature of each non-periodic face
+  const float* Tface[6];  // per-node Dirichlet temperature of each face that holds one (tface)
   int any_nonperiodic;
+  int tface[6];  // 1: the node layer of face f holds a Dirichlet T (non-periodic, or held)
 };
 
 // --------------------------------------------------------------- thermo ----

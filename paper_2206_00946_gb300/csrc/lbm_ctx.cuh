@@ -16,7 +16,7 @@ struct AdjRec;  // recorded forward run of the discrete adjoint (lbm_adjoint.cu)
 void adj_free(lbm_ctx* c);
 int lbm_step_phases_internal(lbm_ctx* c);  // one step, one launch per phase
 
-#define LBM_PROF_KINDS 8
+#define LBM_PROF_KINDS 6
 
 // Slab-pipelined schedule: the lattice is cut into slabs of whole z-planes and
 // every phase kernel runs per slab.  Stage (phase, slab) waits only for the
@@ -42,16 +42,6 @@ struct SlabPlan {
   std::vector<cudaEvent_t> ev;         // per stage code
   cudaEvent_t fork = nullptr, join[kMaxSlabStreams] = {};
   int graph_steps = 0;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-};
-
-// z-marching schedule: the launch grid (tiles of the xy-plane x z-ranges) and graphs of
-// graph_steps steps per buffer parity, captured on their own stream at lbm_init.
-struct MarchPlan {
-  dim3 grid;
-  int zchunk = 0;
-  int graph_steps = 0;
-  cudaStream_t cs = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
 };
 
@@ -82,7 +72,6 @@ struct lbm_ctx {
   cudaStream_t side;  // second stream for the D3Q7 collision
   cudaEvent_t ev_fork, ev_join;
   SlabPlan* slabs;    // slab-pipelined schedule (LBM_SCHED_SLABS)
-  MarchPlan* march;   // z-marching schedule (LBM_SCHED_MARCH)
   // kernel timing: event pairs bracketing each launch while profiling is on
   bool profiling;
   struct Ev {

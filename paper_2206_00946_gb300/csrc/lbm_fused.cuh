@@ -52,8 +52,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 __host__ __device__ inline bool plane_has_boundary(const Params& P, int z) {
-  if (P.face_kind[0] != FACE_PERIODIC || P.face_kind[2] != FACE_PERIODIC) return true;
-  return P.face_kind[4] != FACE_PERIODIC && (z == 0 || z == P.nz - 1);
+  if (P.tface[0] || P.tface[1] || P.tface[2] || P.tface[3]) return true;
+  return (P.tface[4] || P.tface[5]) && (z == 0 || z == P.nz - 1);
 }
 
 // Planes a stage reads from the previous phase: radius 1 for B and C, 2 for D.
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(256, LBM_FUSED_MINBLOCKS) k_fused(Params P, Au
       for (int k = t * A.tile + threadIdx.x; k < min(cnt, (t + 1) * A.tile); k += blockDim.x) {
         int x, y;
         boundary_xy(P, z, k, x, y);
-        const int m = node_faces(P, x, y, z);
+        const int m = node_tfaces(P, x, y, z);
         if (m) phaseD(P, cell_of(P, x, y, z), x, y, z, m, A.fB, A.gB, X);
       }
     } else {
@@ -250,7 +250,7 @@ inline int fused_plan(const Params& P, FusedPlan* plan, int threads = 256, int c
     const int ph = plan->stages_h[s] >> 24, z = plan->stages_h[s] & 0xffffff;
     long long n = plan->tiles_per_plane;
     if (ph == PH_D) {
-      const long long cnt = (P.face_kind[4] != FACE_PERIODIC && (z == 0 || z == P.nz - 1)) ? plane : P.bd_perim;
+      const long long cnt = ((P.tface[4] || P.tface[5]) && (z == 0 || z == P.nz - 1)) ? plane : P.bd_perim;
       n = std::max(1LL, (cnt + tile - 1) / tile);
     }
     plan->stage_first_h[s] = (int)items;

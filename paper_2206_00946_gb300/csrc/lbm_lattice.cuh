@@ -32,6 +32,19 @@ LBM_HD int node_faces(const Params& P, int x, int y, int z) {
   return m;
 }
 
+// bit f set <=> (x,y,z) lies on face f and that face's node layer holds a Dirichlet
+// temperature (every non-periodic face; a periodic face when held, Sec. 4.2)
+LBM_HD int node_tfaces(const Params& P, int x, int y, int z) {
+  int m = 0;
+  if (P.tface[0]) m |= (x == 0) ? 1 : 0;
+  if (P.tface[1]) m |= (x == P.nx - 1) ? 2 : 0;
+  if (P.tface[2]) m |= (y == 0) ? 4 : 0;
+  if (P.tface[3]) m |= (y == P.ny - 1) ? 8 : 0;
+  if (P.tface[4]) m |= (z == 0) ? 16 : 0;
+  if (P.tface[5]) m |= (z == P.nz - 1) ? 32 : 0;
+  return m;
+}
+
 LBM_HD bool on_open(const Params& P, int m) {
   bool o = false;
 #pragma unroll

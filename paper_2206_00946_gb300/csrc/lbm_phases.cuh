@@ -239,11 +239,14 @@ LBM_DEV void cell_xyz(const Params& P, int c, int& x, int& y, int& z) {
 }
 
 // Boundary nodes of plane z are enumerated as candidates k = 0..count-1: the
-// whole plane when z lies on a non-periodic z face, otherwise its perimeter
-// rows/columns on non-periodic x or y faces.
+// whole plane when z lies on a z face that holds a Dirichlet temperature, otherwise
+// its perimeter rows/columns on such x or y faces (non-periodic faces, and periodic
+// faces whose node layer is held).
+LBM_DEV bool axis_bounded(const Params& P, int a) { return P.tface[2 * a] || P.tface[2 * a + 1]; }
+
 LBM_DEV int boundary_count(const Params& P, int z) {
-  const bool xnp = P.face_kind[0] != FACE_PERIODIC, ynp = P.face_kind[2] != FACE_PERIODIC;
-  if (P.face_kind[4] != FACE_PERIODIC && (z == 0 || z == P.nz - 1)) return P.nx * P.ny;
+  const bool xnp = axis_bounded(P, 0), ynp = axis_bounded(P, 1);
+  if (axis_bounded(P, 2) && (z == 0 || z == P.nz - 1)) return P.nx * P.ny;
   if (xnp && ynp) return 2 * P.nx + 2 * (P.ny - 2);
   if (xnp) return 2 * P.ny;
   if (ynp) return 2 * P.nx;
@@ -251,8 +254,8 @@ LBM_DEV int boundary_count(const Params& P, int z) {
 }
 
 LBM_DEV void boundary_xy(const Params& P, int z, int k, int& x, int& y) {
-  const bool xnp = P.face_kind[0] != FACE_PERIODIC, ynp = P.face_kind[2] != FACE_PERIODIC;
-  if (P.face_kind[4] != FACE_PERIODIC && (z == 0 || z == P.nz - 1)) {
+  const bool xnp = axis_bounded(P, 0), ynp = axis_bounded(P, 1);
+  if (axis_bounded(P, 2) && (z == 0 || z == P.nz - 1)) {
     y = (int)fdiv((unsigned)k, P.dnx_mul, P.dnx_shr);
     x = k - y * P.nx;
   } else if (xnp && ynp) {
@@ -274,7 +277,7 @@ LBM_DEV void boundary_xy(const Params& P, int z, int k, int& x, int& y) {
 }
 
 // All boundary nodes of the lattice as one flat index range: the whole planes
-// z = 0 and nz-1 when the z faces are not periodic, then the perimeter
+// z = 0 and nz-1 when a z face holds a Dirichlet temperature, then the perimeter
 // candidates of the other planes.
 LBM_DEV void boundary_candidate(const Params& P, int idx, int& x, int& y, int& z) {
   const int plane = P.nx * P.ny;
@@ -320,21 +323,22 @@ LBM_DEV unsigned unknown19(const Params& P, int x, int y, int z) {
 }
 
 // The rules of phase D (constant-pressure open faces, Sec. 3.3; the
-// non-equilibrium extrapolation of g, Sec. 3.1) at a face node whose streamed
-// populations are in fl: the rewritten populations are stored (and replaced in
+// non-equilibrium extrapolation of g, Sec. 3.1) at a face node (m: node_tfaces)
+// whose streamed populations are in fl: the rewritten populations are stored (and replaced in
 // fl / gl by the values a later load returns).  Every load is issued before the
 // first store, so that the node's memory round trips overlap.
 template <typename ST>
 LBM_DEV void boundary_rules(const Params& P, int c, int x, int y, int z, int m, float* fl,
                                                   float* gl, ST* f, ST* g, const AuxFor<ST>& X) {
   const long long N = P.N;
-  int nnp = 0, nopen = 0, oface = -1;
+  int nnp = 0, nvel = 0, nopen = 0, oface = -1;  // faces holding T; of them, non-periodic; open
   float rb = 0.f, Tb = 0.f;
   int q[3] = {x, y, z};
 #pragma unroll
   for (int fc = 0; fc < 6; ++fc) {
     if (!((m >> fc) & 1)) continue;
     ++nnp;
+    if (P.face_kind[fc] != FACE_PERIODIC) ++nvel;
     if (P.face_kind[fc] == FACE_OPEN) {
       ++nopen;
       oface = fc;
@@ -354,12 +358,12 @@ LBM_DEV void boundary_rules(const Params& P, int c, int x, int y, int z, int m, 
     // one open face: Zou-He (writes only the unknowns); edges and corners of open
     // faces: every unknown = f^eq(rho_b, 0) = w_i rho_b, rho_b the faces' mean
     const unsigned unk = unknown19(P, x, y, z);
-    if (nnp == 1) zouhe(oface, P.face_rho[oface], Fx, Fy, Fz, fl);
+    if (nvel == 1) zouhe(oface, P.face_rho[oface], Fx, Fy, Fz, fl);
     const float rbm = rb / (float)nopen;
 #pragma unroll
     for (int i = 1; i < 19; ++i)
       if ((unk >> i) & 1u) {
-        const float v = nnp == 1 ? fl[i] : w19(i) * rbm;
+        const float v = nvel == 1 ? fl[i] : w19(i) * rbm;
         PopStore<ST>::st(f + i * N + c, v, fbase_at<ST>(P, i, rc.x));
         fl[i] = PopStore<ST>::round(v, fbase_at<ST>(P, i, rc.x));
       }

@@ -21,7 +21,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_PSI_DOMAIN, ERR_TIMEOUT, ERR_STATE = 0
 FACE_PERIODIC, FACE_WALL, FACE_OPEN = 0, 1, 2
 STORE_F32, STORE_F16_SHIFTED, STORE_BF16_SHIFTED, STORE_F16_LOCAL = 0, 1, 2, 3
 MEM_DEVICE, MEM_HOST = 0, 1
-SCHED_FUSED, SCHED_PHASES, SCHED_SLABS, SCHED_MARCH = 0, 1, 2, 3
+SCHED_FUSED, SCHED_PHASES, SCHED_SLABS = 0, 1, 2
 
 _D = ct.c_double
 
@@ -37,6 +37,7 @@ class lbm_params(ct.Structure):
         ("eos_kind", ct.c_int), ("eos_c0", _D),
         ("face_kind", ct.c_int * 6), ("face_T", _D * 6), ("face_rho", _D * 6), ("face_theta_deg", _D * 6),
         ("storage", ct.c_int), ("store_rho_ref", _D), ("store_T_ref", _D), ("schedule", ct.c_int),
+        ("face_T_fixed", ct.c_int * 6),
     ]
 
 
@@ -47,7 +48,7 @@ EXPORTS = ["lbm_init", "lbm_set_state", "lbm_get_state", "lbm_set_face_T", "lbm_
            "lbm_checkpoint_bytes", "lbm_checkpoint", "lbm_restore", "lbm_record", "lbm_adjoint_step",
            "lbm_adjoint_state", "lbm_batch_create", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_sync",
            "lbm_batch_cells", "lbm_batch_destroy", "lbm_batch_inject_stall", "lbm_inject_stall"]
-PROFILE_KINDS = ["phaseA", "phaseB", "phaseC", "phaseD", "fused", "phaseC7", "march19", "march7"]
+PROFILE_KINDS = ["phaseA", "phaseB", "phaseC", "phaseD", "fused", "phaseC7"]
 
 _lib = None
 

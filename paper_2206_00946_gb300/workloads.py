@@ -25,6 +25,7 @@ DEFAULTS = dict(
     vartheta=0, meq_printed=0, wall_ueq_zero=1, eos_kind=0, eos_c0=0.0, storage=0,
     store_rho_ref=0.0, store_T_ref=0.0,
     face_kind=[PERIODIC] * 6, face_T=[0.0] * 6, face_rho=[0.0] * 6, face_theta_deg=[90.0] * 6,
+    face_T_fixed=[0] * 6,
 )
 
 
@@ -124,9 +125,10 @@ def droplet(Tc, rho_v, rho_l, n=128, R=15.0, W=5.0, seed=2206, amp=1e-4, Ts_frac
     """Spherical droplet of radius R at the domain centre in vapor at coexistence density.
 
     faces=OPEN: constant-pressure faces (rho_b = rho_v) on all six sides with T = Tg;
-    faces=PERIODIC: the paper's own periodic velocity field.  T0 = T_s inside the
-    liquid, Tg outside, blended by the liquid fraction.  rho carries a seeded
-    uniform(-amp, amp) perturbation.
+    faces=PERIODIC: the paper's own setting of Sec. 4.2, a periodic velocity field with
+    the boundary node layers held at Tg.  T0 = T_s inside the liquid, Tg outside,
+    blended by the liquid fraction.  rho carries a seeded uniform(-amp, amp)
+    perturbation.
     """
     nx, ny, nz = (n, n, n) if shape is None else shape
     Ts, Tg = Ts_frac * Tc, Tg_frac * Tc
@@ -140,7 +142,8 @@ def droplet(Tc, rho_v, rho_l, n=128, R=15.0, W=5.0, seed=2206, amp=1e-4, Ts_frac
     T0 = Ts + (Tg - Ts) * (1.0 - phi)
     kinds = [faces] * 6
     p = base_params(nx, ny, nz, rho_l=rho_l, rho_v=rho_v, lambda_l=lam, lambda_v=lam,
-                    face_kind=kinds, face_T=[Tg] * 6, face_rho=[rho_v] * 6)
+                    face_kind=kinds, face_T=[Tg] * 6, face_rho=[rho_v] * 6,
+                    face_T_fixed=[1 if faces == PERIODIC else 0] * 6)
     return p, rho0, T0
 
 
@@ -161,6 +164,30 @@ def sessile(Tc, rho_v, rho_l, nx=256, ny=256, nz=128, R=30.0, W=5.0, dTw=0.1, Ts
     T0 = np.full_like(rho0, Ts)
     T0[0] = Tw
     p = base_params(nx, ny, nz, rho_l=rho_l, rho_v=rho_v, lambda_l=lam, lambda_v=lam,
+                    face_kind=[PERIODIC, PERIODIC, PERIODIC, PERIODIC, WALL, OPEN],
+                    face_T=[0, 0, 0, 0, Tw, Ts], face_rho=[0, 0, 0, 0, 0, rho_v],
+                    face_theta_deg=[90, 90, 90, 90, theta, 90])
+    return p, rho0, T0
+
+
+def heated_surface(Tc, rho_v, rho_l, nx=160, ny=160, nz=100, D=70.0, W=5.0, theta=120.0, Tw_frac=0.8931,
+                   Ts_frac=0.86, lam=1.0 / 3.0):
+    """Droplet evaporating on a heated surface as in Sec. 4.3: a droplet of diameter D on
+    the bounce-back bottom wall (contact angle theta, held at Tw_frac Tc), constant-pressure
+    top face (rho_b = rho_v at T_s), periodic in x and y, everything initially at T_s.  The
+    droplet is the sphere of diameter D whose cap meets the wall layer at the angle theta:
+    its centre lies R cos(pi - theta) above the wall layer.  The paper's a = 3/49 (with
+    which its h_lv = 0.5032 and T_w = 0.8931 T_c hold); Tc and the coexistence densities
+    are those of the caller (they depend on a only through Tc)."""
+    Ts, Tw = Ts_frac * Tc, Tw_frac * Tc
+    R = 0.5 * D
+    x, y, z = grid(nx, ny, nz)
+    zc = R * np.cos(np.pi - np.radians(theta))
+    r = np.sqrt((x - nx / 2.0) ** 2 + (y - ny / 2.0) ** 2 + (z - zc) ** 2)
+    rho0 = tanh_profile(r - R, rho_v, rho_l, W)
+    T0 = np.full_like(rho0, Ts)
+    T0[0] = Tw
+    p = base_params(nx, ny, nz, a=3.0 / 49.0, rho_l=rho_l, rho_v=rho_v, lambda_l=lam, lambda_v=lam,
                     face_kind=[PERIODIC, PERIODIC, PERIODIC, PERIODIC, WALL, OPEN],
                     face_T=[0, 0, 0, 0, Tw, Ts], face_rho=[0, 0, 0, 0, 0, rho_v],
                     face_theta_deg=[90, 90, 90, 90, theta, 90])

@@ -50,6 +50,8 @@ CASES = {
     "ragged_open_x": dict(shape=(13, 7, 11), face_kind=[2, 2, 0, 0, 0, 0]),
     "column_1x1": dict(shape=(1, 1, 40), face_kind=[0, 0, 0, 0, 1, 1]),
     "multi_tile_plane": dict(shape=(40, 30, 6), face_kind=[0, 0, 2, 2, 0, 0]),
+    # Sec. 4.2: periodic velocity field, every boundary node layer held at its face temperature
+    "periodic_held_T": dict(shape=(9, 10, 11), face_kind=[0] * 6, held=[1] * 6),
 }
 
 
@@ -60,7 +62,7 @@ def case_params(name, thermo):
     return W.base_params(nx, ny, nz, rho_l=thermo["rho_l"], rho_v=thermo["rho_v"], lambda_l=0.4, lambda_v=0.2,
                          face_kind=c["face_kind"], face_T=[Ts * (1 + 0.01 * k) for k in range(6)],
                          face_rho=[thermo["rho_v"] * (1 + 0.02 * k) for k in range(6)],
-                         face_theta_deg=c.get("theta", [90] * 6))
+                         face_theta_deg=c.get("theta", [90] * 6), face_T_fixed=c.get("held", [0] * 6))
 
 
 HALF_ULP = {lbm.STORE_F16_SHIFTED: 2.0 ** -11, lbm.STORE_BF16_SHIFTED: 2.0 ** -8, lbm.STORE_F16_LOCAL: 2.0 ** -11}
@@ -73,12 +75,14 @@ def _local_refs(f, g):
 
 
 def _face_nodes(p):
-    """Cells on a non-periodic face (where Zou-He and the extrapolation rewrite populations)."""
+    """Cells on a non-periodic face or a held temperature layer (where Zou-He and the
+    extrapolation rewrite populations)."""
     x, y, z = (a.reshape(-1) for a in W.grid(p["nx"], p["ny"], p["nz"]))
     n = (p["nx"], p["ny"], p["nz"])
     m = np.zeros(x.size, dtype=bool)
+    held = p.get("face_T_fixed", [0] * 6)
     for face, kind in enumerate(p["face_kind"]):
-        if kind != 0:
+        if kind != 0 or held[face]:
             coord = (x, y, z)[face // 2]
             m |= coord == (0 if face % 2 == 0 else n[face // 2] - 1)
     return m

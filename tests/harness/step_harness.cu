@@ -25,7 +25,7 @@ int host_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps,
   const long long N = P.N;
   std::vector<std::vector<float>> tface(6);
   for (int f = 0; f < 6; ++f)
-    if (hp->face_kind[f] != LBM_FACE_PERIODIC) {
+    if (P.tface[f]) {
       tface[f].assign((size_t)face_len(*hp, f), (float)hp->face_T[f]);
       if (tface_in && tface_in[f])
         for (size_t k = 0; k < tface[f].size(); ++k) tface[f][k] = tface_in[f][k];
@@ -85,7 +85,7 @@ int host_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps,
     for (long long k = 0; k < P.bd_total; ++k) {
       int x, y, z;
       boundary_candidate(P, (int)k, x, y, z);
-      const int m = node_faces(P, x, y, z);
+      const int m = node_tfaces(P, x, y, z);
       if (m) phaseD<ST>(P, cell_of(P, x, y, z), x, y, z, m, fb[B].data(), gb[B].data(), Xs);
     }
     cur = B;

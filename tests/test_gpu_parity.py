@@ -30,18 +30,6 @@ def _cuda():
     lbm.load()
 
 
-def march_rejects(p, schedule):
-    """The z-marching schedule takes walls with a contact angle of 90 degrees only; for
-    other walls lbm_init must refuse it (LBM_ERR_ARG)."""
-    if schedule != lbm.SCHED_MARCH or all(k != W.WALL or t == 90 for k, t in zip(p["face_kind"],
-                                                                                p["face_theta_deg"])):
-        return False
-    with pytest.raises(lbm.LBMError) as e:
-        lbm.Lattice(dict(p, schedule=schedule))
-    assert e.value.status == lbm.ERR_ARG
-    return True
-
-
 def gpu_step(p, f, g, n=1, schedule=lbm.SCHED_FUSED, tface=None):
     q = dict(p, schedule=schedule)
     lat = lbm.Lattice(q)
@@ -55,12 +43,10 @@ def gpu_step(p, f, g, n=1, schedule=lbm.SCHED_FUSED, tface=None):
     return st, fo, go
 
 
-@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_PHASES, lbm.SCHED_SLABS, lbm.SCHED_MARCH])
+@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_PHASES, lbm.SCHED_SLABS])
 @pytest.mark.parametrize("name", list(CASES))
 def test_one_step_populations_match_oracle(name, schedule, thermo):
     p = case_params(name, thermo)
-    if march_rejects(p, schedule):
-        return
     f, g = droplet_state(p, thermo, seed=11)
     o = Oracle(p)
     st_o, fo, go = o.step(f.astype(np.float64), g.astype(np.float64))
@@ -90,31 +76,6 @@ def test_fused_and_phase_schedules_agree(name, thermo):
     assert ef < 1e-5 and eg < 1e-5, (ef, eg)
 
 
-@pytest.mark.parametrize("zchunks", [1, 3, 7])
-@pytest.mark.parametrize("name", ["walls_z", "open_all", "periodic", "multi_tile_plane", "ragged_open_x"])
-def test_march_z_ranges_match_oracle(name, zchunks, thermo, monkeypatch):
-    """The z-marching kernels cut the lattice into z-ranges, each re-reading the planes
-    next to it; any cut gives the oracle's step (1e-5) and, over 20 steps, the one-launch-
-    per-phase schedule's result to rounding."""
-    p = case_params(name, thermo)
-    monkeypatch.setenv("LBM_MARCH_ZCHUNKS", str(zchunks))
-    f, g = droplet_state(p, thermo, seed=21)
-    st_o, fo, go = Oracle(p).step(f.astype(np.float64), g.astype(np.float64))
-    assert st_o == 0
-    st, fg, gg = gpu_step(p, f, g, 1, lbm.SCHED_MARCH)
-    assert st == lbm.OK
-    assert pop_err(fg, fo, thermo) < 1e-5 and pop_err(gg, go, thermo) < 1e-5
-    x, y, z = W.grid(p["nx"], p["ny"], p["nz"])
-    r2 = (x - 0.45 * p["nx"]) ** 2 + (y - 0.55 * p["ny"]) ** 2 + (z - 0.5 * p["nz"]) ** 2
-    rho0 = W.perturb(thermo["rho_v"] * (1.0 + 0.03 * np.exp(-r2 / 4.0)), 1e-3, seed=12)
-    f, g = Oracle(p).init_state(rho0, np.full(rho0.shape, thermo["Ts"]))
-    f, g = f32(f), f32(g)
-    _, f1, g1 = gpu_step(p, f, g, 20, lbm.SCHED_MARCH)
-    _, f2, g2 = gpu_step(p, f, g, 20, lbm.SCHED_PHASES)
-    ef, eg = pop_err(f1, f2.astype(np.float64), thermo), pop_err(g1, g2.astype(np.float64), thermo)
-    assert ef < 1e-5 and eg < 1e-5, (ef, eg)
-
-
 @pytest.mark.parametrize("name", list(CASES))
 def test_stream_maps_and_node_classes_bit_exact(name, thermo):
     p = case_params(name, thermo)
@@ -131,7 +92,7 @@ def test_stream_maps_and_node_classes_bit_exact(name, thermo):
     np.testing.assert_array_equal(cls, o.node_class())
 
 
-@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_PHASES, lbm.SCHED_SLABS, lbm.SCHED_MARCH])
+@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_PHASES, lbm.SCHED_SLABS])
 @pytest.mark.parametrize("name", ["open_all", "wall_bottom_open_top", "periodic"])
 def test_vartheta_one_steps_match_oracle(name, schedule, thermo):
     """Eq. 13 with the correction S_i of Eq. 16 (vartheta = 1), d^2T/dt^2 the backward second
@@ -237,7 +198,7 @@ def _slab_oracle(thermo):
     return _SLAB
 
 
-@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_PHASES, lbm.SCHED_SLABS, lbm.SCHED_MARCH])
+@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_PHASES, lbm.SCHED_SLABS])
 def test_slab_1000_steps_rho_T_match_oracle(schedule, thermo):
     """16x16x64 flat slab between bounce-back walls (bottom T_s + 0.02 T_c, top T_s), W = 2."""
     s = _slab_oracle(thermo)
@@ -263,13 +224,40 @@ def _drop_oracle(thermo):
     return tuple(_DROP[k] for k in ("p", "f0", "g0", "fo", "go"))
 
 
-@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_PHASES, lbm.SCHED_SLABS, lbm.SCHED_MARCH])
+@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_PHASES, lbm.SCHED_SLABS])
 def test_open_droplet_1000_steps_rho_T_match_oracle(schedule, thermo):
     """Evaporating droplet with constant-pressure faces on all six sides (20^3, R = 5)."""
     p, f0, g0, fo, go = _drop_oracle(thermo)
     _, fg, gg = gpu_step(p, f0, g0, 1000, schedule)
     assert relerr(fg.sum(0), fo.sum(0)) < 1e-3
     assert relerr(gg.sum(0), go.sum(0)) < 1e-3
+
+
+_DROP42 = {}
+
+
+@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_PHASES, lbm.SCHED_SLABS])
+def test_sec42_periodic_droplet_1000_steps_rho_T_match_oracle(schedule, thermo):
+    """The droplet of Sec. 4.2 in the paper's own setting: periodic velocity field, every
+    boundary node layer held at T_g = T_c (20^3, R = 5, W = 3)."""
+    if not _DROP42:
+        p, rho0, T0 = W.droplet(thermo["Tc"], thermo["rho_v"], thermo["rho_l"], n=20, R=5.0, W=3.0,
+                                faces=W.PERIODIC)
+        assert p["face_T_fixed"] == [1] * 6
+        o = Oracle(p)
+        f0, g0 = o.init_state(rho0, T0)
+        f0, g0 = f32(f0), f32(g0)
+        st, fo, go = o.run(f0.astype(np.float64), g0.astype(np.float64), 1000)
+        assert st == 0
+        _DROP42.update(p=p, f0=f0, g0=g0, fo=fo, go=go)
+    p, f0, g0, fo, go = (_DROP42[k] for k in ("p", "f0", "g0", "fo", "go"))
+    st, fg, gg = gpu_step(p, f0, g0, 1000, schedule)
+    assert st == lbm.OK
+    assert relerr(fg.sum(0), fo.sum(0)) < 1e-3
+    assert relerr(gg.sum(0), go.sum(0)) < 1e-3
+    # the held layers sit at T_g
+    T = gg.sum(0).reshape(20, 20, 20)
+    assert np.allclose(T[0], thermo["Tc"], rtol=1e-5) and np.allclose(T[:, :, -1], thermo["Tc"], rtol=1e-5)
 
 
 _FULL = {}
@@ -279,6 +267,10 @@ def _full_size_oracle(cfg, thermo):
     if cfg not in _FULL:
         if cfg == "d2_128":
             p, rho0, T0 = W.droplet(thermo["Tc"], thermo["rho_v"], thermo["rho_l"], n=128, R=15.0)
+        elif cfg == "heated_surface_160":
+            # Sec. 4.3 with the paper's a = 3/49: T_c from the oracle for that a
+            Tc = Oracle(W.base_params(4, 4, 4, a=3.0 / 49.0)).Tc()
+            p, rho0, T0 = W.heated_surface(Tc, thermo["rho_v"], thermo["rho_l"])
         else:
             p, rho0, T0 = W.sessile(thermo["Tc"], thermo["rho_v"], thermo["rho_l"])
         o = Oracle(p)
@@ -293,10 +285,11 @@ def _full_size_oracle(cfg, thermo):
     return _FULL[cfg]
 
 
-@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_SLABS, lbm.SCHED_MARCH])
-@pytest.mark.parametrize("cfg", ["d2_128", "sessile_256"])
+@pytest.mark.parametrize("schedule", [lbm.SCHED_FUSED, lbm.SCHED_SLABS])
+@pytest.mark.parametrize("cfg", ["d2_128", "sessile_256", "heated_surface_160"])
 def test_full_size_one_step_matches_oracle(cfg, schedule, thermo):
-    """One step at the benchmark sizes, in the launch configurations the benchmark times."""
+    """One step at the benchmark sizes, in the launch configurations the benchmark times, and
+    on the heated surface of Sec. 4.3 (160 x 160 x 100, contact angle 120 degrees)."""
     p, f0, g0, fo, go = _full_size_oracle(cfg, thermo)
     _, fg, gg = gpu_step(p, f0, g0, 1, schedule)
     assert pop_err(fg, fo, thermo) < 1e-5
@@ -332,12 +325,11 @@ def test_nonfinite_population_error_status(thermo):
 # With per-cell references (STORE_F16_LOCAL) rho_ref and T_ref of a population
 # written by a step are the rho and T its cell had before that step.
 @pytest.mark.parametrize("storage", STORAGES_16)
-@pytest.mark.parametrize("schedule", [lbm.SCHED_PHASES, lbm.SCHED_SLABS, lbm.SCHED_MARCH])
-@pytest.mark.parametrize("name", ["periodic", "open_all", "wall_bottom_open_top", "walls_xy_theta", "ragged_open_x"])
+@pytest.mark.parametrize("schedule", [lbm.SCHED_PHASES, lbm.SCHED_SLABS])
+@pytest.mark.parametrize("name", ["periodic", "open_all", "wall_bottom_open_top", "walls_xy_theta", "ragged_open_x",
+                                  "periodic_held_T"])
 def test_16bit_storage_one_step_within_half_ulp(name, schedule, storage, thermo):
     p = case_params(name, thermo)
-    if march_rejects(p, schedule):
-        return
     rho_ref, T_ref = 0.8 * thermo["rho_v"], thermo["Ts"]
     p.update(storage=storage, schedule=schedule, store_rho_ref=rho_ref, store_T_ref=T_ref)
     f, g = droplet_state(p, thermo, seed=11)

@@ -409,6 +409,7 @@ def test_mass_conserved_periodic_and_walls(thermo):
 def test_total_momentum_conserved_periodic(thermo):
     """Pairwise-antisymmetric interaction force: sum_x F = 0, so total momentum is invariant."""
     p, rho0, T0 = W.droplet(thermo["Tc"], thermo["rho_v"], thermo["rho_l"], n=8, R=2.5, W=2.0, faces=0)
+    p["face_T_fixed"] = [0] * 6
     o = Oracle(p)
     f, g = o.init_state(rho0, T0)
     f = f * (1 + 1e-3 * W.uniform(6, f.size).reshape(f.shape))
@@ -616,6 +617,28 @@ def test_steady_conduction_between_dirichlet_walls_is_exactly_linear():
     st, f, g = o.run(f, g, 4000)
     assert st == 0
     np.testing.assert_allclose(g.sum(0), 1.0 + 0.2 * np.arange(nz) / (nz - 1), rtol=1e-10)
+
+
+@pytest.mark.parametrize("both", [True, False])
+def test_fixed_temperature_layers_of_a_periodic_box(both):
+    """The setting of Sec. 4.2: the velocity field is periodic while the boundary node layers
+    hold a Dirichlet temperature (the extrapolation of Sec. 3.1 at those nodes).  A uniform
+    conductor at rest (ideal EOS) held at T = 1.0 on the layer z = 0 and 1.2 on z = nz - 1
+    reaches the linear profile exactly at every node: what crosses the periodic face lands
+    on a held layer and is overwritten.  With the top layer free instead, the heat that
+    leaves through the periodic face returns at the bottom and the column settles at the
+    held temperature everywhere.  The flow stays at rest (mass and f unchanged)."""
+    nz = 12
+    p = W.base_params(3, 2, nz, eos_kind=1, eos_c0=0.2, lambda_l=0.3, lambda_v=0.3, cv=1.0,
+                      face_T=[0, 0, 0, 0, 1.0, 1.2], face_T_fixed=[0, 0, 0, 0, 1, 1 if both else 0])
+    o = Oracle(p)
+    f, g = o.init_state(np.ones(3 * 2 * nz), np.full(3 * 2 * nz, 1.1))
+    st, f2, g2 = o.run(f, g, 6000)
+    assert st == 0
+    np.testing.assert_allclose(f2, f, rtol=1e-13)
+    T = g2.sum(0).reshape(nz, 2, 3)
+    expect = 1.0 + 0.2 * np.arange(nz) / (nz - 1) if both else np.ones(nz)
+    np.testing.assert_allclose(T, np.broadcast_to(expect[:, None, None], T.shape), rtol=1e-10)
 
 
 @pytest.mark.parametrize("theta", [90.0, 120.0, 60.0])
