@@ -93,6 +93,24 @@ def src_digest():
     return h.hexdigest()[:16]
 
 
+# the per-cell and phase code of the step kernels, and the block of lbm_api.cu that defines
+# the phase kernels (their launch bounds and loops)
+KERNEL_HEADERS = ("lbm_cell.cuh", "lbm_lattice.cuh", "lbm_phases.cuh")
+KERNEL_BLOCK = ("// Phase kernels over the cell range", "// FP64 block reduction")
+
+
+def kernel_digest():
+    """Digest of the step kernels' own source, so that host-side edits of the library do not
+    void an ncu traffic figure taken on unchanged kernels."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2206_00946_gb300", "csrc")
+    for f in KERNEL_HEADERS:
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    api = open(os.path.join(csrc, "lbm_api.cu")).read()
+    h.update(api[api.index(KERNEL_BLOCK[0]):api.index(KERNEL_BLOCK[1])].encode())
+    return h.hexdigest()[:16]
+
+
 def ncu_traffic(kernel: str, kernel_digest: str, n_cells: int):
     """DRAM bytes per launch from the committed ncu summary of `kernel`, if it was taken on this kernel source."""
     path = os.path.join(ROOT, "profiles", f"traffic_{kernel}.json")
@@ -652,7 +670,7 @@ def main():
     peak_src = "measured" if "hbm_gbs" in pk else "fallback"
     alg = kernel_alg_bytes(dom, esize)
     achieved = alg * N / (per_launch_ms * 1e-3) / 1e9 if alg else None
-    digest = src_digest()
+    digest = kernel_digest()
     traffic = ncu_traffic(dom + ("" if args.storage == "f32" else "_" + args.storage), digest, N)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:

@@ -565,8 +565,10 @@ int env_int(const char* name, int dflt) {
 
 void slab_plan_destroy(SlabPlan* S) {
   if (!S) return;
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < 2; ++k) {
     if (S->graph[k]) cudaGraphExecDestroy(S->graph[k]);
+    if (S->graph1[k]) cudaGraphExecDestroy(S->graph1[k]);
+  }
   for (auto e : S->ev)
     if (e) cudaEventDestroy(e);
   if (S->fork) cudaEventDestroy(S->fork);
@@ -723,11 +725,11 @@ void slab_join(lbm_ctx* c, cudaStream_t main) {
   }
 }
 
-// Captures graph_steps steps starting from the current parity into a graph.
-// The capture runs on the first slab stream (the caller's stream may be the
-// legacy default stream, which cannot be captured); the graph is then launched
-// on the caller's stream.
-int slab_capture(lbm_ctx* c) {
+// Captures `steps` steps starting from the current parity into *dst.  The capture
+// runs on the first slab stream (the caller's stream may be the legacy default
+// stream, which cannot be captured); the graph is then launched on the caller's
+// stream.
+int slab_capture(lbm_ctx* c, int steps, cudaGraphExec_t* dst) {
   SlabPlan& S = *c->slabs;
   const int parity = c->cur;
   cudaStream_t cs = S.st[0];
@@ -735,7 +737,7 @@ int slab_capture(lbm_ctx* c) {
   if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LBM_ERR_CUDA;
   slab_fork(c, cs);
   int st = LBM_OK;
-  for (int k = 0; k < S.graph_steps && st == LBM_OK; ++k) st = slab_enqueue_step(c, k == 0);
+  for (int k = 0; k < steps && st == LBM_OK; ++k) st = slab_enqueue_step(c, k == 0);
   slab_join(c, cs);
   const cudaError_t e = cudaStreamEndCapture(cs, &g);
   c->cur = parity;  // capture recorded the steps without running them
@@ -744,13 +746,13 @@ int slab_capture(lbm_ctx* c) {
     cudaGetLastError();
     return LBM_ERR_CUDA;
   }
-  const cudaError_t ie = cudaGraphInstantiate(&S.graph[parity], g, 0);
+  const cudaError_t ie = cudaGraphInstantiate(dst, g, 0);
   cudaGraphDestroy(g);
   return ie == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
-// Captures the graphs of both buffer parities up front (lbm_init), so that the first
-// lbm_step of a run of graph_steps or more steps pays no capture.
+// Captures the graphs of both buffer parities up front (lbm_init), so that no lbm_step
+// pays a capture: graph_steps steps for long runs and one step for the remainder.
 int slab_capture_both(lbm_ctx* c) {
   SlabPlan& S = *c->slabs;
   if (S.graph_steps <= 0) return LBM_OK;
@@ -758,7 +760,8 @@ int slab_capture_both(lbm_ctx* c) {
   int st = LBM_OK;
   for (int k = 0; k < 2 && st == LBM_OK; ++k) {
     c->cur = k;
-    if (!S.graph[k]) st = slab_capture(c);
+    if (!S.graph[k]) st = slab_capture(c, S.graph_steps, &S.graph[k]);
+    if (st == LBM_OK && !S.graph1[k]) st = slab_capture(c, 1, &S.graph1[k]);
   }
   c->cur = cur;
   return st;
@@ -771,10 +774,14 @@ int step_slabs(lbm_ctx* c, int n) {
   int done = 0;
   if (S.graph_steps > 0) {
     while (n - done >= S.graph_steps && st == LBM_OK) {
-      if (!S.graph[c->cur]) st = slab_capture(c);
+      if (!S.graph[c->cur]) st = slab_capture(c, S.graph_steps, &S.graph[c->cur]);
       if (st != LBM_OK) break;
       if (cudaGraphLaunch(S.graph[c->cur], c->stream) != cudaSuccess) st = LBM_ERR_CUDA;
       done += S.graph_steps;  // parity unchanged: graph_steps is even
+    }
+    for (; done < n && st == LBM_OK && S.graph1[c->cur]; ++done) {
+      if (cudaGraphLaunch(S.graph1[c->cur], c->stream) != cudaSuccess) st = LBM_ERR_CUDA;
+      c->cur = 1 - c->cur;
     }
   }
   if (st == LBM_OK && done < n) {

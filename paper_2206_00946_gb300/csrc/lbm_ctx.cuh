@@ -27,8 +27,8 @@ int lbm_step_phases_internal(lbm_ctx* c);  // one step, one launch per phase
 // C7(s) <- BC19(s-1..s+1); D(s) <- BC19, C7 (s-1..s+1); and across steps
 // A_t(s) <- BC19_{t-1}, C7_{t-1} (s-1..s+1), D_{t-1}(s).  Slabs hold at least
 // three planes, so the inward neighbour of a face node lies in its own slab.
-// A run of steps is captured once into a CUDA graph per buffer parity and
-// replayed.
+// A run of steps, and a single step, are captured once into CUDA graphs per
+// buffer parity and replayed.
 enum { SPH_A = 0, SPH_C19 = 1, SPH_C7 = 2, SPH_D = 3, SPH_N = 4 };
 constexpr int kMaxSlabStreams = 8;
 
@@ -42,7 +42,8 @@ struct SlabPlan {
   std::vector<cudaEvent_t> ev;         // per stage code
   cudaEvent_t fork = nullptr, join[kMaxSlabStreams] = {};
   int graph_steps = 0;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};   // graph_steps steps from buffer parity k
+  cudaGraphExec_t graph1[2] = {nullptr, nullptr};  // one step from buffer parity k
 };
 
 struct lbm_ctx {

@@ -47,6 +47,25 @@ def test_source_digest_covers_the_kernel_sources(tmp_path, monkeypatch):
     assert bench.src_digest() != d0
 
 
+def test_kernel_digest_follows_the_kernel_code_only(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_2206_00946_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in bench.KERNEL_HEADERS:
+        (csrc / f).write_text(f"header {f}")
+    api = ("host code before\n" + bench.KERNEL_BLOCK[0] + "\nKBODY\n" + bench.KERNEL_BLOCK[1] +
+           "\nreductions and host code after\n")
+    (csrc / "lbm_api.cu").write_text(api)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    d0 = bench.kernel_digest()
+    (csrc / "lbm_api.cu").write_text(api.replace("host code after", "host code edited"))
+    assert bench.kernel_digest() == d0
+    (csrc / "lbm_api.cu").write_text(api.replace("KBODY", "KBODY edited"))
+    assert bench.kernel_digest() != d0
+    (csrc / "lbm_api.cu").write_text(api)
+    (csrc / bench.KERNEL_HEADERS[2]).write_text("edited")
+    assert bench.kernel_digest() != d0
+
+
 def test_clock_summary_reads_median_max_and_reasons():
     s = bench.ClockSampler(0)
     s.lines = [
