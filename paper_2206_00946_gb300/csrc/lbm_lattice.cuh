@@ -122,6 +122,28 @@ LBM_HD void make_nb(const Params& P, int x, int y, int z, Nb& nb) {
   }
 }
 
+// The table of a cell whose moves cross no wall or open face and no y or z face: plain
+// strides, wrapped across periodic x faces, kind 0 everywhere (INNER).
+LBM_HD void make_nb_inner(const Params& P, int x, Nb& nb) {
+  const int st[3] = {1, P.nx, P.nx * P.ny};
+  nb.off[0][0] = x == 0 ? P.nx - 1 : -1;
+  nb.off[0][1] = x == P.nx - 1 ? 1 - P.nx : 1;
+#pragma unroll
+  for (int a = 1; a < 3; ++a) {
+    nb.off[a][0] = -st[a];
+    nb.off[a][1] = st[a];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) nb.kind[a][0] = nb.kind[a][1] = 0;
+}
+
+// true when the cell lies away from the y and z faces and, unless x is periodic, from
+// the x faces: the cells that make_nb_inner describes
+LBM_HD bool inner_cell(const Params& P, int x, int y, int z) {
+  return (P.face_kind[0] == FACE_PERIODIC || (x >= 1 && x <= P.nx - 2)) && y >= 1 && y <= P.ny - 2 && z >= 1 &&
+         z <= P.nz - 2;
+}
+
 // kinds crossed by a move (cx, cy, cz), OR-ed (FACE_WALL = 1, FACE_OPEN = 2)
 LBM_HD int nb_kind(const Nb& nb, int cx, int cy, int cz) {
   return (cx ? nb.kind[0][cx > 0] : 0) | (cy ? nb.kind[1][cy > 0] : 0) | (cz ? nb.kind[2][cz > 0] : 0);
@@ -137,6 +159,32 @@ LBM_HD int nb_off_psi(const Nb& nb, int cx, int cy, int cz) {
   if (cy) o += nb.kind[1][cy > 0] == FACE_WALL ? nb.off[1][cy < 0] : nb.off[1][cy > 0];
   if (cz) o += nb.kind[2][cz > 0] == FACE_WALL ? nb.off[2][cz < 0] : nb.off[2][cz > 0];
   return o;
+}
+
+// The lookups of a table known at compile time to belong to a cell that crosses no wall
+// or open face (INNER): the kind is 0 and the psi rule is the (wrapped) offset.
+template <bool INNER>
+LBM_HD int nbk(const Nb& nb, int cx, int cy, int cz) {
+  if constexpr (INNER)
+    return 0;
+  else
+    return nb_kind(nb, cx, cy, cz);
+}
+template <bool INNER>
+LBM_HD int nbo_psi(const Nb& nb, int cx, int cy, int cz) {
+  if constexpr (INNER)
+    return nb_off(nb, cx, cy, cz);
+  else
+    return nb_off_psi(nb, cx, cy, cz);
+}
+
+// v on every active lane of the warp (device); the lane's own v on the host
+LBM_DEV bool warp_all(bool v) {
+#if defined(__CUDA_ARCH__)
+  return __all_sync(__activemask(), v);
+#else
+  return v;
+#endif
 }
 
 // load through L2 only (cache-global); a plain load on the host

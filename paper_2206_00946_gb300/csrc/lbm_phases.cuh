@@ -295,10 +295,6 @@ LBM_DEV void boundary_candidate(const Params& P, int idx, int& x, int& y, int& z
   boundary_xy(P, z, k, x, y);
 }
 
-LBM_DEV bool interior1(const Params& P, int x, int y, int z) {
-  return x >= 1 && x <= P.nx - 2 && y >= 1 && y <= P.ny - 2 && z >= 1 && z <= P.nz - 2;
-}
-
 // ------------------------------------------------------------------- A -----
 LBM_DEV float face_T_at(const Params& P, int face, int x, int y, int z) {
   const int a = face >> 1;
@@ -422,14 +418,16 @@ LBM_DEV bool needs_wetting(const Params& P, const Nb& nb) {
 }
 
 // F = -G psi(x) sum_i varpi_i psi(x + c_i) c_i (Eq. 6), ghost psi beyond the faces
+// (INNER: no move of the cell crosses a wall or an open face)
+template <bool INNER = false>
 LBM_DEV void force_at(const Params& P, int c, int x, int y, int z, const Nb& nb, const Aux& X,
                                          const Hint& h, float& Fx, float& Fy, float& Fz) {
   const float* psi = X.psi;
   float sx = 0.f, sy = 0.f, sz = 0.f;
-  if (!needs_wetting(P, nb)) {
+  if (INNER || !needs_wetting(P, nb)) {
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
-      const float v = varpi19(i) * ld_aux(psi + c + nb_off_psi(nb, c19x(i), c19y(i), c19z(i)), h);
+      const float v = varpi19(i) * ld_aux(psi + c + nbo_psi<INNER>(nb, c19x(i), c19y(i), c19z(i)), h);
       if (c19x(i)) sx += c19x(i) * v;  // zero components skipped (0 * v is not folded away)
       if (c19y(i)) sy += c19y(i) * v;
       if (c19z(i)) sz += c19z(i) * v;
@@ -514,27 +512,34 @@ LBM_DEV void phaseC19_cell(const Params& P, int c, const float* fl, ST* fB, cons
 
 // Phases B and C19 of one cell in one pass: the force from the psi stencil, the
 // real velocity (both stored for the D3Q7 phase and the next step's open faces),
-// then the D3Q19 collision and push of phaseC19_cell.
-template <typename ST>
-LBM_DEV void phaseBC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB, const AuxFor<ST>& X) {
-  int x, y, z;
-  cell_xyz(P, c, x, y, z);
+// then the D3Q19 collision and push of phaseC19_cell.  INNER: no move of the cell
+// crosses a wall or an open face (periodic faces only wrap the offsets).
+template <typename ST, bool INNER>
+LBM_DEV void phaseBC19_body(const Params& P, int c, int x, int y, int z, const ST* __restrict__ fA, ST* fB,
+                            const AuxFor<ST>& X) {
   Nb nb;
-  make_nb(P, x, y, z, nb);
+  if (INNER)
+    make_nb_inner(P, x, nb);
+  else
+    make_nb(P, x, y, z, nb);
   const long long N = P.N;
   const Hint h = make_hint();
   float Fx, Fy, Fz;
-  force_at(P, c, x, y, z, nb, X, h, Fx, Fy, Fz);
-  st_aux(X.Fx + c, Fx, h);
-  st_aux(X.Fy + c, Fy, h);
-  st_aux(X.Fz + c, Fz, h);
+  force_at<INNER>(P, c, x, y, z, nb, X, h, Fx, Fy, Fz);
+  // F is read again only by the open-face rule at face nodes (never in an interior warp)
+  // and by the adjoint, whose recomputed steps pass the g* slot
+  if (!INNER || X.gstar) {
+    st_aux(X.Fx + c, Fx, h);
+    st_aux(X.Fy + c, Fy, h);
+    st_aux(X.Fz + c, Fz, h);
+  }
   const float rin = ref_in_at<ST>(X, c).x;
   float fl[19];
 #pragma unroll
   for (int i = 0; i < 19; ++i) fl[i] = PopStore<ST>::ld(fA + i * N + c, fbase_at<ST>(P, i, rin), h);
   float rho, jx, jy, jz;
   sum19(fl, rho, jx, jy, jz);
-  const int m = P.any_nonperiodic ? node_faces(P, x, y, z) : 0;
+  const int m = (!INNER && P.any_nonperiodic) ? node_faces(P, x, y, z) : 0;
   const bool wall = m && on_wall(P, m);
   const float ir = rcp(rho);
   float vx = 0.f, vy = 0.f, vz = 0.f;
@@ -555,7 +560,7 @@ LBM_DEV void phaseBC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB
     collide19(P, fl, rho, ux, uy, uz, Fx, Fy, Fz, fs);
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
-    const int k = nb_kind(nb, c19x(i), c19y(i), c19z(i));
+    const int k = nbk<INNER>(nb, c19x(i), c19y(i), c19z(i));
     if (k == 0) {
       const int d = c + nb_off(nb, c19x(i), c19y(i), c19z(i));
       // per-cell references: the destination's rho of this step (phase A stored it)
@@ -568,13 +573,26 @@ LBM_DEV void phaseBC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB
   }
 }
 
+// The force + D3Q19 pass of one cell: warps none of whose cells crosses a wall or an open
+// face take the interior form (the same arithmetic without the face rules).
+template <typename ST>
+LBM_DEV void phaseBC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB, const AuxFor<ST>& X) {
+  int x, y, z;
+  cell_xyz(P, c, x, y, z);
+  if (warp_all(inner_cell(P, x, y, z)))
+    phaseBC19_body<ST, true>(P, c, x, y, z, fA, fB, X);
+  else
+    phaseBC19_body<ST, false>(P, c, x, y, z, fA, fB, X);
+}
+
 // div u = 3 sum_i w_i c_i . u(x + c_i): the isotropic D3Q19 difference of the
 // real velocity (zero beyond a wall, the boundary node's value beyond an open face).
+template <bool INNER = false>
 LBM_DEV float divu_at(const Params& P, int c, const Nb& nb, const Aux& X, const Hint& h) {
   float du = 0.f;
 #pragma unroll
   for (int i = 1; i < 19; ++i) {
-    const int k = nb_kind(nb, c19x(i), c19y(i), c19z(i));
+    const int k = nbk<INNER>(nb, c19x(i), c19y(i), c19z(i));
     if (k & FACE_WALL) continue;  // zero velocity beyond a wall
     const int n = c + nb_off(nb, c19x(i), c19y(i), c19z(i));
     float s = 0.f;
@@ -589,15 +607,17 @@ LBM_DEV float divu_at(const Params& P, int c, const Nb& nb, const Aux& X, const 
 // Phase C, D3Q7 part: div u by the isotropic D3Q19 difference, grad T from the
 // local moments, collision with the source, relaxed push streaming.  rho and the
 // real velocity of the cell come from phases A and B.
-// VT: vartheta known at compile time (0 or 1), or -1 to read it from P.
-template <typename ST, int VT = -1>
-LBM_DEV void phaseC7_cell(const Params& P, int c, const float* gl, const ST* __restrict__ gA, ST* gB,
-                                             const AuxFor<ST>& X) {
+// VT: vartheta known at compile time (0 or 1), or -1 to read it from P.  INNER: no move
+// of the cell crosses a wall or an open face.
+template <typename ST, int VT, bool INNER>
+LBM_DEV void phaseC7_body(const Params& P, int c, int x, int y, int z, const float* gl, const ST* __restrict__ gA,
+                          ST* gB, const AuxFor<ST>& X) {
   const bool vt = VT < 0 ? P.vartheta != 0 : VT != 0;
-  int x, y, z;
-  cell_xyz(P, c, x, y, z);
   Nb nb;
-  make_nb(P, x, y, z, nb);
+  if (INNER)
+    make_nb_inner(P, x, nb);
+  else
+    make_nb(P, x, y, z, nb);
   const long long N = P.N;
   const Hint h = make_hint();
   // the destinations' g_i and rho of the relaxed streaming, loaded first so that
@@ -609,7 +629,7 @@ LBM_DEV void phaseC7_cell(const Params& P, int c, const float* gl, const ST* __r
   int yc[7];
 #pragma unroll
   for (int i = 1; i < 7; ++i) {
-    const bool ok = nb_kind(nb, c7x(i), c7y(i), c7z(i)) == 0;
+    const bool ok = nbk<INNER>(nb, c7x(i), c7y(i), c7z(i)) == 0;
     yc[i] = c + (ok ? nb_off(nb, c7x(i), c7y(i), c7z(i)) : 0);
     gold[i] = PopStore<ST>::ld(gA + i * N + yc[i], gbase_at<ST>(P, i, ref_in_at<ST>(X, yc[i]).y), h);
     if constexpr (LocalRef<ST>::on) {
@@ -631,7 +651,7 @@ LBM_DEV void phaseC7_cell(const Params& P, int c, const float* gl, const ST* __r
     T1 = X.T1[c];
     d2T = T - 2.f * T1 + X.T2[c];
   }
-  const float du = divu_at(P, c, nb, X, h);
+  const float du = divu_at<INNER>(P, c, nb, X, h);
   float p, dpdT;
   eos_pr(P, rho, T, p, dpdT);
   float gs[7];
@@ -646,13 +666,26 @@ LBM_DEV void phaseC7_cell(const Params& P, int c, const float* gl, const ST* __r
   PopStore<ST>::st(gB + c, gl[0] + (gs[0] - gl[0]) * rcp(rho * P.cv), gbase_at<ST>(P, 0, rc.y));
 #pragma unroll
   for (int i = 1; i < 7; ++i) {
-    if (nb_kind(nb, c7x(i), c7y(i), c7z(i))) continue;
+    if (nbk<INNER>(nb, c7x(i), c7y(i), c7z(i))) continue;
     PopStore<ST>::st(gB + i * N + yc[i], gold[i] + (gs[i] - gold[i]) * rcp(ry[i] * P.cv), gbase_at<ST>(P, i, ty[i]));
   }
   if (vt) {
     X.T2[c] = T1;
     X.T1[c] = T;
   }
+}
+
+// The D3Q7 pass of one cell: warps none of whose cells crosses a wall or an open face
+// take the interior form.
+template <typename ST, int VT = -1>
+LBM_DEV void phaseC7_cell(const Params& P, int c, const float* gl, const ST* __restrict__ gA, ST* gB,
+                                             const AuxFor<ST>& X) {
+  int x, y, z;
+  cell_xyz(P, c, x, y, z);
+  if (warp_all(inner_cell(P, x, y, z)))
+    phaseC7_body<ST, VT, true>(P, c, x, y, z, gl, gA, gB, X);
+  else
+    phaseC7_body<ST, VT, false>(P, c, x, y, z, gl, gA, gB, X);
 }
 
 template <typename ST>
