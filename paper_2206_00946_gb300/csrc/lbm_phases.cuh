@@ -40,12 +40,19 @@ struct AuxRef : Aux {
 // while the 44 B/cell of scratch written by phases A and B and read by the
 // next phases (92 MB at 128^3) is kept (evict-last), so that it is served from
 // L2 instead of making a round trip to HBM between kernels.
-struct Hint {
+// FREE: the loads below are plain asm statements, which the compiler may reorder and
+// interleave; otherwise they are volatile and keep the order of the source, which the
+// kernels were written for (the per-cell-reference D3Q7 kernel is faster with FREE, the
+// others without).
+template <bool FREE>
+struct HintT {
   unsigned long long stream, keep;
 };
+using Hint = HintT<false>;
 
-LBM_DEV Hint make_hint() {
-  Hint h;
+template <bool FREE = false>
+LBM_DEV HintT<FREE> make_hint() {
+  HintT<FREE> h;
 #if defined(__CUDA_ARCH__)
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(h.stream));
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(h.keep));
@@ -58,24 +65,32 @@ LBM_DEV Hint make_hint() {
 // Population stores keep the default policy: a push-streamed warp store is shifted
 // by one cell for x-moving directions and so covers two sectors partially; evicting
 // early would write each sector twice and force an ECC read-modify-write in HBM.
-LBM_DEV void st_pop(float* a, float v, const Hint&) { *a = v; }
+template <bool F>
+LBM_DEV void st_pop(float* a, float v, const HintT<F>&) { *a = v; }
 
 #if defined(LBM_NO_L2HINT)
-LBM_DEV float ld_pop(const float* a, const Hint&) {
+template <bool F>
+LBM_DEV float ld_pop(const float* a, const HintT<F>&) {
 #if defined(__CUDA_ARCH__)
   return __ldg(a);
 #else
   return *a;
 #endif
 }
-LBM_DEV float ld_aux(const float* a, const Hint&) { return *a; }
-LBM_DEV void st_aux(float* a, float v, const Hint&) { *a = v; }
+template <bool F>
+LBM_DEV float ld_aux(const float* a, const HintT<F>&) { return *a; }
+template <bool F>
+LBM_DEV void st_aux(float* a, float v, const HintT<F>&) { *a = v; }
 #else
 // populations of the previous time step (read-only during the step)
-LBM_DEV float ld_pop(const float* a, const Hint& h) {
+template <bool F>
+LBM_DEV float ld_pop(const float* a, const HintT<F>& h) {
 #if defined(__CUDA_ARCH__)
   float v;
-  asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(h.stream));
+  if constexpr (F)
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(h.stream));
+  else
+    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(h.stream));
   return v;
 #else
   return *a;
@@ -83,16 +98,21 @@ LBM_DEV float ld_pop(const float* a, const Hint& h) {
 }
 
 // scratch written and read within the step
-LBM_DEV float ld_aux(const float* a, const Hint& h) {
+template <bool F>
+LBM_DEV float ld_aux(const float* a, const HintT<F>& h) {
 #if defined(__CUDA_ARCH__)
   float v;
-  asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(h.keep));
+  if constexpr (F)
+    asm("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(h.keep));
+  else
+    asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(h.keep));
   return v;
 #else
   return *a;
 #endif
 }
-LBM_DEV void st_aux(float* a, float v, const Hint& h) {
+template <bool F>
+LBM_DEV void st_aux(float* a, float v, const HintT<F>& h) {
 #if defined(__CUDA_ARCH__)
   asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(h.keep));
 #else
@@ -130,16 +150,23 @@ struct PopStore;
 
 template <>
 struct PopStore<float> {
-  LBM_DEV static float ld(const float* a, float, const Hint& h) { return ld_pop(a, h); }
+  template <bool F>
+  LBM_DEV static float ld(const float* a, float, const HintT<F>& h) {
+    return ld_pop(a, h);
+  }
   LBM_DEV static float ld_plain(const float* a, float) { return *a; }
   LBM_DEV static void st(float* a, float v, float) { *a = v; }
   LBM_DEV static float round(float v, float) { return v; }
 };
 
-LBM_DEV unsigned short ld_u16_stream(const void* a, const Hint& h) {
+template <bool F>
+LBM_DEV unsigned short ld_u16_stream(const void* a, const HintT<F>& h) {
 #if defined(__CUDA_ARCH__)
   unsigned short v;
-  asm volatile("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(a), "l"(h.stream));
+  if constexpr (F)
+    asm("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(a), "l"(h.stream));
+  else
+    asm volatile("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(a), "l"(h.stream));
   return v;
 #else
   return *static_cast<const unsigned short*>(a);
@@ -148,7 +175,8 @@ LBM_DEV unsigned short ld_u16_stream(const void* a, const Hint& h) {
 
 template <>
 struct PopStore<__half> {
-  LBM_DEV static float ld(const __half* a, float base, const Hint& h) {
+  template <bool F>
+  LBM_DEV static float ld(const __half* a, float base, const HintT<F>& h) {
     return base + __half2float(__ushort_as_half(ld_u16_stream(a, h)));
   }
   LBM_DEV static float ld_plain(const __half* a, float base) { return base + __half2float(*a); }
@@ -161,7 +189,8 @@ struct PopStore<__half> {
 
 template <>
 struct PopStore<lhalf> {
-  LBM_DEV static float ld(const lhalf* a, float base, const Hint& h) {
+  template <bool F>
+  LBM_DEV static float ld(const lhalf* a, float base, const HintT<F>& h) {
     return base + __half2float(__ushort_as_half(ld_u16_stream(a, h)));
   }
   LBM_DEV static float ld_plain(const lhalf* a, float base) { return base + __half2float(a->v); }
@@ -173,7 +202,8 @@ struct PopStore<lhalf> {
 
 template <>
 struct PopStore<__nv_bfloat16> {
-  LBM_DEV static float ld(const __nv_bfloat16* a, float base, const Hint& h) {
+  template <bool F>
+  LBM_DEV static float ld(const __nv_bfloat16* a, float base, const HintT<F>& h) {
     return base + __bfloat162float(__ushort_as_bfloat16(ld_u16_stream(a, h)));
   }
   LBM_DEV static float ld_plain(const __nv_bfloat16* a, float base) {
@@ -524,6 +554,12 @@ LBM_DEV void phaseBC19_body(const Params& P, int c, int x, int y, int z, const S
     make_nb(P, x, y, z, nb);
   const long long N = P.N;
   const Hint h = make_hint();
+  // the populations first (they come from HBM), so that their latency overlaps the
+  // psi stencil of the force (mostly served by L1 and L2)
+  const float rin = ref_in_at<ST>(X, c).x;
+  float fl[19];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) fl[i] = PopStore<ST>::ld(fA + i * N + c, fbase_at<ST>(P, i, rin), h);
   float Fx, Fy, Fz;
   force_at<INNER>(P, c, x, y, z, nb, X, h, Fx, Fy, Fz);
   // F is read again only by the open-face rule at face nodes (never in an interior warp)
@@ -533,10 +569,6 @@ LBM_DEV void phaseBC19_body(const Params& P, int c, int x, int y, int z, const S
     st_aux(X.Fy + c, Fy, h);
     st_aux(X.Fz + c, Fz, h);
   }
-  const float rin = ref_in_at<ST>(X, c).x;
-  float fl[19];
-#pragma unroll
-  for (int i = 0; i < 19; ++i) fl[i] = PopStore<ST>::ld(fA + i * N + c, fbase_at<ST>(P, i, rin), h);
   float rho, jx, jy, jz;
   sum19(fl, rho, jx, jy, jz);
   const int m = (!INNER && P.any_nonperiodic) ? node_faces(P, x, y, z) : 0;
@@ -587,8 +619,8 @@ LBM_DEV void phaseBC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB
 
 // div u = 3 sum_i w_i c_i . u(x + c_i): the isotropic D3Q19 difference of the
 // real velocity (zero beyond a wall, the boundary node's value beyond an open face).
-template <bool INNER = false>
-LBM_DEV float divu_at(const Params& P, int c, const Nb& nb, const Aux& X, const Hint& h) {
+template <bool INNER = false, bool F = false>
+LBM_DEV float divu_at(const Params& P, int c, const Nb& nb, const Aux& X, const HintT<F>& h) {
   float du = 0.f;
 #pragma unroll
   for (int i = 1; i < 19; ++i) {
@@ -619,7 +651,7 @@ LBM_DEV void phaseC7_body(const Params& P, int c, int x, int y, int z, const flo
   else
     make_nb(P, x, y, z, nb);
   const long long N = P.N;
-  const Hint h = make_hint();
+  const auto h = make_hint<LocalRef<ST>::on>();
   // the destinations' g_i and rho of the relaxed streaming, loaded first so that
   // their latency overlaps the stencil and the collision (a move beyond a
   // non-periodic face reads the cell itself and stores nothing)
@@ -709,7 +741,7 @@ LBM_DEV void phaseC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB,
 template <typename ST, int VT = -1>
 LBM_DEV void phaseC7(const Params& P, int c, const ST* __restrict__ gA, ST* gB, const AuxFor<ST>& X) {
   const long long N = P.N;
-  const Hint h = make_hint();
+  const auto h = make_hint<LocalRef<ST>::on>();
   const float tin = ref_in_at<ST>(X, c).y;
   float gl[7];
 #pragma unroll
