@@ -748,11 +748,14 @@ int slab_capture(lbm_ctx* c, int steps, cudaGraphExec_t* dst) {
   }
   const cudaError_t ie = cudaGraphInstantiate(dst, g, 0);
   cudaGraphDestroy(g);
-  return ie == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+  if (ie != cudaSuccess) return LBM_ERR_CUDA;
+  // move the graph to the device now rather than at its first launch
+  return cudaGraphUpload(*dst, cs) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
-// Captures the graphs of both buffer parities up front (lbm_init), so that no lbm_step
-// pays a capture: graph_steps steps for long runs and one step for the remainder.
+// Captures (and uploads) the graphs of both buffer parities up front (lbm_init), so that no
+// lbm_step pays a capture or an upload: graph_steps steps for long runs and one step for the
+// remainder.
 int slab_capture_both(lbm_ctx* c) {
   SlabPlan& S = *c->slabs;
   if (S.graph_steps <= 0) return LBM_OK;
