@@ -95,7 +95,7 @@ def src_digest():
 
 # the per-cell and phase code of the step kernels, and the block of lbm_api.cu that defines
 # the phase kernels (their launch bounds and loops)
-KERNEL_HEADERS = ("lbm_cell.cuh", "lbm_lattice.cuh", "lbm_phases.cuh")
+KERNEL_HEADERS = ("lbm_cell.cuh", "lbm_lattice.cuh", "lbm_phases.cuh", "lbm_stage.cuh")
 KERNEL_BLOCK = ("// Phase kernels over the cell range", "// FP64 block reduction")
 
 

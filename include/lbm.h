@@ -38,6 +38,10 @@
  * beyond rounding):
  *   LBM_SLAB_PLANES, LBM_SLAB_STREAMS, LBM_GRAPH_STEPS  planes per slab, streams
  *       and steps per CUDA graph of the pipelined slab schedule (read by lbm_init);
+ *   LBM_STAGE19, LBM_STAGE7  tiles of 256 cells per CTA of the FP32 force + D3Q19 and D3Q7
+ *       kernels that stage their populations in shared memory (default 4; 0 turns staging
+ *       off; read by lbm_init; lattices whose planes do not divide into 256-cell tiles, or
+ *       of fewer than 622,592 cells, never stage);
  *   LBM_ADJ_EAGER, LBM_ADJ_NOPDL  launch every adjoint step on its own instead of
  *       replaying K-step segments from graphs / without programmatic dependent
  *       launches (read by each lbm_adjoint_step).
@@ -223,13 +227,19 @@ int lbm_set_face_T(lbm_ctx* ctx, int face, const float* T_face, int mem);
 /* Advances n >= 0 time steps; asynchronous on the context stream. */
 int lbm_step(lbm_ctx* ctx, int n);
 
-/* Failure detection test support (host-side injection; no GPU fault).  Makes the
- * next lbm_step of a LBM_SCHED_FUSED context wait on plane-completion counters that
+/* Failure detection test support (host-side injection; no GPU fault).
+ * LBM_SCHED_FUSED: makes the next lbm_step wait on plane-completion counters that
  * nothing will advance (they are cleared while the step count is kept), so that its
- * bounded device-side waits give up after about 2 s; the launch then aborts and
- * lbm_sync returns LBM_ERR_TIMEOUT.  The context stays usable: lbm_set_state or
- * lbm_restore clears the condition.  LBM_ERR_ARG for other schedules; LBM_ERR_STATE
- * before the first step. */
+ * bounded device-side waits give up after about 2 s; the launch then aborts.
+ * LBM_SCHED_PHASES / LBM_SCHED_SLABS with staged kernels (FP32 lattices of at least
+ * 622,592 cells whose planes divide into 256-cell tiles): the first CTA 0 of the next
+ * staged launch expects 16 bytes more than its first tile's bulk copies bring, so that
+ * its bounded mbarrier waits give up after about 1 s; it waits (bounded) for the copies
+ * it issued, which all complete, and leaves its tiles unstepped.
+ * Either way lbm_sync then returns LBM_ERR_TIMEOUT and the state is not to be used; the
+ * context stays usable: lbm_set_state or lbm_restore clears the condition.
+ * LBM_ERR_ARG for a context with neither; LBM_ERR_STATE for a fused context before its
+ * first step. */
 int lbm_inject_stall(lbm_ctx* ctx);
 
 /* Macroscopic fields of the current state: rho = sum f (Eq. 3), the real

@@ -12,6 +12,7 @@
 #include "lbm.h"
 #include "lbm_fused.cuh"
 #include "lbm_phases.cuh"
+#include "lbm_stage.cuh"
 #include "lbm_ctx.cuh"
 
 using namespace lbm;
@@ -107,6 +108,33 @@ __global__ void __launch_bounds__(256, LBM_PHASEC_MINBLOCKS) k_phaseBC19(Params 
     phaseBC19(P, c, fA, fB, X);
 }
 
+// CTAs of a staged launch over ntiles tiles: `per` tiles each, but never fewer than the
+// launch's share of four CTAs per SM among the slab launches that run at once (all of them
+// for the phase schedule's single launch), and at most four per SM.
+int staged_grid(const lbm_ctx* c, int ntiles, int per) {
+  const int slots = 152 * 4;
+  const int conc = c->slabs ? std::max(1, std::min(c->slabs->nslab, c->slabs->nstreams)) : 1;
+  const int g = std::max((ntiles + per - 1) / per, slots / conc);
+  return std::max(1, std::min(std::min(g, ntiles), slots));
+}
+
+// Force + D3Q19 over [c0, c1): with staged populations (k_phaseBC19_staged, stage19 tiles per
+// CTA, at most four CTAs per SM) when the context allows it, else one cell per thread.
+template <typename T>
+void launch_bc19(const lbm_ctx* c, const AuxFor<T>& X, int blocks, cudaStream_t st, const T* fA, T* fB, int c0,
+                 int c1) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->stage19 > 0) {
+      const int ntiles = (c1 - c0) / kStageT;
+      const int grid = staged_grid(c, ntiles, c->stage19);
+      const size_t smem = 2 * 19 * kStageT * sizeof(T) + 16;
+      k_phaseBC19_staged<T><<<grid, kStageT, smem, st>>>(c->P, fA, fB, X, c0, c1, c->err_d);
+      return;
+    }
+  }
+  k_phaseBC19<T><<<blocks, kThreads, 0, st>>>(c->P, fA, fB, X, c0, c1);
+}
+
 // VT: vartheta of the context (a separate instantiation each, launched by launch_c7)
 template <typename T, int VT>
 __global__ void __launch_bounds__(256, 4) k_phaseC7(Params P, const T* __restrict__ gA, T* gB, AuxFor<T> X, int c0,
@@ -117,6 +145,18 @@ __global__ void __launch_bounds__(256, 4) k_phaseC7(Params P, const T* __restric
 
 template <typename T>
 void launch_c7(const lbm_ctx* c, const AuxFor<T>& X, int blocks, cudaStream_t st, const T* gA, T* gB, int c0, int c1) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->stage7 > 0) {
+      const int ntiles = (c1 - c0) / kStageT;
+      const int grid = staged_grid(c, ntiles, c->stage7);
+      const size_t smem = 2 * 7 * kStageT * sizeof(T) + 16;
+      if (c->P.vartheta)
+        k_phaseC7_staged<T, 1><<<grid, kStageT, smem, st>>>(c->P, gA, gB, X, c0, c1, c->err_d);
+      else
+        k_phaseC7_staged<T, 0><<<grid, kStageT, smem, st>>>(c->P, gA, gB, X, c0, c1, c->err_d);
+      return;
+    }
+  }
   if (c->P.vartheta)
     k_phaseC7<T, 1><<<blocks, kThreads, 0, st>>>(c->P, gA, gB, X, c0, c1);
   else
@@ -487,7 +527,7 @@ int step_phases_t(lbm_ctx* c) {
                                                    (int)c->N, 0);
   prof_end(c, 0, e);
   e = prof_begin(c);
-  k_phaseBC19<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, a), fbuf<T>(c, b), X, 0, (int)c->N);
+  launch_bc19<T>(c, X, c->grid, c->stream, fbuf<T>(c, a), fbuf<T>(c, b), 0, (int)c->N);
   prof_end(c, 2, e);
   // the D3Q7 phase needs the velocity of the neighbours: after the whole D3Q19 pass
   e = prof_begin(c);
@@ -684,7 +724,7 @@ int slab_enqueue_step_t(lbm_ctx* c, bool first) {
         k_phaseA<T><<<blocks, kThreads, 0, st>>>(c->P, fbuf<T>(c, a), gbuf<T>(c, a), X, nullptr, c->err_d, c0, c1, 0);
         break;
       case SPH_C19:
-        k_phaseBC19<T><<<blocks, kThreads, 0, st>>>(c->P, fbuf<T>(c, a), fbuf<T>(c, b), X, c0, c1);
+        launch_bc19<T>(c, X, blocks, st, fbuf<T>(c, a), fbuf<T>(c, b), c0, c1);
         break;
       case SPH_C7:
         launch_c7<T>(c, X, blocks, st, gbuf<T>(c, a), gbuf<T>(c, b), c0, c1);
@@ -965,6 +1005,17 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
   c->stream = (cudaStream_t)stream;
   c->N = c->P.N;
   c->grid = grid_for(c->N);
+  // Force + D3Q19 and D3Q7 with staged populations: FP32, every slab and the lattice divide
+  // into whole tiles, and the lattice has at least four tiles per resident CTA (four per SM),
+  // so that the copy of the next tile has one to overlap.  Smaller lattices, and the 16-bit
+  // forms (tile rows of 512 bytes), measured slower staged.  LBM_STAGE19 and LBM_STAGE7 set
+  // the tiles per CTA (0: off).
+  {
+    const bool stage = p->storage == LBM_STORE_F32 && (p->nx * p->ny) % kStageT == 0 &&
+                       c->N >= 4ll * 152 * 4 * kStageT;
+    c->stage19 = stage ? std::max(0, env_int("LBM_STAGE19", 4)) : 0;
+    c->stage7 = stage ? std::max(0, env_int("LBM_STAGE7", 4)) : 0;
+  }
   c->esize = p->storage == LBM_STORE_F32 ? sizeof(float) : 2;
   cudaGetDevice(&c->device);
   const long long N = c->N;
@@ -979,7 +1030,7 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
   ok = ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
-  ok = ok && cudaMalloc(&c->err_d, sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc(&c->err_d, 2 * sizeof(int)) == cudaSuccess;  // error flags, stall request
   ok = ok && cudaMallocHost(&c->err_h, sizeof(int)) == cudaSuccess;
   c->red_blocks = grid_for(N) < 1024 ? grid_for(N) : 1024;
   ok = ok && cudaMalloc(&c->partial, sizeof(double) * 4 * c->red_blocks) == cudaSuccess;
@@ -1004,7 +1055,7 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const float* rho0, const float*
     c->X.T1 = c->hist;
     c->X.T2 = c->hist + N;
   }
-  if (cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream) != cudaSuccess) {
+  if (cudaMemsetAsync(c->err_d, 0, 2 * sizeof(int), c->stream) != cudaSuccess) {
     lbm_destroy(c);
     return LBM_ERR_CUDA;
   }
@@ -1068,7 +1119,7 @@ int lbm_set_state(lbm_ctx* c, const float* f, const float* g, int mem) {
   if (!st) st = hist_reset(c);
   if (!st && mem == LBM_MEM_HOST) st = cuda_status(cudaStreamSynchronize(c->stream));
   if (!st && fused_reset(&c->plan, c->P, c->stream)) st = LBM_ERR_CUDA;
-  if (!st) st = cuda_status(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream));
+  if (!st) st = cuda_status(cudaMemsetAsync(c->err_d, 0, 2 * sizeof(int), c->stream));  // flags and stall request
   if (!st) c->has_state = true;
   return st;
 }
@@ -1171,7 +1222,7 @@ int lbm_restore(lbm_ctx* c, const void* src, int mem) {
     LBM_TRY(cudaMemcpyAsync(ref_of(c, c->cur), s + sizeof(h) + fb + gb + hb, c->N * sizeof(float2), kd, c->stream));
   if (mem == LBM_MEM_HOST) LBM_TRY(cudaStreamSynchronize(c->stream));
   if (fused_reset(&c->plan, c->P, c->stream)) return LBM_ERR_CUDA;
-  LBM_TRY(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream));
+  LBM_TRY(cudaMemsetAsync(c->err_d, 0, 2 * sizeof(int), c->stream));  // flags and stall request
   c->has_state = true;
   return LBM_OK;
 }
@@ -1185,7 +1236,16 @@ int lbm_set_face_T(lbm_ctx* c, int face, const float* T_face, int mem) {
 }
 
 int lbm_inject_stall(lbm_ctx* c) {
-  if (!c || c->hp.schedule != LBM_SCHED_FUSED || !c->plan.done_d) return LBM_ERR_ARG;
+  if (!c) return LBM_ERR_ARG;
+  if (c->hp.schedule != LBM_SCHED_FUSED) {
+    // staged kernels: the next one that runs expects 16 bytes more than its first tile's
+    // copies bring, so that its bounded mbarrier waits give up
+    if (!(c->stage19 > 0 || c->stage7 > 0)) return LBM_ERR_ARG;
+    const int one = 1;
+    LBM_TRY(cudaMemcpyAsync(c->err_d + 1, &one, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    return cuda_status(cudaStreamSynchronize(c->stream));
+  }
+  if (!c->plan.done_d) return LBM_ERR_ARG;
   if (c->plan.epoch == 0) return LBM_ERR_STATE;  // the counters are at their start anyway
   // the next launch waits for (epoch + 1) * tiles completions per plane; from zero it
   // reaches one step's worth only

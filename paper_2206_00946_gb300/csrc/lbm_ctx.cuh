@@ -69,6 +69,8 @@ struct lbm_ctx {
   double* red_h;
   int red_blocks;
   int grid;
+  int stage19;      // force + D3Q19 with staged populations: tiles per CTA (0: off)
+  int stage7;       // D3Q7 with staged populations: tiles per CTA (0: off)
   bool has_state;
   cudaStream_t side;  // second stream for the D3Q7 collision
   cudaEvent_t ev_fork, ev_join;

@@ -544,9 +544,12 @@ LBM_DEV void phaseC19_cell(const Params& P, int c, const float* fl, ST* fB, cons
 // real velocity (both stored for the D3Q7 phase and the next step's open faces),
 // then the D3Q19 collision and push of phaseC19_cell.  INNER: no move of the cell
 // crosses a wall or an open face (periodic faces only wrap the offsets).
-template <typename ST, bool INNER>
+// STAGED: the cell's stored populations are read from sf[i * kStaged] (a tile staged in
+// shared memory) instead of fA.
+constexpr int kStaged = 256;
+template <typename ST, bool INNER, bool STAGED>
 LBM_DEV void phaseBC19_body(const Params& P, int c, int x, int y, int z, const ST* __restrict__ fA, ST* fB,
-                            const AuxFor<ST>& X) {
+                            const AuxFor<ST>& X, const ST* sf) {
   Nb nb;
   if (INNER)
     make_nb_inner(P, x, nb);
@@ -558,8 +561,13 @@ LBM_DEV void phaseBC19_body(const Params& P, int c, int x, int y, int z, const S
   // psi stencil of the force (mostly served by L1 and L2)
   const float rin = ref_in_at<ST>(X, c).x;
   float fl[19];
+  if constexpr (STAGED) {
 #pragma unroll
-  for (int i = 0; i < 19; ++i) fl[i] = PopStore<ST>::ld(fA + i * N + c, fbase_at<ST>(P, i, rin), h);
+    for (int i = 0; i < 19; ++i) fl[i] = PopStore<ST>::ld_plain(sf + i * kStaged, fbase_at<ST>(P, i, rin));
+  } else {
+#pragma unroll
+    for (int i = 0; i < 19; ++i) fl[i] = PopStore<ST>::ld(fA + i * N + c, fbase_at<ST>(P, i, rin), h);
+  }
   float Fx, Fy, Fz;
   force_at<INNER>(P, c, x, y, z, nb, X, h, Fx, Fy, Fz);
   // F is read again only by the open-face rule at face nodes (never in an interior warp)
@@ -607,14 +615,19 @@ LBM_DEV void phaseBC19_body(const Params& P, int c, int x, int y, int z, const S
 
 // The force + D3Q19 pass of one cell: warps none of whose cells crosses a wall or an open
 // face take the interior form (the same arithmetic without the face rules).
+template <typename ST, bool STAGED = false>
+LBM_DEV void phaseBC19(const Params& P, int c, int x, int y, int z, const ST* __restrict__ fA, ST* fB,
+                       const AuxFor<ST>& X, const ST* sf = nullptr) {
+  if (warp_all(inner_cell(P, x, y, z)))
+    phaseBC19_body<ST, true, STAGED>(P, c, x, y, z, fA, fB, X, sf);
+  else
+    phaseBC19_body<ST, false, STAGED>(P, c, x, y, z, fA, fB, X, sf);
+}
 template <typename ST>
 LBM_DEV void phaseBC19(const Params& P, int c, const ST* __restrict__ fA, ST* fB, const AuxFor<ST>& X) {
   int x, y, z;
   cell_xyz(P, c, x, y, z);
-  if (warp_all(inner_cell(P, x, y, z)))
-    phaseBC19_body<ST, true>(P, c, x, y, z, fA, fB, X);
-  else
-    phaseBC19_body<ST, false>(P, c, x, y, z, fA, fB, X);
+  phaseBC19<ST, false>(P, c, x, y, z, fA, fB, X);
 }
 
 // div u = 3 sum_i w_i c_i . u(x + c_i): the isotropic D3Q19 difference of the
@@ -747,6 +760,20 @@ LBM_DEV void phaseC7(const Params& P, int c, const ST* __restrict__ gA, ST* gB, 
 #pragma unroll
   for (int i = 0; i < 7; ++i) gl[i] = PopStore<ST>::ld(gA + i * N + c, gbase_at<ST>(P, i, tin), h);
   phaseC7_cell<ST, VT>(P, c, gl, gA, gB, X);
+}
+
+// phaseC7 with the cell's 7 stored populations read from sg[i * kStaged] (a staged tile)
+template <typename ST, int VT>
+LBM_DEV void phaseC7_staged(const Params& P, int c, int x, int y, int z, const ST* sg, const ST* __restrict__ gA,
+                            ST* gB, const AuxFor<ST>& X) {
+  const float tin = ref_in_at<ST>(X, c).y;
+  float gl[7];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) gl[i] = PopStore<ST>::ld_plain(sg + i * kStaged, gbase_at<ST>(P, i, tin));
+  if (warp_all(inner_cell(P, x, y, z)))
+    phaseC7_body<ST, VT, true>(P, c, x, y, z, gl, gA, gB, X);
+  else
+    phaseC7_body<ST, VT, false>(P, c, x, y, z, gl, gA, gB, X);
 }
 
 template <typename ST>
