@@ -122,6 +122,33 @@ def test_vartheta_one_steps_match_oracle(name, schedule, thermo):
     assert pop_err(gg, go, thermo) < 1e-5
 
 
+@pytest.mark.parametrize("schedule", [lbm.SCHED_PHASES, lbm.SCHED_SLABS])
+@pytest.mark.parametrize("vartheta", [0, 1])
+def test_staged_kernels_match_oracle(vartheta, schedule, thermo):
+    """A 96 x 96 x 72 lattice with open faces (663,552 cells, planes of 36 tiles of 256 cells)
+    is large enough for the FP32 force + D3Q19 and D3Q7 kernels that stage each tile's
+    populations in shared memory.  Three steps of the smooth vapour state of the vartheta test
+    against the oracle (vartheta = 1 with the T history of Eq. 16), every population within the
+    one-step tolerance."""
+    p = dict(case_params("open_all", thermo), nx=96, ny=96, nz=72, vartheta=vartheta)
+    x, y, z = W.grid(p["nx"], p["ny"], p["nz"])
+    r2 = (x - 0.45 * p["nx"]) ** 2 + (y - 0.55 * p["ny"]) ** 2 + (z - 0.5 * p["nz"]) ** 2
+    rho0 = W.perturb(thermo["rho_v"] * (1.0 + 0.03 * np.exp(-r2 / 40.0)), 1e-3, seed=12)
+    T0 = thermo["Ts"] * (1 + 0.01 * np.sin(0.7 * x + 0.5 * y + 0.3 * z))
+    o = Oracle(p, omp=True)
+    f, g = o.init_state(rho0, T0)
+    f, g = f32(f), f32(g)
+    if vartheta:
+        st_o, fo, go, _ = o.run_hist(f.astype(np.float64), g.astype(np.float64), o.history(g.astype(np.float64)), 3)
+    else:
+        st_o, fo, go = o.run(f.astype(np.float64), g.astype(np.float64), 3)
+    assert st_o == 0
+    st, fg, gg = gpu_step(p, f, g, 3, schedule)
+    assert st == lbm.OK
+    assert pop_err(fg, fo, thermo) < 1e-5
+    assert pop_err(gg, go, thermo) < 1e-5
+
+
 @pytest.mark.parametrize("storage", STORAGES_16)
 def test_vartheta_one_with_16bit_storage(storage, thermo):
     """The 16-bit forms apply the correction of Eq. 16 too (the T history stays FP32): after
