@@ -10,7 +10,11 @@
 // stencil reads (psi, u, the destinations of the relaxed push) stay plain loads.
 //
 // Every wait on an mbarrier is bounded (about one second).  On a timeout the kernel raises
-// ERRF_TIMEOUT, waits (again bounded) for the copies it issued and returns.
+// ERRF_TIMEOUT, waits (again bounded) for the copies it issued and returns.  A bulk copy of a
+// valid global range into the CTA's own shared memory always completes, so a wait runs out
+// only when the barrier expects more bytes than its copies bring (the stall that
+// lbm_inject_stall requests); every copy issued has then landed before the CTA exits.  The
+// drain is bounded all the same, so that no CTA can wait forever.
 #pragma once
 
 #include <cuda_runtime.h>
