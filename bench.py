@@ -38,6 +38,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -99,15 +100,23 @@ KERNEL_HEADERS = ("lbm_cell.cuh", "lbm_lattice.cuh", "lbm_phases.cuh", "lbm_stag
 KERNEL_BLOCK = ("// Phase kernels over the cell range", "// FP64 block reduction")
 
 
+def code_only(text: str) -> str:
+    """C++ source without its // and /* */ comments, runs of whitespace collapsed."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_digest():
-    """Digest of the step kernels' own source, so that host-side edits of the library do not
-    void an ncu traffic figure taken on unchanged kernels."""
+    """Digest of the step kernels' own code (comments and layout left out), so that host-side
+    edits of the library and edits of comments do not void an ncu traffic figure taken on
+    unchanged kernels."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2206_00946_gb300", "csrc")
     for f in KERNEL_HEADERS:
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        h.update(code_only(open(os.path.join(csrc, f)).read()).encode())
     api = open(os.path.join(csrc, "lbm_api.cu")).read()
-    h.update(api[api.index(KERNEL_BLOCK[0]):api.index(KERNEL_BLOCK[1])].encode())
+    h.update(code_only(api[api.index(KERNEL_BLOCK[0]):api.index(KERNEL_BLOCK[1])]).encode())
     return h.hexdigest()[:16]
 
 

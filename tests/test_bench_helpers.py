@@ -61,6 +61,8 @@ def test_kernel_digest_follows_the_kernel_code_only(tmp_path, monkeypatch):
     assert bench.kernel_digest() == d0
     (csrc / "lbm_api.cu").write_text(api.replace("KBODY", "KBODY edited"))
     assert bench.kernel_digest() != d0
+    (csrc / "lbm_api.cu").write_text(api.replace("KBODY", "KBODY // a comment"))
+    assert bench.kernel_digest() == d0  # comments and layout do not count
     (csrc / "lbm_api.cu").write_text(api)
     (csrc / bench.KERNEL_HEADERS[2]).write_text("edited")
     assert bench.kernel_digest() != d0
