@@ -310,8 +310,15 @@ int lbm_profile_read(lbm_ctx* ctx, long long* launches, double* ms, int nkinds);
 int lbm_reduce_static(const float* f, const float* g, long long n_cells, double cv, double rho_v, double rho_l,
                       double* out, void* stream);
 
-/* Number of kernel launches one lbm_step(ctx, 1) enqueues. */
+/* Kernel launches per time step within a long run.  When the face nodes are whole
+ * z planes (x and y faces periodic without held temperature layers) and the
+ * storage has no per-cell references, the slab schedule leaves the face rules
+ * (phase D) of every step but the last of a call to the next step's phase A, so
+ * a call adds its phase D launches once per sequence; lbm_step_launches counts
+ * them: the exact number of kernel launches of lbm_step(ctx, n), -1 for a bad
+ * argument. */
 int lbm_launches_per_step(const lbm_ctx* ctx);
+long long lbm_step_launches(const lbm_ctx* ctx, int n);
 
 #ifdef __cplusplus
 }

@@ -80,12 +80,13 @@ __global__ void k_load(Params P, const T* __restrict__ src, float* dst, int q, i
 
 // Phase kernels over the cell range [c0, c1) (whole planes) with grid-stride loops.
 // write_j: store j for phase B (only lbm_macros runs phase B on its own).
-template <typename T>
-__global__ void k_phaseA(Params P, const T* __restrict__ f, const T* __restrict__ g, AuxFor<T> X, float* Tout, int* err,
-                         int c0, int c1, int write_j) {
+// FUSE_D: also the face rules of the step that wrote the state (see phaseA)
+template <typename T, bool FUSE_D = false>
+__global__ void k_phaseA(Params P, const T* f, const T* g, AuxFor<T> X, float* Tout, int* err, int c0, int c1,
+                         int write_j) {
   int e = 0;
   for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x)
-    phaseA(P, c, f, g, X, Tout, e, write_j != 0);
+    phaseA<T, FUSE_D>(P, c, f, g, X, Tout, e, write_j != 0);
   if (e) atomicOr(err, e);
 }
 
@@ -585,8 +586,9 @@ void slab_deps_within(const SlabPlan& S, bool zper, int ph, int s, std::vector<i
 
 // stages of the previous step that phase A of slab s waits for: the pushes and
 // boundary rules that write slab s, and the reads of the scratch of slab s
-// that phase A overwrites
-void slab_deps_prev(const SlabPlan& S, bool zper, int s, std::vector<int>& d) {
+// that phase A overwrites.  with_d: the previous step ran its phase D stages (otherwise
+// this phase A applies the face rules itself; see phaseA)
+void slab_deps_prev(const SlabPlan& S, bool zper, int s, std::vector<int>& d, bool with_d = true) {
   d.clear();
   for (int k = -1; k <= 1; ++k) {
     bool ok;
@@ -595,7 +597,7 @@ void slab_deps_prev(const SlabPlan& S, bool zper, int s, std::vector<int>& d) {
     d.push_back(SPH_C19 * S.nslab + w);
     d.push_back(SPH_C7 * S.nslab + w);
   }
-  if (S.has_d[s]) d.push_back(SPH_D * S.nslab + s);
+  if (with_d && S.has_d[s]) d.push_back(SPH_D * S.nslab + s);
 }
 
 int env_int(const char* name, int dflt) {
@@ -697,9 +699,11 @@ int slab_plan_create(lbm_ctx* c) {
 
 // Enqueues one time step (buffers cur -> 1-cur) on the slab streams.  `first`:
 // the previous step's per-slab events are not waited for (the caller forked
-// all slab streams from the main stream after that step).
+// all slab streams from the main stream after that step).  `fuse`: the previous step left
+// its face rules to this step's phase A (it enqueued no phase D).  `emit_d`: this step
+// enqueues its phase D stages (the last step of every sequence does).
 template <typename T>
-int slab_enqueue_step_t(lbm_ctx* c, bool first) {
+int slab_enqueue_step_t(lbm_ctx* c, bool first, bool fuse, bool emit_d) {
   SlabPlan& S = *c->slabs;
   const int a = c->cur, b = 1 - c->cur;
   const AuxFor<T> X = aux_for<T>(c, a);
@@ -708,9 +712,10 @@ int slab_enqueue_step_t(lbm_ctx* c, bool first) {
   std::vector<int> d;
   for (int code : S.order) {
     const int ph = code / n, s = code % n;
+    if (ph == SPH_D && !emit_d) continue;
     cudaStream_t st = S.st[s % S.nstreams];
     if (ph == SPH_A) {
-      if (!first) slab_deps_prev(S, zper, s, d);
+      if (!first) slab_deps_prev(S, zper, s, d, !fuse);
       else d.clear();
     } else {
       slab_deps_within(S, zper, ph, s, d);
@@ -721,6 +726,13 @@ int slab_enqueue_step_t(lbm_ctx* c, bool first) {
     const int blocks = std::min(grid_for((long long)(c1 - c0)), 152 * 8);
     switch (ph) {
       case SPH_A:
+        if constexpr (!LocalRef<T>::on) {
+          if (fuse && S.has_d[s]) {
+            k_phaseA<T, true><<<blocks, kThreads, 0, st>>>(c->P, fbuf<T>(c, a), gbuf<T>(c, a), X, nullptr, c->err_d,
+                                                           c0, c1, 0);
+            break;
+          }
+        }
         k_phaseA<T><<<blocks, kThreads, 0, st>>>(c->P, fbuf<T>(c, a), gbuf<T>(c, a), X, nullptr, c->err_d, c0, c1, 0);
         break;
       case SPH_C19:
@@ -745,7 +757,24 @@ int slab_enqueue_step_t(lbm_ctx* c, bool first) {
   return cuda_status(cudaGetLastError());
 }
 
-int slab_enqueue_step(lbm_ctx* c, bool first) { return LBM_WITH_STORAGE(c, slab_enqueue_step_t, c, first); }
+int slab_enqueue_step(lbm_ctx* c, bool first, bool fuse, bool emit_d) {
+  return LBM_WITH_STORAGE(c, slab_enqueue_step_t, c, first, fuse, emit_d);
+}
+
+// Steps k = 0 .. steps-1 of one sequence of slab steps: phase D of every step but the last
+// goes into the next step's phase A, so that the state is complete when the sequence ends.
+// Only where the face nodes are whole z planes (the x and y faces periodic, without held
+// temperature layers): there every lane of a phase-A warp on a face plane applies the rules.
+// With x or y face nodes one lane in a warp would apply them while the others wait, and the
+// separate pass measured faster.  Not with per-cell references.
+bool slab_fuse_d(const lbm_ctx* c) {
+  const Params& P = c->P;
+  return c->hp.storage != LBM_STORE_F16_LOCAL && !(P.tface[0] || P.tface[1] || P.tface[2] || P.tface[3]);
+}
+int slab_enqueue_seq_step(lbm_ctx* c, int k, int steps) {
+  const bool fd = slab_fuse_d(c);
+  return slab_enqueue_step(c, k == 0, fd && k > 0, !fd || k == steps - 1);
+}
 
 // every slab stream waits for `main`
 void slab_fork(lbm_ctx* c, cudaStream_t main) {
@@ -777,7 +806,7 @@ int slab_capture(lbm_ctx* c, int steps, cudaGraphExec_t* dst) {
   if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LBM_ERR_CUDA;
   slab_fork(c, cs);
   int st = LBM_OK;
-  for (int k = 0; k < steps && st == LBM_OK; ++k) st = slab_enqueue_step(c, k == 0);
+  for (int k = 0; k < steps && st == LBM_OK; ++k) st = slab_enqueue_seq_step(c, k, steps);
   slab_join(c, cs);
   const cudaError_t e = cudaStreamEndCapture(cs, &g);
   c->cur = parity;  // capture recorded the steps without running them
@@ -829,7 +858,8 @@ int step_slabs(lbm_ctx* c, int n) {
   }
   if (st == LBM_OK && done < n) {
     slab_fork(c, c->stream);
-    for (int k = 0; done < n && st == LBM_OK; ++done, ++k) st = slab_enqueue_step(c, k == 0);
+    const int rest = n - done;
+    for (int k = 0; done < n && st == LBM_OK; ++done, ++k) st = slab_enqueue_seq_step(c, k, rest);
     slab_join(c, c->stream);
   }
   prof_end(c, 4, e);
@@ -1293,11 +1323,36 @@ int lbm_profile_read(lbm_ctx* c, long long* launches, double* ms, int nkinds) {
   return st;
 }
 
+namespace {
+int slab_d_stages(const lbm_ctx* c) {
+  int nd = 0;
+  for (char h : c->slabs->has_d) nd += h != 0;
+  return nd;
+}
+}  // namespace
+
 int lbm_launches_per_step(const lbm_ctx* c) {
   if (!c) return 0;
-  if (c->hp.schedule == LBM_SCHED_SLABS) return (int)c->slabs->order.size();
+  // slab schedule: in a long run the face rules of a step go into the next step's phase A
+  if (c->hp.schedule == LBM_SCHED_SLABS)
+    return (int)c->slabs->order.size() - (slab_fuse_d(c) ? slab_d_stages(c) : 0);
   if (c->hp.schedule == LBM_SCHED_FUSED) return fused_launches(&c->plan);
   return c->P.bd_total > 0 ? 4 : 3;
+}
+
+long long lbm_step_launches(const lbm_ctx* c, int n) {
+  if (!c || n < 0) return -1;
+  if (c->hp.schedule != LBM_SCHED_SLABS || !slab_fuse_d(c)) return (long long)n * lbm_launches_per_step(c);
+  // every sequence (a replayed graph, a one-step graph or an eager run) ends with phase D
+  const SlabPlan& S = *c->slabs;
+  long long seq = 0;
+  if (n > 0) {
+    if (S.graph_steps > 0 && S.graph1[0] && S.graph1[1])
+      seq = n / S.graph_steps + n % S.graph_steps;
+    else
+      seq = S.graph_steps > 0 ? n / S.graph_steps + (n % S.graph_steps ? 1 : 0) : 1;
+  }
+  return (long long)n * lbm_launches_per_step(c) + seq * slab_d_stages(c);
 }
 
 int lbm_macros(lbm_ctx* c, float* rho, float* ux, float* uy, float* uz, float* T, int mem) {

@@ -407,9 +407,18 @@ LBM_DEV void boundary_rules(const Params& P, int c, int x, int y, int z, int m, 
 }
 
 // write_j: store j for phase B (the fused force + D3Q19 pass recomputes it).
-template <typename ST>
-LBM_DEV void phaseA(const Params& P, int c, const ST* __restrict__ f, const ST* __restrict__ g,
-                                       const AuxFor<ST>& X, float* __restrict__ Tout, int& err, bool write_j = true) {
+// FUSE_D: the state's face rules were not applied by the step that wrote it (the slab
+// schedule leaves phase D of every step but the last of a call to the next step's phase A):
+// at a face node the rules of phase D (open-face rule, NEE) are applied here to the loaded
+// populations, written back to f and g, and the sums below use the corrected values.  The
+// rules read only the node's own populations, its force F and g at its inward neighbour,
+// which lies inside along every face normal and is never a face node, so no other thread of
+// this pass reads what they write.  Not for per-cell references, whose rules need the
+// references of the state being written.
+template <typename ST, bool FUSE_D = false>
+LBM_DEV void phaseA(const Params& P, int c, const ST* f, const ST* g, const AuxFor<ST>& X,
+                    float* __restrict__ Tout, int& err, bool write_j = true) {
+  static_assert(!(FUSE_D && LocalRef<ST>::on), "fused face rules need a global storage shift");
   const Hint h = make_hint();
   const float2 rin = ref_in_at<ST>(X, c);
   float fl[19], gl[7];
@@ -417,6 +426,12 @@ LBM_DEV void phaseA(const Params& P, int c, const ST* __restrict__ f, const ST* 
   for (int i = 0; i < 19; ++i) fl[i] = PopStore<ST>::ld(f + i * P.N + c, fbase_at<ST>(P, i, rin.x), h);
 #pragma unroll
   for (int i = 0; i < 7; ++i) gl[i] = PopStore<ST>::ld(g + i * P.N + c, gbase_at<ST>(P, i, rin.y), h);
+  if constexpr (FUSE_D) {
+    int x, y, z;
+    cell_xyz(P, c, x, y, z);
+    const int m = node_tfaces(P, x, y, z);
+    if (m) boundary_rules<ST>(P, c, x, y, z, m, fl, gl, const_cast<ST*>(f), const_cast<ST*>(g), X);
+  }
   float rho, jx, jy, jz;
   sum19(fl, rho, jx, jy, jz);
   const float T = sum7(gl);

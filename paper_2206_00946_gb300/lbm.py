@@ -44,7 +44,7 @@ class lbm_params(ct.Structure):
 # every symbol declared in include/lbm.h
 EXPORTS = ["lbm_init", "lbm_set_state", "lbm_get_state", "lbm_set_face_T", "lbm_step", "lbm_macros",
            "lbm_reduce", "lbm_sync", "lbm_stream_map", "lbm_destroy", "lbm_status_string", "lbm_Tc",
-           "lbm_maxwell", "lbm_launches_per_step", "lbm_profile", "lbm_profile_read", "lbm_reduce_static",
+           "lbm_maxwell", "lbm_launches_per_step", "lbm_step_launches", "lbm_profile", "lbm_profile_read", "lbm_reduce_static",
            "lbm_checkpoint_bytes", "lbm_checkpoint", "lbm_restore", "lbm_record", "lbm_adjoint_step",
            "lbm_adjoint_state", "lbm_batch_create", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_sync",
            "lbm_batch_cells", "lbm_batch_destroy", "lbm_batch_inject_stall", "lbm_inject_stall"]
@@ -86,6 +86,8 @@ def load(path: str = LIB_PATH):
     L.lbm_Tc.restype = _D
     L.lbm_maxwell.argtypes = [P, _D, ct.POINTER(_D), ct.POINTER(_D), ct.POINTER(_D)]
     L.lbm_launches_per_step.argtypes = [vp]
+    L.lbm_step_launches.argtypes = [vp, ct.c_int]
+    L.lbm_step_launches.restype = ct.c_longlong
     L.lbm_profile.argtypes = [vp, ct.c_int]
     L.lbm_profile_read.argtypes = [vp, vp, vp, ct.c_int]
     L.lbm_reduce_static.argtypes = [vp, vp, ct.c_longlong, _D, _D, _D, vp, vp]
@@ -319,6 +321,10 @@ class Lattice:
 
     def lbm_launches_per_step(self):
         return load().lbm_launches_per_step(self._ctx)
+
+    def lbm_step_launches(self, n):
+        """Kernel launches of lbm_step(n)."""
+        return load().lbm_step_launches(self._ctx, n)
 
     def lbm_profile(self, enable=True):
         _check(load().lbm_profile(self._ctx, int(bool(enable))), "lbm_profile")

@@ -122,10 +122,12 @@ extern "C" {
 // (stage code = phase * nslab + slab; phases A, BC19, C7, D = 0..3), for every stage
 // code the stages of the same step it waits for (deps_within, 8 per code, -1 padded),
 // and for every slab the stages of the previous step its phase A waits for
-// (deps_prev, 8 per slab, -1 padded).  max_slab bounds the arrays: zb holds max_slab + 1,
-// order and deps_within 4 * max_slab (x 8), deps_prev max_slab x 8.  Returns 0 or -1.
+// (deps_prev, 8 per slab, -1 padded), and the same when the previous step left its face
+// rules to this phase A (deps_prev_fused).  max_slab bounds the arrays: zb holds
+// max_slab + 1, order and deps_within 4 * max_slab (x 8), deps_prev and deps_prev_fused
+// max_slab x 8.  has_d (max_slab) receives the slabs that hold face nodes.  Returns 0 or -1.
 int h_slab_plan(const lbm_params* hp, int sp, int max_slab, int* nslab, int* zb, int* order, int* norder,
-                int* deps_within, int* deps_prev) {
+                int* deps_within, int* deps_prev, int* deps_prev_fused, int* has_d) {
   if (check_params(hp) != LBM_OK) return -1;
   const Params P = make_device_params(*hp);
   SlabPlan S;
@@ -145,6 +147,10 @@ int h_slab_plan(const lbm_params* hp, int sp, int max_slab, int* nslab, int* zb,
     slab_deps_prev(S, zper, s, d);
     if (d.size() > 8) return -1;
     for (int k = 0; k < 8; ++k) deps_prev[s * 8 + k] = k < (int)d.size() ? d[k] : -1;
+    slab_deps_prev(S, zper, s, d, false);
+    if (d.size() > 8) return -1;
+    for (int k = 0; k < 8; ++k) deps_prev_fused[s * 8 + k] = k < (int)d.size() ? d[k] : -1;
+    has_d[s] = S.has_d[s];
   }
   return 0;
 }

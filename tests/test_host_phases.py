@@ -209,17 +209,21 @@ def slab_plan(H, p, sp, max_slab=64):
     order = np.zeros(4 * max_slab, np.int32)
     dw = np.zeros(4 * max_slab * 8, np.int32)
     dp = np.zeros(max_slab * 8, np.int32)
+    dpf = np.zeros(max_slab * 8, np.int32)
+    hd = np.zeros(max_slab, np.int32)
     H.h_slab_plan.argtypes = [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p,
-                              ct.c_void_p, ct.c_void_p]
+                              ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]
     assert H.h_slab_plan(ct.byref(P), sp, max_slab, ct.byref(nslab), zb.ctypes.data, order.ctypes.data,
-                         ct.byref(norder), dw.ctypes.data, dp.ctypes.data) == 0
+                         ct.byref(norder), dw.ctypes.data, dp.ctypes.data, dpf.ctypes.data, hd.ctypes.data) == 0
     n = nslab.value
     within = {c: [q for q in dw[c * 8:(c + 1) * 8] if q >= 0] for c in range(4 * n)}
     prev = {s: [q for q in dp[s * 8:(s + 1) * 8] if q >= 0] for s in range(n)}
+    prev_fused = {s: [q for q in dpf[s * 8:(s + 1) * 8] if q >= 0] for s in range(n)}
+    slab_plan.fused = (prev_fused, [bool(h) for h in hd[:n]])
     return n, list(zb[:n + 1]), list(order[:norder.value]), within, prev
 
 
-def stage_access(ph, s, t, zb, nz, zper):
+def stage_access(ph, s, t, zb, nz, zper, fused=False):
     """(resource, mode, planes) of stage (phase ph, slab s) in step t: what its kernel reads ('r')
     and writes ('w').  'p' marks the writes of the streaming pushes: every (direction,
     destination) has exactly one source cell, so two pushes never write the same element.
@@ -233,8 +237,11 @@ def stage_access(ph, s, t, zb, nz, zper):
         elif zper:
             halo.add(z % nz)
     if ph == A_:
-        return [(f"f{a}", "r", own), (f"g{a}", "r", own), (f"ref{a}", "r", own),
-                ("rho", "w", own), ("psi", "w", own), (f"ref{b}", "w", own)]
+        acc = [(f"f{a}", "r", own), (f"g{a}", "r", own), (f"ref{a}", "r", own),
+               ("rho", "w", own), ("psi", "w", own), (f"ref{b}", "w", own)]
+        if fused:  # the previous step's face rules on this slab's face nodes (F of that step)
+            acc += [("F", "r", own), (f"f{a}", "w", own), (f"g{a}", "w", own)]
+        return acc
     if ph == BC19_:  # force from the psi stencil; collide; push (with the destinations' rho)
         return [("psi", "r", halo), ("rho", "r", halo), (f"f{a}", "r", own), (f"ref{a}", "r", own),
                 ("F", "w", own), ("u", "w", own), (f"f{b}", "p", halo)]
@@ -245,16 +252,25 @@ def stage_access(ph, s, t, zb, nz, zper):
             (f"f{b}", "w", own), (f"g{b}", "w", own)]
 
 
-def unordered_conflicts(n, zb, order, within, prev, nz, zper):
-    seq = [(t, code) for t in (0, 1) for code in order]
+def unordered_conflicts(n, zb, order, within, prev, nz, zper, modes=((False, True, True), (False, True, False)),
+                        prev_fused=None, has_d=None):
+    """modes[t] = (fused, emit_d, first) of step t: its phase A applies the previous step's
+    face rules (waiting on prev_fused instead of prev), it runs its phase D stages, it starts
+    a new sequence (the library joins every slab stream before it)."""
+    seq = [(t, code) for t in range(len(modes)) for code in order if code // n != D_ or modes[t][1]]
     pos = {st: i for i, st in enumerate(seq)}
     preds = {st: set() for st in seq}
     for t, code in seq:
+        fused, _, first = modes[t]
         for q in within[code]:
-            preds[(t, code)].add((t, q))
-        if t == 1 and code // n == A_:
-            for q in prev[code % n]:
-                preds[(t, code)].add((0, q))
+            if (t, q) in pos:
+                preds[(t, code)].add((t, q))
+        if t > 0 and first:  # a new sequence: after everything before it
+            preds[(t, code)] |= {st for st in seq if st[0] < t}
+        elif t > 0 and code // n == A_:
+            for q in (prev_fused if fused else prev)[code % n]:
+                assert (t - 1, q) in pos, (t, code, q)
+                preds[(t, code)].add((t - 1, q))
     last_on_stream = {}
     for st in seq:  # the order of each stream
         k = (st[1] % n) % N_STREAMS
@@ -269,7 +285,9 @@ def unordered_conflicts(n, zb, order, within, prev, nz, zper):
             acc.add(q)
             acc |= before[q]
         before[st] = acc
-    acc = {st: stage_access(st[1] // n, st[1] % n, st[0], zb, nz, zper) for st in seq}
+    acc = {st: stage_access(st[1] // n, st[1] % n, st[0], zb, nz, zper,
+                            modes[st[0]][0] and st[1] // n == A_ and has_d is not None and has_d[st[1] % n])
+           for st in seq}
     bad = []
     for i, x in enumerate(seq):
         for y in seq[i + 1:]:
@@ -294,6 +312,12 @@ def test_slab_pipeline_orders_every_conflict(H, faces_z, nz, sp, thermo):
     assert len(set(order)) == len(order) and all(0 <= c < 4 * n for c in order)
     assert {c for c in order if c // n != D_} == {c for c in range(3 * n)}  # every A, BC19, C7 stage once
     bad = unordered_conflicts(n, zb, order, within, prev, nz, faces_z == 0)
+    assert not bad, bad[:5]
+    # sequences whose face rules go into the next step's phase A: three steps (plain, fused,
+    # fused with phase D), then a second sequence of two
+    prev_fused, has_d = slab_plan.fused
+    modes = ((False, False, True), (True, False, False), (True, True, False), (False, False, True), (True, True, False))
+    bad = unordered_conflicts(n, zb, order, within, prev, nz, faces_z == 0, modes, prev_fused, has_d)
     assert not bad, bad[:5]
 
 
