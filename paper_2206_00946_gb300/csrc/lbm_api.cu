@@ -90,6 +90,32 @@ __global__ void k_phaseA(Params P, const T* f, const T* g, AuxFor<T> X, float* T
   if (e) atomicOr(err, e);
 }
 
+int grid_for(long long n);
+
+// phase A of the cell pairs of [c0, c1) (c0 and c1 even), one global 16-bit shift
+template <typename T>
+__global__ void k_phaseA2(Params P, const T* f, const T* g, AuxFor<T> X, int* err, int c0, int c1) {
+  int e = 0;
+  for (int c = c0 + 2 * (blockIdx.x * blockDim.x + threadIdx.x); c < c1; c += 2 * gridDim.x * blockDim.x)
+    phaseA2<T>(P, c, f, g, X, e);
+  if (e) atomicOr(err, e);
+}
+
+// phase A of [c0, c1) in a step: two cells per thread for the global 16-bit shifts when the
+// planes have an even number of cells (every range then starts and ends on a pair)
+template <typename T>
+void launch_phaseA(const lbm_ctx* c, const AuxFor<T>& X, int blocks, cudaStream_t st, const T* f, const T* g, int c0,
+                   int c1) {
+  if constexpr (sizeof(T) == 2 && !LocalRef<T>::on) {
+    if ((c->P.nx * c->P.ny) % 2 == 0) {
+      const int grid = std::max(1, std::min(blocks, grid_for((long long)(c1 - c0) / 2)));
+      k_phaseA2<T><<<grid, kThreads, 0, st>>>(c->P, f, g, X, c->err_d, c0, c1);
+      return;
+    }
+  }
+  k_phaseA<T><<<blocks, kThreads, 0, st>>>(c->P, f, g, X, nullptr, c->err_d, c0, c1, 0);
+}
+
 __global__ void k_phaseB(Params P, Aux X, int c0, int c1) {
   for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x) phaseB(P, c, X);
 }
@@ -524,8 +550,7 @@ int step_phases_t(lbm_ctx* c) {
   const int a = c->cur, b = 1 - c->cur;
   const AuxFor<T> X = aux_for<T>(c, a);
   cudaEvent_t e = prof_begin(c);
-  k_phaseA<T><<<c->grid, kThreads, 0, c->stream>>>(c->P, fbuf<T>(c, a), gbuf<T>(c, a), X, nullptr, c->err_d, 0,
-                                                   (int)c->N, 0);
+  launch_phaseA<T>(c, X, c->grid, c->stream, fbuf<T>(c, a), gbuf<T>(c, a), 0, (int)c->N);
   prof_end(c, 0, e);
   e = prof_begin(c);
   launch_bc19<T>(c, X, c->grid, c->stream, fbuf<T>(c, a), fbuf<T>(c, b), 0, (int)c->N);
@@ -733,7 +758,7 @@ int slab_enqueue_step_t(lbm_ctx* c, bool first, bool fuse, bool emit_d) {
             break;
           }
         }
-        k_phaseA<T><<<blocks, kThreads, 0, st>>>(c->P, fbuf<T>(c, a), gbuf<T>(c, a), X, nullptr, c->err_d, c0, c1, 0);
+        launch_phaseA<T>(c, X, blocks, st, fbuf<T>(c, a), gbuf<T>(c, a), c0, c1);
         break;
       case SPH_C19:
         launch_bc19<T>(c, X, blocks, st, fbuf<T>(c, a), fbuf<T>(c, b), c0, c1);

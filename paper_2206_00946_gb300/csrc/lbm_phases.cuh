@@ -173,12 +173,27 @@ LBM_DEV unsigned short ld_u16_stream(const void* a, const HintT<F>& h) {
 #endif
 }
 
+// two neighbouring stored 16-bit populations as one 32-bit word (the lower cell in the low
+// half); a must be 4-byte aligned
+LBM_DEV unsigned ld_u32_stream(const void* a, const Hint& h) {
+#if defined(__CUDA_ARCH__)
+  unsigned v;
+  asm volatile("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(h.stream));
+  return v;
+#else
+  (void)h;
+  return *static_cast<const unsigned*>(a);
+#endif
+}
+
 template <>
 struct PopStore<__half> {
   template <bool F>
   LBM_DEV static float ld(const __half* a, float base, const HintT<F>& h) {
     return base + __half2float(__ushort_as_half(ld_u16_stream(a, h)));
   }
+  // the value of stored bits b
+  LBM_DEV static float dec(unsigned short b, float base) { return base + __half2float(__ushort_as_half(b)); }
   LBM_DEV static float ld_plain(const __half* a, float base) { return base + __half2float(*a); }
   LBM_DEV static void st(__half* a, float v, float base) { *a = __float2half_rn(v - base); }
   // the value a later load of st(v) returns
@@ -205,6 +220,9 @@ struct PopStore<__nv_bfloat16> {
   template <bool F>
   LBM_DEV static float ld(const __nv_bfloat16* a, float base, const HintT<F>& h) {
     return base + __bfloat162float(__ushort_as_bfloat16(ld_u16_stream(a, h)));
+  }
+  LBM_DEV static float dec(unsigned short b, float base) {
+    return base + __bfloat162float(__ushort_as_bfloat16(b));
   }
   LBM_DEV static float ld_plain(const __nv_bfloat16* a, float base) {
     return base + __bfloat162float(*a);
@@ -406,11 +424,36 @@ LBM_DEV void boundary_rules(const Params& P, int c, int x, int y, int z, int m, 
   }
 }
 
+// The sums, the EOS and psi of one cell whose stored populations are in fl, gl, and the
+// stores of phase A (shared by the per-cell and the two-cell forms).
+template <typename ST>
+LBM_DEV void phaseA_finish(const Params& P, int c, const float* fl, const float* gl, const AuxFor<ST>& X,
+                           float* __restrict__ Tout, int& err, bool write_j) {
+  const Hint h = make_hint();
+  float rho, jx, jy, jz;
+  sum19(fl, rho, jx, jy, jz);
+  const float T = sum7(gl);
+  // the references of the populations this step writes: this state's rho and T
+  if constexpr (LocalRef<ST>::on) X.ref_out[c] = make_float2(rho, T);
+  if (!isfinite(rho) || !isfinite(T) || !isfinite(jx + jy + jz)) err |= ERRF_NONFINITE;
+  float p, dpdT, psi;
+  eos_pr(P, rho, T, p, dpdT);
+  if (!psi_of(P, rho, p, psi)) err |= ERRF_PSI;
+  st_aux(X.rho + c, rho, h);
+  if (write_j) {
+    st_aux(X.jx + c, jx, h);
+    st_aux(X.jy + c, jy, h);
+    st_aux(X.jz + c, jz, h);
+  }
+  st_aux(X.psi + c, psi, h);
+  if (Tout) Tout[c] = T;
+}
+
 // write_j: store j for phase B (the fused force + D3Q19 pass recomputes it).
 // FUSE_D: the state's face rules were not applied by the step that wrote it (the slab
 // schedule leaves phase D of every step but the last of a call to the next step's phase A):
 // at a face node the rules of phase D (open-face rule, NEE) are applied here to the loaded
-// populations, written back to f and g, and the sums below use the corrected values.  The
+// populations, written back to f and g, and the sums of phaseA_finish use the corrected values.  The
 // rules read only the node's own populations, its force F and g at its inward neighbour,
 // which lies inside along every face normal and is never a face node, so no other thread of
 // this pass reads what they write.  Not for per-cell references, whose rules need the
@@ -432,23 +475,31 @@ LBM_DEV void phaseA(const Params& P, int c, const ST* f, const ST* g, const AuxF
     const int m = node_tfaces(P, x, y, z);
     if (m) boundary_rules<ST>(P, c, x, y, z, m, fl, gl, const_cast<ST*>(f), const_cast<ST*>(g), X);
   }
-  float rho, jx, jy, jz;
-  sum19(fl, rho, jx, jy, jz);
-  const float T = sum7(gl);
-  // the references of the populations this step writes: this state's rho and T
-  if constexpr (LocalRef<ST>::on) X.ref_out[c] = make_float2(rho, T);
-  if (!isfinite(rho) || !isfinite(T) || !isfinite(jx + jy + jz)) err |= ERRF_NONFINITE;
-  float p, dpdT, psi;
-  eos_pr(P, rho, T, p, dpdT);
-  if (!psi_of(P, rho, p, psi)) err |= ERRF_PSI;
-  st_aux(X.rho + c, rho, h);
-  if (write_j) {
-    st_aux(X.jx + c, jx, h);
-    st_aux(X.jy + c, jy, h);
-    st_aux(X.jz + c, jz, h);
+  phaseA_finish<ST>(P, c, fl, gl, X, Tout, err, write_j);
+}
+
+// Phase A of the two cells c and c + 1 (c even; N even) with one global storage shift: each
+// population pair is one 32-bit load, half the load instructions of two per-cell passes.
+template <typename ST>
+LBM_DEV void phaseA2(const Params& P, int c, const ST* f, const ST* g, const AuxFor<ST>& X, int& err) {
+  static_assert(sizeof(ST) == 2 && !LocalRef<ST>::on, "the two-cell form is for one global 16-bit shift");
+  const Hint h = make_hint();
+  unsigned wf[19], wg[7];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) wf[i] = ld_u32_stream(f + i * P.N + c, h);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) wg[i] = ld_u32_stream(g + i * P.N + c, h);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    float fl[19], gl[7];
+#pragma unroll
+    for (int i = 0; i < 19; ++i)
+      fl[i] = PopStore<ST>::dec((unsigned short)(k ? wf[i] >> 16 : wf[i] & 0xffffu), fbase_at<ST>(P, i, 0.f));
+#pragma unroll
+    for (int i = 0; i < 7; ++i)
+      gl[i] = PopStore<ST>::dec((unsigned short)(k ? wg[i] >> 16 : wg[i] & 0xffffu), gbase_at<ST>(P, i, 0.f));
+    phaseA_finish<ST>(P, c + k, fl, gl, X, nullptr, err, false);
   }
-  st_aux(X.psi + c, psi, h);
-  if (Tout) Tout[c] = T;
 }
 
 // ------------------------------------------------------------------- B -----
