@@ -16,10 +16,12 @@ void adj_free(lbm_ctx*) {}
 namespace {
 
 // tface[f] (may be NULL, as may any entry): a per-node Dirichlet temperature of face f, as
-// lbm_set_face_T takes it; NULL entries use face_T[f]
+// lbm_set_face_T takes it; NULL entries use face_T[f].  mode bit 1: the face rules of every
+// step but the last are applied by the next step's phase A (phaseA<ST, true>), as the slab
+// schedule does; bit 2: phase A two cells at a time (phaseA2; global 16-bit shifts, even N).
 template <typename ST>
 int host_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps, float* f_out, float* g_out,
-             const float* const* tface_in) {
+             const float* const* tface_in, int mode = 0) {
   if (check_params(hp) != LBM_OK) return LBM_ERR_ARG;
   Params P = make_device_params(*hp);
   const long long N = P.N;
@@ -74,7 +76,21 @@ int host_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps,
       Xs.ref_in = refs(A);
       Xs.ref_out = refs(B);
     }
-    for (long long c = 0; c < N; ++c) phaseA<ST>(P, (int)c, fb[A].data(), gb[A].data(), Xs, nullptr, err, false);
+    bool done_a = false;
+    if constexpr (!LocalRef<ST>::on) {
+      if ((mode & 1) && s > 0) {
+        for (long long c = 0; c < N; ++c)
+          phaseA<ST, true>(P, (int)c, fb[A].data(), gb[A].data(), Xs, nullptr, err, false);
+        done_a = true;
+      } else if constexpr (sizeof(ST) == 2) {
+        if ((mode & 2) && N % 2 == 0) {
+          for (long long c = 0; c < N; c += 2) phaseA2<ST>(P, (int)c, fb[A].data(), gb[A].data(), Xs, err);
+          done_a = true;
+        }
+      }
+    }
+    if (!done_a)
+      for (long long c = 0; c < N; ++c) phaseA<ST>(P, (int)c, fb[A].data(), gb[A].data(), Xs, nullptr, err, false);
     for (long long c = 0; c < N; ++c) phaseBC19<ST>(P, (int)c, fb[A].data(), fb[B].data(), Xs);
     for (long long c = 0; c < N; ++c) {
       if (hp->vartheta)
@@ -82,7 +98,8 @@ int host_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps,
       else
         phaseC7<ST, 0>(P, (int)c, gb[A].data(), gb[B].data(), Xs);
     }
-    for (long long k = 0; k < P.bd_total; ++k) {
+    const bool fused_next = (mode & 1) && !LocalRef<ST>::on && s < nsteps - 1;
+    for (long long k = 0; k < (fused_next ? 0 : P.bd_total); ++k) {
       int x, y, z;
       boundary_candidate(P, (int)k, x, y, z);
       const int m = node_tfaces(P, x, y, z);
@@ -111,6 +128,19 @@ int h_run(const lbm_params* hp, const float* f0, const float* g0, int nsteps, fl
     case LBM_STORE_F16_SHIFTED: return host_run<__half>(hp, f0, g0, nsteps, f_out, g_out, tface);
     case LBM_STORE_BF16_SHIFTED: return host_run<__nv_bfloat16>(hp, f0, g0, nsteps, f_out, g_out, tface);
     case LBM_STORE_F16_LOCAL: return host_run<lhalf>(hp, f0, g0, nsteps, f_out, g_out, tface);
+    default: return LBM_ERR_ARG;
+  }
+}
+
+// h_run with the schedule variants of host_run's mode (1: face rules in the next step's
+// phase A; 2: phase A two cells at a time)
+int h_run_mode(const lbm_params* hp, const float* f0, const float* g0, int nsteps, float* f_out, float* g_out,
+               const float* const* tface, int mode) {
+  switch (hp->storage) {
+    case LBM_STORE_F32: return host_run<float>(hp, f0, g0, nsteps, f_out, g_out, tface, mode);
+    case LBM_STORE_F16_SHIFTED: return host_run<__half>(hp, f0, g0, nsteps, f_out, g_out, tface, mode);
+    case LBM_STORE_BF16_SHIFTED: return host_run<__nv_bfloat16>(hp, f0, g0, nsteps, f_out, g_out, tface, mode);
+    case LBM_STORE_F16_LOCAL: return host_run<lhalf>(hp, f0, g0, nsteps, f_out, g_out, tface, mode);
     default: return LBM_ERR_ARG;
   }
 }
